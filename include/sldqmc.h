@@ -1,0 +1,202 @@
+/*
+ * sldqmc.h -- C ABI of the GB300 (sm_103a) self-learning determinantal QMC
+ * library.  Every entry point returns an int status: SLDQMC_OK (0) or a
+ * negative SLDQMC_ERR_* code; sldqmc_strerror() names it.
+ *
+ * Paper: X. Y. Xu, Y. Qi, J. Liu, L. Fu, Z. Y. Meng, "Self-Learning
+ * Determinantal Quantum Monte Carlo Method", arXiv:1612.03804 (PRB 96,
+ * 041119 (2017)).  Sections cited below: "Basics of DQMC" (Eq. 1 and the
+ * local update), "Formalism of SLDQMC" (Eqs. 2-4, steps i-iv), "Results"
+ * (Eq. 6, the model and the fit score R^2).
+ *
+ * Conventions shared by every call:
+ *   - Lattice: Lx x Ly periodic square lattice, N = Lx*Ly, site
+ *     i = x + Lx*y.  A direction of length 1 has no bond; a direction of
+ *     length 2 carries its bond twice (both wrap directions).
+ *   - Imaginary time: M = round(beta/dtau) slices; beta must equal M*dtau to
+ *     1e-12 relative.
+ *   - Field configuration s: int8 array of M*N values in {-1,+1},
+ *     tau-major (s[tau*N + i]); tau = 0..M-1 is slice tau+1.  Any other
+ *     value is rejected with SLDQMC_ERR_ARG (host-pointer calls) or flagged
+ *     as SLDQMC_ERR_ARG by the device checks (device-pointer calls).
+ *   - Slice matrix (Eq. 1 with K the hopping of Eq. 6):
+ *       B_tau = exp(-dtau K) diag(exp(eta dtau xi s_tau)),  K = -t A - mu I,
+ *     for flavour eta = +1 or -1.  The bilayer of Eq. 6 has two flavours of
+ *     each eta, so the fermion weight is
+ *       log omega_F = 2 ld(+1) + 2 ld(-1),  ld(eta) = log|det(1 + B_M..B_1)|.
+ *   - Matrices are row-major double, N x N.
+ *
+ * Ownership and threading: a context owns all device memory it allocates
+ * (at create time) and one CUDA stream (the caller's, or the legacy default
+ * stream when NULL).  Host-pointer calls copy in, run and copy out, and
+ * return after the stream has finished (synchronous).  Device-pointer calls
+ * (suffix _dev) take caller-owned device memory, are ordered on the
+ * context's stream and return before completion; their error flags are
+ * reported by sldqmc_sync().  A context is not thread-safe: use one per host
+ * thread / stream.  On any error the caller's output buffers are left
+ * unchanged by host-pointer calls.
+ */
+#ifndef SLDQMC_H
+#define SLDQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SLDQMC_OK 0
+#define SLDQMC_ERR_ARG (-1)       /* invalid argument or field value */
+#define SLDQMC_ERR_OOM (-2)       /* device allocation failed */
+#define SLDQMC_ERR_CUDA (-3)      /* a CUDA runtime call failed */
+#define SLDQMC_ERR_NUMERICAL (-4) /* non-positive Cholesky pivot, zero LU pivot or non-finite value */
+#define SLDQMC_ERR_TIMEOUT (-5)   /* a bounded device-side wait ran out */
+#define SLDQMC_ERR_UNSUPPORTED (-6)
+
+/* Arithmetic of the slice products inside a stabilisation block.  The
+ * stabilisation (QR), the final determinant, the Green's function and every
+ * Monte Carlo decision are FP64 in all modes. */
+typedef enum {
+    SLDQMC_FP64 = 0,   /* FP64 FMA products */
+    SLDQMC_3XTF32 = 1, /* split-TF32 tensor-core products (3 MMAs), FP32 accumulate */
+    SLDQMC_BF16 = 2    /* BF16 tensor-core products, FP32 accumulate */
+} sldqmc_prec;
+
+typedef struct {
+    int Lx, Ly;         /* lattice */
+    double t, mu, xi;   /* hopping, chemical potential, Ising-fermion coupling (Eq. 6) */
+    double beta, dtau;  /* inverse temperature and Trotter step */
+    int n_wrap;         /* slices per stabilisation block (>= 1) */
+    double J_ising, h;  /* Ising exchange and transverse field of H_s (Eq. 6) */
+    int prec;           /* sldqmc_prec */
+    int max_batch;      /* configurations evaluated together (workspace size), >= 1 */
+} sldqmc_params;
+
+typedef struct sldqmc_ctx sldqmc_ctx;
+
+typedef struct {
+    long long accepted;      /* accepted local flips */
+    long long proposed;      /* proposed local flips */
+    long long margin_events; /* decisions with |log r - log u| <= 1e-8 */
+    double max_drift;        /* max |G_wrapped - G_fresh| at re-computation */
+} sldqmc_stats;
+
+/* Create a context: validates params, allocates the workspace for
+ * max_batch configurations and builds exp(-dtau K) and exp(+dtau K) on the
+ * device.  stream: a cudaStream_t, or NULL for the default stream. */
+int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out);
+void sldqmc_destroy(sldqmc_ctx *ctx);
+const char *sldqmc_strerror(int status);
+/* N and M of the context. */
+int sldqmc_dims(const sldqmc_ctx *ctx, int *N, int *M);
+/* Waits for the context's stream and returns the first device-side error
+ * flag raised since the last call (then clears it). */
+int sldqmc_sync(sldqmc_ctx *ctx);
+
+/* build_K ("Basics of DQMC": K the hopping matrix; Eq. 6 fixes
+ * K = -t A - mu I).  Copies K, exp(-dtau K) and exp(+dtau K) (each N x N,
+ * row-major) to host buffers; any pointer may be NULL. */
+int sldqmc_build_K(sldqmc_ctx *ctx, double *K, double *expmK, double *exppK);
+
+/* weight (Eq. 1): log|det(1 + B_M..B_1)| and its sign for flavour eta
+ * (+1/-1).  eta = 0 returns the bilayer fermion weight
+ * log omega_F = 2 ld(+1) + 2 ld(-1) with sign +1.  s: host, M*N int8. */
+int sldqmc_weight(sldqmc_ctx *ctx, const int8_t *s, int eta, double *logabsdet, int *sign);
+
+/* Batched weight over B configurations (host buffers, synchronous).
+ * s: B*M*N int8; logabsdet: B doubles; sign: B ints (may be NULL).
+ * B may exceed max_batch (processed in chunks). */
+int sldqmc_weight_batch(sldqmc_ctx *ctx, const int8_t *s, int B, int eta, double *logabsdet,
+                        int *sign);
+
+/* Same on device buffers, stream-ordered.  eta must be +1 or -1. */
+int sldqmc_weight_batch_dev(sldqmc_ctx *ctx, const int8_t *d_s, int B, int eta,
+                            double *d_logabsdet, int *d_sign);
+
+/* green ("Basics of DQMC": the equal-time Green's function the local update
+ * needs): G(tau) = (1 + B_tau..B_1 B_M..B_{tau+1})^{-1}, N x N, for
+ * 0 <= tau <= M (tau = 0 and tau = M both give (1 + B_M..B_1)^{-1}), with
+ * the log|det| and sign of the same cyclic product.  Host buffers. */
+int sldqmc_green(sldqmc_ctx *ctx, const int8_t *s, int eta, int tau, double *G,
+                 double *logabsdet, int *sign);
+int sldqmc_green_batch_dev(sldqmc_ctx *ctx, const int8_t *d_s, int B, int eta, int tau,
+                           double *d_G, double *d_logabsdet, int *d_sign);
+
+/* Bare Ising weight phi(C) ("Basics of DQMC": the bare part including the
+ * transformation constant), read as the Trotter map of H_s of Eq. 6:
+ *   log phi = dtau J sum_tau sum_<ij> s s + Kt sum_i sum_tau s_{i,tau} s_{i,tau+1},
+ *   Kt = -ln(tanh(dtau h))/2, periodic in tau, configuration-independent
+ * constant dropped.  Host s. */
+int sldqmc_log_bare_weight(sldqmc_ctx *ctx, const int8_t *s, double *log_phi);
+
+/* Local DQMC sweeps ("Basics of DQMC"): flips s(i,tau) one by one in
+ * order tau = 1..M, i = 0..N-1; O(1) ratio from the Green's function
+ * (both flavours, each squared, times the phi ratio), O(N^2) Sherman-Morrison
+ * update on acceptance, slice-to-slice wrapping and a fresh Green's function
+ * every n_wrap slices.  Uniforms come from Philox-4x32-10 with key = seed and
+ * counter (i, tau, sweep0 + k, 1); accept iff log u < log r.
+ * s: host, M*N int8, updated in place.  stats may be NULL. */
+int sldqmc_local_sweep(sldqmc_ctx *ctx, int8_t *s, uint64_t seed, uint64_t sweep0, int n_sweeps,
+                       sldqmc_stats *stats);
+/* Batched over B independent chains on device buffers (chain b uses key
+ * seed + (b << 32)); stats: host array of B (may be NULL). */
+int sldqmc_local_sweep_batch_dev(sldqmc_ctx *ctx, int8_t *d_s, int B, uint64_t seed,
+                                 uint64_t sweep0, int n_sweeps, sldqmc_stats *stats);
+
+/* Effective model (Eq. 2): H_eff = E0 + sum_c J_c f_c(C),
+ * f_c(C) = sum_x sum_{o in class c} s_x s_{x+o}.  Class c has n_off[c]
+ * offsets (dx, dy, dtau), stored consecutively as int triples in offsets
+ * (each unordered pair once: give one of o and -o).  Self-pairs count 1.
+ * At most 32 classes and 64 offsets in total. */
+int sldqmc_set_effective_model(sldqmc_ctx *ctx, int n_class, const int *n_off, const int *offsets,
+                               const double *J, double E0);
+
+/* Features f_c for n_cfg configurations (host): F[n_cfg * n_class]. */
+int sldqmc_features(sldqmc_ctx *ctx, const int8_t *cfgs, int n_cfg, int64_t *F);
+
+/* Training, step ii / Eq. 3: regress y = ln omega = log phi + log omega_F on
+ * [1, f_1..f_nc] by least squares in FP64; -beta H_eff = ln omega gives
+ * E0 = -a_0/beta, J_c = -a_c/beta.  R^2 = 1 - SS_res/SS_tot (the score of
+ * "Results").  cfgs: host n_cfg*M*N; logw: host n_cfg (if NULL, the library
+ * evaluates ln omega itself).  The fitted model becomes the context's
+ * effective model.  J: n_class doubles. */
+int sldqmc_fit_effective_action(sldqmc_ctx *ctx, const int8_t *cfgs, const double *logw, int n_cfg,
+                                double *J, double *E0, double *r2);
+
+/* Effective-model sweeps (step iii): n_sweeps colour-ordered single-spin
+ * Metropolis sweeps on H_eff (log acceptance 2 beta s sum_c J_c n_c), colour
+ * order forward (dir = 0) or reversed (dir = 1).  Uniforms: Philox key seed,
+ * counter (i, tau, step, 2 | sweep << 8).  Host s in place. */
+int sldqmc_eff_sweeps(sldqmc_ctx *ctx, int8_t *s, int n_sweeps, uint64_t seed, uint32_t step,
+                      int dir, long long *n_accept);
+
+/* Cumulative update (steps iii + iv, acceptance Eq. 4): proposes C' by
+ * n_eff effective sweeps from C (direction bit from Philox counter
+ * (0,0,step,3)), evaluates log omega(C') exactly (two flavours, FP64
+ * finalisation) and accepts iff log u < log r with
+ *   log r = [log omega(C') - log omega(C)] + beta sum_c J_c (f_c(C') - f_c(C)),
+ * u from counter (0,0,step,4).  logw: log omega(C), cached, in/out. */
+int sldqmc_cumulative_update(sldqmc_ctx *ctx, int8_t *s, double *logw, int n_eff, uint64_t seed,
+                             uint32_t step, int *accepted, double *log_r);
+
+/* n_steps cumulative updates for B chains on device buffers, stream-ordered
+ * and free of host synchronisation (capturable in a CUDA graph).  Chain b
+ * uses key seed + (b << 32) and steps step0 .. step0+n_steps-1.
+ * d_s: B*M*N, d_logw: B (in/out), d_accepts: B ints incremented per
+ * accepted step, d_log_r: B doubles (last step's log r; may be NULL). */
+int sldqmc_cumulative_batch_dev(sldqmc_ctx *ctx, int8_t *d_s, double *d_logw, int B, int n_eff,
+                                uint64_t seed, uint32_t step0, int n_steps, int *d_accepts,
+                                double *d_log_r);
+
+/* log omega = log phi + 2 ld(+1) + 2 ld(-1) for B configurations on device
+ * buffers (the exact weight a cumulative update needs). */
+int sldqmc_log_weight_batch_dev(sldqmc_ctx *ctx, const int8_t *d_s, int B, double *d_logw);
+
+/* Number of this library's kernels launched on the context since create. */
+long long sldqmc_kernel_launches(const sldqmc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLDQMC_H */

@@ -1,0 +1,102 @@
+// internal.h -- shared declarations of the sldqmc CUDA library (not part of
+// the public C ABI).  All kernels are written for sm_103a (GB300).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "sldqmc.h"
+
+namespace sldqmc {
+
+// Error bits raised by kernels into the context's device flag word.
+enum : int {
+    FLAG_NUMERICAL = 1,  // non-positive Cholesky pivot, zero LU pivot or non-finite value
+    FLAG_ARG = 2,        // field value outside {-1, +1}
+    FLAG_TIMEOUT = 4,    // a bounded device wait ran out
+};
+
+// Batched FP64 GEMM description: for each batch item b,
+//   C = alpha * op(A) * diag(kscale) * op(B) * diag(nscale) * diag(mscale) + beta * C
+// op(A) is M x K: A[m*lda + k] (TA = false) or A[k*lda + m] (TA = true).
+// op(B) is K x N: B[k*ldb + n] (TB = false) or B[n*ldb + k] (TB = true).
+// kscale/nscale/(s_m row scale) come from a field slice: value cu where s > 0, cd otherwise.
+// mscale is a double vector (or its reciprocal when ms_recip).
+// a_upper: A is upper triangular (op(A)[m][k] = 0 for k < m): skip those k.
+// c_upper: only tiles touching the upper triangle of C (n >= m) are written.
+struct GemmF64 {
+    int M, N, K;
+    const double *A;
+    long long lda, sA;
+    const double *B;
+    long long ldb, sB;
+    double *C;
+    long long ldc, sC;
+    double alpha, beta;
+    const int8_t *s_k;
+    long long sSk;
+    const int8_t *s_n;
+    long long sSn;
+    const int8_t *s_m;  // row scale of C from a field slice
+    long long sSm;
+    double cu, cd;
+    const double *ms;
+    long long sMs;
+    int ms_recip;
+    int a_upper;
+    int c_upper;
+    int batch;
+};
+
+void gemm_f64(const GemmF64 &g, bool TA, bool TB, cudaStream_t st);
+GemmF64 gemm_desc(int M, int N, int K, const double *A, long long lda, long long sA,
+                  const double *B, long long ldb, long long sB, double *C, long long ldc,
+                  long long sC, int batch);
+
+// Mixed-precision slice GEMM (tensor cores, tcgen05): C = A * E with the
+// same scale options as the FP64 GEMM's chain use.  Defined in tc_gemm.cu.
+struct ChainTC;
+
+}  // namespace sldqmc
+
+// The context (opaque in the public header).
+struct sldqmc_ctx {
+    sldqmc_params p;
+    int N, M;
+    cudaStream_t st;
+    long long launches;
+    int *d_flag;  // device error bits
+    // constants
+    double *d_K, *d_E, *d_Einv;  // N x N
+    float *d_Ehi, *d_Elo;        // split-TF32 copies of E (3xTF32 mode)
+    void *d_Ebf;                 // BF16 copy of E (BF16 mode)
+    double ex_scale[2][2];       // [eta==-1][s<0]: exp(eta*dtau*xi*s)
+    double dtauJ, Ktau;          // bare-weight constants
+    // stabilisation workspace, cap items each
+    int cap;
+    long long nn;      // N*N
+    double *buf[9];    // Ut, V, X1, X2, W(2*nn), Y, R1, R2, Vg
+    double *d_D, *d_Dp, *d_logacc;
+    int *d_perm, *d_sgn, *d_piv;
+    void *tc_ws;       // tensor-core operand workspace (split copies)
+    // Monte Carlo state
+    int8_t *d_s_tmp;   // cap * M * N proposal buffer
+    int8_t *d_s_one;   // staging for host calls
+    double *d_G[2];    // Gt for the local sweep: cap items per flavour
+    double *d_ld_tmp, *d_ld_tmp2;
+    int *d_sg_tmp;
+    long long *d_stats; // cap * 4 (accepted, proposed, margin, drift bits)
+    // effective model
+    int n_class, n_off_total;
+    int h_n_off[32];
+    int h_offsets[64 * 3];
+    double h_J[32];
+    double E0;
+    int have_model;
+    int n_colors;
+    int *d_col_start, *d_col_sites;
+    long long *d_feat0, *d_feat1;
+    double *d_Jdev;
+    int *d_offdev, *d_noffdev;
+};

@@ -1,0 +1,894 @@
+// sldqmc.cu -- context management and the C ABI of include/sldqmc.h.
+//
+// Everything numerical runs in this library's kernels on the context's
+// stream; the host side only validates arguments, sizes workspaces, orders
+// launches and copies inputs and results.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace sldqmc {
+// stab.cu
+void launch_init_udv(sldqmc_ctx *c, double *Ut, double *V, int B);
+void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B);
+void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign, double *d_G,
+              double scale, int accumulate);
+// mc.cu
+void launch_check_field(sldqmc_ctx *c, const int8_t *d_s, long long n);
+void launch_log_bare(sldqmc_ctx *c, const int8_t *d_s, int B, double *out, int accumulate);
+void launch_local_flips(sldqmc_ctx *c, double *Gp, double *Gm, int8_t *d_s, int B, int tau,
+                        uint32_t sweep, uint64_t seed, long long *stats);
+void launch_drift(sldqmc_ctx *c, const double *Gw, const double *Gf, int B2x, int B, long long *stats);
+int upload_effective_model(sldqmc_ctx *c);
+void launch_eff_sweeps(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t seed, uint32_t step,
+                       int dir, long long *n_accept, long long *n_margin);
+void launch_features(sldqmc_ctx *c, const int8_t *d_s, int B, long long *out);
+void launch_cumulative_accept(sldqmc_ctx *c, const double *lw1, double *lw0, const long long *f0,
+                              const long long *f1, uint64_t seed, uint32_t step, int B, int *accepted,
+                              int *accept_count, double *log_r, long long *margin);
+void launch_commit(sldqmc_ctx *c, int8_t *d_s, const int8_t *d_sp, const int *accepted, int B);
+void set_eff_smem_limits();
+void stab_set_limits(int Npad);
+// tc_gemm.cu
+void tc_convert_E(sldqmc_ctx *c);
+int tc_prepare(sldqmc_ctx *c);
+void tc_release(sldqmc_ctx *c);
+void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, double cu, double cd,
+                    const int *slices, int nb, double *Xt_out, double *scratch_a, double *scratch_b);
+}  // namespace sldqmc
+
+using namespace sldqmc;
+
+namespace {
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Ring propagator e^{c A_1} on a ring of length L by its Fourier sum
+// E1(d) = (1/L) sum_n exp(2c cos k_n) cos(k_n d), k_n = 2 pi n / L; L = 1
+// has no bond.  One thread per distance d.
+__global__ void k_ring(int L, double c, double *E1)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= L) return;
+    if (L == 1) { E1[0] = 1.0; return; }
+    double acc = 0.0;
+    for (int n = 0; n < L; ++n) {
+        const double k = 2.0 * M_PI * (double)n / (double)L;
+        acc += exp(2.0 * c * cos(k)) * cos(k * (double)d);
+    }
+    E1[d] = acc / (double)L;
+}
+
+// K = -t A - mu I and the separable exp(-+dtau K) = e^{+-dtau mu} Ex (x) Ey.
+__global__ void k_build_K(int Lx, int Ly, double t, double mu, double dtau, const double *ex_p,
+                          const double *ey_p, const double *ex_m, const double *ey_m, double *K,
+                          double *E, double *Einv)
+{
+    const int N = Lx * Ly;
+    const long long nn = (long long)N * N;
+    const double sp = exp(dtau * mu), sm = exp(-dtau * mu);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e % N);
+        const int xi = i % Lx, yi = i / Lx, xj = j % Lx, yj = j / Lx;
+        int dx = (xi - xj) % Lx; if (dx < 0) dx += Lx;
+        int dy = (yi - yj) % Ly; if (dy < 0) dy += Ly;
+        E[e] = sp * ex_p[dx] * ey_p[dy];
+        Einv[e] = sm * ex_m[dx] * ey_m[dy];
+        double k = (i == j) ? -mu : 0.0;
+        if (Lx > 1) {
+            int dxa = (xj - xi) % Lx; if (dxa < 0) dxa += Lx;
+            if (yi == yj) {
+                if (dxa == 1) k -= t;
+                if (dxa == Lx - 1) k -= t;
+            }
+        }
+        if (Ly > 1) {
+            int dya = (yj - yi) % Ly; if (dya < 0) dya += Ly;
+            if (xi == xj) {
+                if (dya == 1) k -= t;
+                if (dya == Ly - 1) k -= t;
+            }
+        }
+        K[e] = k;
+    }
+}
+
+int flag_to_status(int f)
+{
+    if (f & FLAG_ARG) return SLDQMC_ERR_ARG;
+    if (f & FLAG_TIMEOUT) return SLDQMC_ERR_TIMEOUT;
+    if (f & FLAG_NUMERICAL) return SLDQMC_ERR_NUMERICAL;
+    return SLDQMC_OK;
+}
+
+int sync_and_flag(sldqmc_ctx *c)
+{
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return SLDQMC_ERR_CUDA;
+    int f = 0;
+    if (cudaMemcpy(&f, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    if (f) cudaMemset(c->d_flag, 0, sizeof(int));
+    return flag_to_status(f);
+}
+
+template <typename T>
+int dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return SLDQMC_OK;
+    if (cudaMalloc((void **)p, sizeof(T) * count) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return SLDQMC_ERR_OOM;
+    }
+    return SLDQMC_OK;
+}
+
+bool host_field_ok(const int8_t *s, long long n)
+{
+    for (long long e = 0; e < n; ++e)
+        if (s[e] != 1 && s[e] != -1) return false;
+    return true;
+}
+
+// One batch of weight (or Green's function) evaluations on device data.
+// Slices are processed in the cyclic order tau0, tau0+1, ... (0-based),
+// i.e. the product B_tau0 .. B_1 B_M .. B_{tau0+1}.
+int weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, int tau0, double *d_ld, int *d_sign,
+               double *d_G, double scale, int accumulate)
+{
+    const int N = c->N, M = c->M;
+    const long long nn = c->nn;
+    const double cu = c->ex_scale[eta < 0][0], cd = c->ex_scale[eta < 0][1];
+    double *Ut = c->buf[0], *Yb = c->buf[5], *X1 = c->buf[2], *X2 = c->buf[3];
+    launch_init_udv(c, Ut, c->buf[1], B);
+    std::vector<int> slices;
+    for (int m = 0; m < M; m += c->p.n_wrap) {
+        const int nb = std::min(c->p.n_wrap, M - m);
+        double *Xt;
+        if (c->p.prec == SLDQMC_FP64) {
+            const double *cur = Ut;
+            double *outs[2] = {X1, X2};
+            int o = 0;
+            for (int j = 0; j < nb; ++j) {
+                const int slice = (tau0 + m + j) % M;
+                GemmF64 g = gemm_desc(N, N, N, cur, N, nn, c->d_E, N, 0, outs[o], N, nn, B);
+                g.cu = cu; g.cd = cd;
+                if (j == 0) { g.s_k = d_s + (long long)slice * N; g.sSk = (long long)M * N; }
+                if (j < nb - 1) { g.s_n = d_s + (long long)((tau0 + m + j + 1) % M) * N; g.sSn = (long long)M * N; }
+                gemm_f64(g, false, false, c->st);
+                c->launches++;
+                cur = outs[o];
+                o ^= 1;
+            }
+            Xt = const_cast<double *>(cur);
+        } else {
+            slices.assign(nb, 0);
+            for (int j = 0; j < nb; ++j) slices[j] = (tau0 + m + j) % M;
+            tc_chain_block(c, Ut, d_s, B, cu, cd, slices.data(), nb, X1, X2, Yb);
+            Xt = X1;
+        }
+        stabilize(c, Xt, Ut, Yb, B);
+        std::swap(Ut, Yb);
+    }
+    finalize(c, Ut, B, d_ld, d_sign, d_G, scale, accumulate);
+    return SLDQMC_OK;
+}
+
+// log omega = log phi + 2 ld(+1) + 2 ld(-1) into d_lw.
+int log_weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, double *d_lw)
+{
+    int rc = weight_run(c, d_s, B, 1, 0, d_lw, nullptr, nullptr, 2.0, 0);
+    if (rc) return rc;
+    rc = weight_run(c, d_s, B, -1, 0, d_lw, nullptr, nullptr, 2.0, 1);
+    if (rc) return rc;
+    launch_log_bare(c, d_s, B, d_lw, 1);
+    return SLDQMC_OK;
+}
+
+int ensure_local_buffers(sldqmc_ctx *c)
+{
+    if (c->d_G[0]) return SLDQMC_OK;
+    const size_t n = (size_t)c->cap * c->nn;
+    int rc = dalloc(&c->d_G[0], 6 * n);
+    if (rc) return rc;
+    c->d_G[1] = c->d_G[0] + n;
+    return SLDQMC_OK;
+}
+
+// Greedy colouring of the effective model's interaction graph: sites
+// v = tau*N + i in increasing order take the smallest colour not used by an
+// already coloured neighbour (v +- o for every offset o, self excluded).
+void build_colouring(sldqmc_ctx *c, std::vector<int> &start, std::vector<int> &sites)
+{
+    const int Lx = c->p.Lx, Ly = c->p.Ly, M = c->M, N = c->N, V = N * M;
+    std::vector<int> colour(V, -1);
+    std::vector<int> nbr;
+    int ncol = 0;
+    auto wrap = [](int a, int L) { a %= L; return a < 0 ? a + L : a; };
+    std::vector<char> used;
+    for (int v = 0; v < V; ++v) {
+        const int tau = v / N, i = v % N, x = i % Lx, y = i / Lx;
+        used.assign(ncol + 2, 0);
+        for (int q = 0; q < c->n_off_total; ++q) {
+            const int *o = c->h_offsets + 3 * q;
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const int w = wrap(tau + sg * o[2], M) * N + wrap(x + sg * o[0], Lx) + Lx * wrap(y + sg * o[1], Ly);
+                if (w != v && colour[w] >= 0) used[colour[w]] = 1;
+            }
+        }
+        int col = 0;
+        while (used[col]) ++col;
+        colour[v] = col;
+        ncol = std::max(ncol, col + 1);
+    }
+    start.assign(ncol + 1, 0);
+    for (int v = 0; v < V; ++v) start[colour[v] + 1]++;
+    for (int k = 0; k < ncol; ++k) start[k + 1] += start[k];
+    sites.assign(V, 0);
+    std::vector<int> pos(start.begin(), start.end() - 1);
+    for (int v = 0; v < V; ++v) sites[pos[colour[v]]++] = v;
+}
+
+// Least squares min |A x - y| for a tall n x p matrix (column-major
+// work copy) by modified Gram-Schmidt applied twice (reorthogonalised),
+// then back substitution.  Host FP64; p is at most 33.
+int lstsq_mgs2(int n, int p, const std::vector<double> &A_rowmajor, const std::vector<double> &y,
+               std::vector<double> &x)
+{
+    std::vector<double> Q((size_t)n * p), R((size_t)p * p, 0.0);
+    for (int r = 0; r < n; ++r)
+        for (int k = 0; k < p; ++k) Q[(size_t)k * n + r] = A_rowmajor[(size_t)r * p + k];
+    for (int k = 0; k < p; ++k) {
+        double *qk = &Q[(size_t)k * n];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int j = 0; j < k; ++j) {
+                const double *qj = &Q[(size_t)j * n];
+                double d = 0.0;
+                for (int r = 0; r < n; ++r) d += qj[r] * qk[r];
+                R[(size_t)j * p + k] += d;
+                for (int r = 0; r < n; ++r) qk[r] -= d * qj[r];
+            }
+        double nrm = 0.0;
+        for (int r = 0; r < n; ++r) nrm += qk[r] * qk[r];
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0)) return SLDQMC_ERR_NUMERICAL;
+        R[(size_t)k * p + k] = nrm;
+        for (int r = 0; r < n; ++r) qk[r] /= nrm;
+    }
+    std::vector<double> qty(p, 0.0);
+    std::vector<double> res(y);
+    for (int k = 0; k < p; ++k) {
+        const double *qk = &Q[(size_t)k * n];
+        double d = 0.0;
+        for (int r = 0; r < n; ++r) d += qk[r] * res[r];
+        qty[k] = d;
+        for (int r = 0; r < n; ++r) res[r] -= d * qk[r];
+    }
+    x.assign(p, 0.0);
+    for (int k = p - 1; k >= 0; --k) {
+        double acc = qty[k];
+        for (int j = k + 1; j < p; ++j) acc -= R[(size_t)k * p + j] * x[j];
+        x[k] = acc / R[(size_t)k * p + k];
+    }
+    return SLDQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sldqmc_strerror(int status)
+{
+    switch (status) {
+    case SLDQMC_OK: return "ok";
+    case SLDQMC_ERR_ARG: return "invalid argument";
+    case SLDQMC_ERR_OOM: return "device out of memory";
+    case SLDQMC_ERR_CUDA: return "CUDA runtime error";
+    case SLDQMC_ERR_NUMERICAL: return "numerical failure (non-positive pivot or non-finite value)";
+    case SLDQMC_ERR_TIMEOUT: return "device wait timed out";
+    case SLDQMC_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+long long sldqmc_kernel_launches(const sldqmc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int sldqmc_dims(const sldqmc_ctx *ctx, int *N, int *M)
+{
+    if (!ctx) return SLDQMC_ERR_ARG;
+    if (N) *N = ctx->N;
+    if (M) *M = ctx->M;
+    return SLDQMC_OK;
+}
+
+int sldqmc_sync(sldqmc_ctx *ctx)
+{
+    if (!ctx) return SLDQMC_ERR_ARG;
+    return sync_and_flag(ctx);
+}
+
+void sldqmc_destroy(sldqmc_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    tc_release(c);
+    cudaFree(c->d_flag);
+    cudaFree(c->d_K);
+    cudaFree(c->buf[0]);
+    cudaFree(c->d_D);
+    cudaFree(c->d_perm);
+    cudaFree(c->d_s_tmp);
+    cudaFree(c->d_G[0]);
+    cudaFree(c->d_ld_tmp);
+    cudaFree(c->d_stats);
+    cudaFree(c->d_col_start);
+    cudaFree(c->d_col_sites);
+    cudaFree(c->d_feat0);
+    free(c);
+}
+
+int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
+{
+    if (!p || !out) return SLDQMC_ERR_ARG;
+    *out = nullptr;
+    if (p->Lx < 1 || p->Ly < 1 || p->n_wrap < 1 || p->max_batch < 1 || !(p->dtau > 0.0) ||
+        !(p->beta > 0.0) || p->prec < 0 || p->prec > 2 || !isfinite(p->t) || !isfinite(p->mu) ||
+        !isfinite(p->xi) || !isfinite(p->J_ising) || !(p->h > 0.0))
+        return SLDQMC_ERR_ARG;
+    const long long N = (long long)p->Lx * p->Ly;
+    const long long M = llround(p->beta / p->dtau);
+    if (M < 1 || fabs((double)M * p->dtau - p->beta) > 1e-12 * p->beta) return SLDQMC_ERR_ARG;
+    if (N > 16384 || M > 100000) return SLDQMC_ERR_UNSUPPORTED;
+    // Cholesky-QR of one block needs kappa(X)^2 eps << 1; kappa(X) is
+    // bounded by exp(n_wrap dtau (8|t| + 2|xi|)).
+    const double logk = (double)std::min<long long>(p->n_wrap, M) * p->dtau * (8.0 * fabs(p->t) + 2.0 * fabs(p->xi));
+    if (logk > 14.0) return SLDQMC_ERR_UNSUPPORTED;
+
+    sldqmc_ctx *c = (sldqmc_ctx *)calloc(1, sizeof(sldqmc_ctx));
+    if (!c) return SLDQMC_ERR_OOM;
+    c->p = *p;
+    c->N = (int)N;
+    c->M = (int)M;
+    c->p.beta = (double)M * p->dtau;
+    c->st = (cudaStream_t)stream;
+    c->cap = p->max_batch;
+    c->nn = N * N;
+    for (int e = 0; e < 2; ++e) {
+        const double eta = e == 0 ? 1.0 : -1.0;
+        c->ex_scale[e][0] = exp(eta * p->dtau * p->xi);
+        c->ex_scale[e][1] = exp(-eta * p->dtau * p->xi);
+    }
+    c->dtauJ = p->dtau * p->J_ising;
+    c->Ktau = -0.5 * log(tanh(p->dtau * p->h));
+    int rc = SLDQMC_OK;
+    const size_t nn = (size_t)c->nn, cap = (size_t)c->cap;
+    if ((rc = dalloc(&c->d_flag, 1))) goto fail;
+    cudaMemset(c->d_flag, 0, sizeof(int));
+    if ((rc = dalloc(&c->d_K, 3 * nn + 4 * (size_t)(p->Lx + p->Ly)))) goto fail;
+    c->d_E = c->d_K + nn;
+    c->d_Einv = c->d_E + nn;
+    // 9 workspaces; W (index 4) is twice the size for the LU with a
+    // right-hand side.
+    if ((rc = dalloc(&c->buf[0], 10 * nn * cap))) goto fail;
+    {
+        double *q = c->buf[0];
+        for (int k = 0; k < 9; ++k) {
+            c->buf[k] = q;
+            q += (k == 4 ? 2 : 1) * nn * cap;
+        }
+    }
+    if ((rc = dalloc(&c->d_D, 2 * N * cap + cap + 4 * cap))) goto fail;
+    c->d_Dp = c->d_D + N * cap;
+    c->d_logacc = c->d_Dp + N * cap;
+    c->d_ld_tmp = nullptr;
+    if ((rc = dalloc(&c->d_perm, 2 * N * cap + 2 * cap + 2 * cap))) goto fail;
+    c->d_piv = c->d_perm + N * cap;
+    c->d_sgn = c->d_piv + N * cap;
+    c->d_sg_tmp = c->d_sgn + 2 * cap;
+    if ((rc = dalloc(&c->d_s_tmp, 2 * (size_t)M * N * cap))) goto fail;
+    c->d_s_one = c->d_s_tmp + (size_t)M * N * cap;
+    if ((rc = dalloc(&c->d_ld_tmp, 4 * cap))) goto fail;
+    c->d_ld_tmp2 = c->d_ld_tmp + cap;
+    if ((rc = dalloc(&c->d_stats, 4 * cap + 8 * cap))) goto fail;
+    if (p->prec != SLDQMC_FP64 && (rc = tc_prepare(c))) goto fail;
+    {
+        // build K, E, E^{-1}
+        double *ex_p = c->d_Einv + nn, *ey_p = ex_p + p->Lx, *ex_m = ey_p + p->Ly, *ey_m = ex_m + p->Lx;
+        k_ring<<<cdiv(p->Lx, 128), 128, 0, c->st>>>(p->Lx, p->dtau * p->t, ex_p);
+        k_ring<<<cdiv(p->Ly, 128), 128, 0, c->st>>>(p->Ly, p->dtau * p->t, ey_p);
+        k_ring<<<cdiv(p->Lx, 128), 128, 0, c->st>>>(p->Lx, -p->dtau * p->t, ex_m);
+        k_ring<<<cdiv(p->Ly, 128), 128, 0, c->st>>>(p->Ly, -p->dtau * p->t, ey_m);
+        int g = cdiv((long long)nn, 256);
+        if (g > 4096) g = 4096;
+        k_build_K<<<g, 256, 0, c->st>>>(p->Lx, p->Ly, p->t, p->mu, p->dtau, ex_p, ey_p, ex_m, ey_m, c->d_K,
+                                        c->d_E, c->d_Einv);
+        c->launches += 5;
+    }
+    if (p->prec != SLDQMC_FP64) tc_convert_E(c);
+    set_eff_smem_limits();
+    {
+        int Npad = 1;
+        while (Npad < N) Npad <<= 1;
+        stab_set_limits(Npad);
+    }
+    rc = sync_and_flag(c);
+    if (rc) goto fail;
+    *out = c;
+    return SLDQMC_OK;
+fail:
+    sldqmc_destroy(c);
+    return rc;
+}
+
+int sldqmc_build_K(sldqmc_ctx *c, double *K, double *expmK, double *exppK)
+{
+    if (!c) return SLDQMC_ERR_ARG;
+    const size_t bytes = sizeof(double) * (size_t)c->nn;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    if (K && cudaMemcpy(K, c->d_K, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    if (expmK && cudaMemcpy(expmK, c->d_E, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    if (exppK && cudaMemcpy(exppK, c->d_Einv, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    return SLDQMC_OK;
+}
+
+int sldqmc_weight_batch_dev(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, double *d_ld, int *d_sign)
+{
+    if (!c || B < 0 || (B > 0 && (!d_s || !d_ld)) || (eta != 1 && eta != -1)) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    launch_check_field(c, d_s, V * B);
+    for (int b0 = 0; b0 < B; b0 += c->cap) {
+        const int nb = std::min(c->cap, B - b0);
+        int rc = weight_run(c, d_s + V * b0, nb, eta, 0, d_ld + b0, d_sign ? d_sign + b0 : nullptr, nullptr,
+                            1.0, 0);
+        if (rc) return rc;
+    }
+    return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
+}
+
+int sldqmc_log_weight_batch_dev(sldqmc_ctx *c, const int8_t *d_s, int B, double *d_lw)
+{
+    if (!c || B < 0 || (B > 0 && (!d_s || !d_lw))) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    launch_check_field(c, d_s, V * B);
+    for (int b0 = 0; b0 < B; b0 += c->cap) {
+        const int nb = std::min(c->cap, B - b0);
+        int rc = log_weight_run(c, d_s + V * b0, nb, d_lw + b0);
+        if (rc) return rc;
+    }
+    return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
+}
+
+int sldqmc_weight_batch(sldqmc_ctx *c, const int8_t *s, int B, int eta, double *ld, int *sign)
+{
+    if (!c || B < 0 || (B > 0 && (!s || !ld)) || eta < -1 || eta > 1) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    if (!host_field_ok(s, V * B)) return SLDQMC_ERR_ARG;
+    std::vector<double> hld(B);
+    std::vector<int> hsg(B, 1);
+    for (int b0 = 0; b0 < B; b0 += c->cap) {
+        const int nb = std::min(c->cap, B - b0);
+        if (cudaMemcpyAsync(c->d_s_one, s + V * b0, (size_t)(V * nb), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+            return SLDQMC_ERR_CUDA;
+        int rc;
+        if (eta == 0) {
+            rc = weight_run(c, c->d_s_one, nb, 1, 0, c->d_ld_tmp, nullptr, nullptr, 2.0, 0);
+            if (!rc) rc = weight_run(c, c->d_s_one, nb, -1, 0, c->d_ld_tmp, nullptr, nullptr, 2.0, 1);
+        } else {
+            rc = weight_run(c, c->d_s_one, nb, eta, 0, c->d_ld_tmp, c->d_sg_tmp, nullptr, 1.0, 0);
+        }
+        if (rc) return rc;
+        if (cudaMemcpyAsync(hld.data() + b0, c->d_ld_tmp, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st) !=
+            cudaSuccess)
+            return SLDQMC_ERR_CUDA;
+        if (eta != 0 && cudaMemcpyAsync(hsg.data() + b0, c->d_sg_tmp, sizeof(int) * nb, cudaMemcpyDeviceToHost,
+                                        c->st) != cudaSuccess)
+            return SLDQMC_ERR_CUDA;
+        rc = sync_and_flag(c);
+        if (rc) return rc;
+    }
+    memcpy(ld, hld.data(), sizeof(double) * B);
+    if (sign) memcpy(sign, hsg.data(), sizeof(int) * B);
+    return SLDQMC_OK;
+}
+
+int sldqmc_weight(sldqmc_ctx *c, const int8_t *s, int eta, double *logabsdet, int *sign)
+{
+    return sldqmc_weight_batch(c, s, 1, eta, logabsdet, sign);
+}
+
+int sldqmc_green_batch_dev(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, int tau, double *d_G,
+                           double *d_ld, int *d_sign)
+{
+    if (!c || B < 0 || (eta != 1 && eta != -1) || tau < 0 || tau > c->M || (B > 0 && (!d_s || !d_G)))
+        return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    launch_check_field(c, d_s, V * B);
+    for (int b0 = 0; b0 < B; b0 += c->cap) {
+        const int nb = std::min(c->cap, B - b0);
+        int rc = weight_run(c, d_s + V * b0, nb, eta, tau % c->M, d_ld ? d_ld + b0 : c->d_ld_tmp,
+                            d_sign ? d_sign + b0 : nullptr, d_G + (long long)b0 * c->nn, 1.0, 0);
+        if (rc) return rc;
+    }
+    return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
+}
+
+int sldqmc_green(sldqmc_ctx *c, const int8_t *s, int eta, int tau, double *G, double *logabsdet, int *sign)
+{
+    if (!c || !s || !G || (eta != 1 && eta != -1) || tau < 0 || tau > c->M) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    if (!host_field_ok(s, V)) return SLDQMC_ERR_ARG;
+    double *dG = c->buf[2];  // reuse a workspace slot not used by the finalisation's output copy
+    // the chain uses buf[2] as scratch, so copy G out through the d_G staging of the local path
+    int rc = ensure_local_buffers(c);
+    if (rc) return rc;
+    dG = c->d_G[0] + 2 * (size_t)c->cap * c->nn;
+    if (cudaMemcpyAsync(c->d_s_one, s, (size_t)V, cudaMemcpyHostToDevice, c->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    rc = weight_run(c, c->d_s_one, 1, eta, tau % c->M, c->d_ld_tmp, c->d_sg_tmp, dG, 1.0, 0);
+    if (rc) return rc;
+    double ld;
+    int sg;
+    if (cudaMemcpyAsync(G, dG, sizeof(double) * c->nn, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(&ld, c->d_ld_tmp, sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(&sg, c->d_sg_tmp, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        return SLDQMC_ERR_CUDA;
+    rc = sync_and_flag(c);
+    if (rc) return rc;
+    if (logabsdet) *logabsdet = ld;
+    if (sign) *sign = sg;
+    return SLDQMC_OK;
+}
+
+int sldqmc_log_bare_weight(sldqmc_ctx *c, const int8_t *s, double *log_phi)
+{
+    if (!c || !s || !log_phi) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    if (!host_field_ok(s, V)) return SLDQMC_ERR_ARG;
+    if (cudaMemcpyAsync(c->d_s_one, s, (size_t)V, cudaMemcpyHostToDevice, c->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    launch_log_bare(c, c->d_s_one, 1, c->d_ld_tmp, 0);
+    double v;
+    if (cudaMemcpyAsync(&v, c->d_ld_tmp, sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        return SLDQMC_ERR_CUDA;
+    int rc = sync_and_flag(c);
+    if (rc) return rc;
+    *log_phi = v;
+    return SLDQMC_OK;
+}
+
+// Fresh Gt_f = E^{-1} G(tau1) E for both flavours into dst[f] (B items).
+static int fresh_gt(sldqmc_ctx *c, const int8_t *d_s, int B, int tau1, double *dstp, double *dstm)
+{
+    const int N = c->N;
+    const long long nn = c->nn;
+    double *Gt = c->d_G[0] + 2 * (size_t)c->cap * nn;  // G(tau1) staging
+    double *T = Gt + (size_t)c->cap * nn;
+    double *dst[2] = {dstp, dstm};
+    for (int f = 0; f < 2; ++f) {
+        int rc = weight_run(c, d_s, B, f == 0 ? 1 : -1, tau1 % c->M, c->d_ld_tmp2, nullptr, Gt, 1.0, 0);
+        if (rc) return rc;
+        GemmF64 g = gemm_desc(N, N, N, c->d_Einv, N, 0, Gt, N, nn, T, N, nn, B);
+        gemm_f64(g, false, false, c->st);
+        GemmF64 h = gemm_desc(N, N, N, T, N, nn, c->d_E, N, 0, dst[f], N, nn, B);
+        gemm_f64(h, false, false, c->st);
+        c->launches += 2;
+    }
+    return SLDQMC_OK;
+}
+
+// Gt <- D_tau E Gt E^{-1} D_tau^{-1} for both flavours, result into dst.
+static void wrap_gt(sldqmc_ctx *c, const int8_t *d_s, int B, int tau, double *srcp, double *srcm,
+                    double *dstp, double *dstm)
+{
+    const int N = c->N, M = c->M;
+    const long long nn = c->nn;
+    double *T = c->d_G[0] + 3 * (size_t)c->cap * nn;
+    double *src[2] = {srcp, srcm}, *dst[2] = {dstp, dstm};
+    for (int f = 0; f < 2; ++f) {
+        const double cu = c->ex_scale[f][0], cd = c->ex_scale[f][1];
+        GemmF64 g = gemm_desc(N, N, N, src[f], N, nn, c->d_Einv, N, 0, T, N, nn, B);
+        g.s_n = d_s + (long long)tau * N; g.sSn = (long long)M * N;
+        g.cu = 1.0 / cu; g.cd = 1.0 / cd;
+        gemm_f64(g, false, false, c->st);
+        GemmF64 h = gemm_desc(N, N, N, c->d_E, N, 0, T, N, nn, dst[f], N, nn, B);
+        h.s_m = d_s + (long long)tau * N; h.sSm = (long long)M * N;
+        h.cu = cu; h.cd = cd;
+        gemm_f64(h, false, false, c->st);
+        c->launches += 2;
+    }
+}
+
+int sldqmc_local_sweep_batch_dev(sldqmc_ctx *c, int8_t *d_s, int B, uint64_t seed, uint64_t sweep0,
+                                 int n_sweeps, sldqmc_stats *stats)
+{
+    if (!c || B < 1 || B > c->cap || !d_s || n_sweeps < 0) return SLDQMC_ERR_ARG;
+    // the flip kernel stages a column and a row of both Green's functions
+    // in shared memory: 4N doubles within the 200 KB opt-in limit
+    if (c->N > 6400) return SLDQMC_ERR_UNSUPPORTED;
+    int rc = ensure_local_buffers(c);
+    if (rc) return rc;
+    const long long V = (long long)c->N * c->M;
+    launch_check_field(c, d_s, V * B);
+    const long long nn = c->nn;
+    cudaMemsetAsync(c->d_stats, 0, sizeof(long long) * 4 * B, c->st);
+    double *Gp = c->d_G[0], *Gm = c->d_G[1];
+    // wrapped copies live in areas 4 and 5 of the local-update buffer
+    double *Wp = c->d_G[0] + 4 * (size_t)c->cap * nn, *Wm = Wp + (size_t)c->cap * nn;
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        const uint32_t sweep_id = (uint32_t)(sweep0 + (uint64_t)sw);
+        for (int tau = 0; tau < c->M; ++tau) {
+            if (tau == 0) {
+                rc = fresh_gt(c, d_s, B, tau + 1, Gp, Gm);
+                if (rc) return rc;
+            } else if (tau % c->p.n_wrap == 0) {
+                wrap_gt(c, d_s, B, tau, Gp, Gm, Wp, Wm);
+                rc = fresh_gt(c, d_s, B, tau + 1, Gp, Gm);
+                if (rc) return rc;
+                launch_drift(c, Wp, Gp, B, B, c->d_stats);
+                launch_drift(c, Wm, Gm, B, B, c->d_stats);
+            } else {
+                wrap_gt(c, d_s, B, tau, Gp, Gm, Wp, Wm);
+                std::swap(Gp, Wp);
+                std::swap(Gm, Wm);
+            }
+            launch_local_flips(c, Gp, Gm, d_s, B, tau, sweep_id, seed, c->d_stats);
+        }
+    }
+    if (stats) {
+        std::vector<long long> h(4 * (size_t)B);
+        if (cudaMemcpyAsync(h.data(), c->d_stats, sizeof(long long) * 4 * B, cudaMemcpyDeviceToHost, c->st) !=
+            cudaSuccess)
+            return SLDQMC_ERR_CUDA;
+        rc = sync_and_flag(c);
+        if (rc) return rc;
+        for (int b = 0; b < B; ++b) {
+            stats[b].accepted = h[4 * b];
+            stats[b].proposed = h[4 * b + 1];
+            stats[b].margin_events = h[4 * b + 2];
+            double d;
+            memcpy(&d, &h[4 * b + 3], sizeof(double));
+            stats[b].max_drift = d;
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
+}
+
+int sldqmc_local_sweep(sldqmc_ctx *c, int8_t *s, uint64_t seed, uint64_t sweep0, int n_sweeps, sldqmc_stats *stats)
+{
+    if (!c || !s || n_sweeps < 0) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    if (!host_field_ok(s, V)) return SLDQMC_ERR_ARG;
+    if (cudaMemcpyAsync(c->d_s_one, s, (size_t)V, cudaMemcpyHostToDevice, c->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    sldqmc_stats st;
+    int rc = sldqmc_local_sweep_batch_dev(c, c->d_s_one, 1, seed, sweep0, n_sweeps, &st);
+    if (rc) return rc;
+    std::vector<int8_t> tmp(V);
+    if (cudaMemcpyAsync(tmp.data(), c->d_s_one, (size_t)V, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        return SLDQMC_ERR_CUDA;
+    rc = sync_and_flag(c);
+    if (rc) return rc;
+    memcpy(s, tmp.data(), (size_t)V);
+    if (stats) *stats = st;
+    return SLDQMC_OK;
+}
+
+int sldqmc_set_effective_model(sldqmc_ctx *c, int n_class, const int *n_off, const int *offsets,
+                               const double *J, double E0)
+{
+    if (!c || n_class < 1 || n_class > 32 || !n_off || !offsets || !J) return SLDQMC_ERR_ARG;
+    int tot = 0;
+    for (int k = 0; k < n_class; ++k) {
+        if (n_off[k] < 1) return SLDQMC_ERR_ARG;
+        tot += n_off[k];
+    }
+    if (tot > 64) return SLDQMC_ERR_ARG;
+    for (int k = 0; k < n_class; ++k)
+        if (!isfinite(J[k])) return SLDQMC_ERR_ARG;
+    c->n_class = n_class;
+    c->n_off_total = tot;
+    memset(c->h_n_off, 0, sizeof(c->h_n_off));
+    memset(c->h_offsets, 0, sizeof(c->h_offsets));
+    memset(c->h_J, 0, sizeof(c->h_J));
+    memcpy(c->h_n_off, n_off, sizeof(int) * n_class);
+    memcpy(c->h_offsets, offsets, sizeof(int) * 3 * tot);
+    memcpy(c->h_J, J, sizeof(double) * n_class);
+    c->E0 = E0;
+    std::vector<int> start, sites;
+    build_colouring(c, start, sites);
+    c->n_colors = (int)start.size() - 1;
+    cudaFree(c->d_col_start);
+    cudaFree(c->d_col_sites);
+    c->d_col_start = nullptr;
+    c->d_col_sites = nullptr;
+    int rc = dalloc(&c->d_col_start, start.size());
+    if (!rc) rc = dalloc(&c->d_col_sites, sites.size());
+    if (rc) return rc;
+    if (cudaMemcpy(c->d_col_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_col_sites, sites.data(), sizeof(int) * sites.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SLDQMC_ERR_CUDA;
+    if (!c->d_feat0) {
+        rc = dalloc(&c->d_feat0, 2 * 32 * (size_t)c->cap);
+        if (rc) return rc;
+        c->d_feat1 = c->d_feat0 + 32 * (size_t)c->cap;
+    }
+    rc = upload_effective_model(c);
+    if (rc) return rc;
+    c->have_model = 1;
+    return sync_and_flag(c);
+}
+
+int sldqmc_features(sldqmc_ctx *c, const int8_t *cfgs, int n_cfg, int64_t *F)
+{
+    if (!c || !c->have_model || n_cfg < 0 || (n_cfg > 0 && (!cfgs || !F))) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    if (!host_field_ok(cfgs, V * n_cfg)) return SLDQMC_ERR_ARG;
+    for (int b0 = 0; b0 < n_cfg; b0 += c->cap) {
+        const int nb = std::min(c->cap, n_cfg - b0);
+        if (cudaMemcpyAsync(c->d_s_one, cfgs + V * b0, (size_t)(V * nb), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+            return SLDQMC_ERR_CUDA;
+        launch_features(c, c->d_s_one, nb, c->d_feat0);
+        if (cudaMemcpyAsync(F + (size_t)b0 * c->n_class, c->d_feat0, sizeof(long long) * nb * c->n_class,
+                            cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+            return SLDQMC_ERR_CUDA;
+        int rc = sync_and_flag(c);
+        if (rc) return rc;
+    }
+    return SLDQMC_OK;
+}
+
+int sldqmc_fit_effective_action(sldqmc_ctx *c, const int8_t *cfgs, const double *logw, int n_cfg, double *J,
+                                double *E0, double *r2)
+{
+    if (!c || !c->have_model || !cfgs || !J || n_cfg < c->n_class + 1) return SLDQMC_ERR_ARG;
+    const int nc = c->n_class, p = nc + 1;
+    std::vector<int64_t> F((size_t)n_cfg * nc);
+    int rc = sldqmc_features(c, cfgs, n_cfg, F.data());
+    if (rc) return rc;
+    std::vector<double> y(n_cfg);
+    if (logw) {
+        memcpy(y.data(), logw, sizeof(double) * n_cfg);
+    } else {
+        const long long V = (long long)c->N * c->M;
+        for (int b0 = 0; b0 < n_cfg; b0 += c->cap) {
+            const int nb = std::min(c->cap, n_cfg - b0);
+            if (cudaMemcpyAsync(c->d_s_one, cfgs + V * b0, (size_t)(V * nb), cudaMemcpyHostToDevice, c->st) !=
+                cudaSuccess)
+                return SLDQMC_ERR_CUDA;
+            rc = log_weight_run(c, c->d_s_one, nb, c->d_ld_tmp);
+            if (rc) return rc;
+            if (cudaMemcpyAsync(y.data() + b0, c->d_ld_tmp, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st) !=
+                cudaSuccess)
+                return SLDQMC_ERR_CUDA;
+            rc = sync_and_flag(c);
+            if (rc) return rc;
+        }
+    }
+    // centre and scale the feature columns for conditioning, solve, map back
+    std::vector<double> mean(nc, 0.0), sc(nc, 0.0);
+    for (int r = 0; r < n_cfg; ++r)
+        for (int k = 0; k < nc; ++k) mean[k] += (double)F[(size_t)r * nc + k];
+    for (int k = 0; k < nc; ++k) mean[k] /= n_cfg;
+    for (int r = 0; r < n_cfg; ++r)
+        for (int k = 0; k < nc; ++k) {
+            double d = (double)F[(size_t)r * nc + k] - mean[k];
+            sc[k] += d * d;
+        }
+    for (int k = 0; k < nc; ++k) sc[k] = sc[k] > 0.0 ? sqrt(sc[k]) : 1.0;
+    std::vector<double> A((size_t)n_cfg * p);
+    for (int r = 0; r < n_cfg; ++r) {
+        A[(size_t)r * p] = 1.0;
+        for (int k = 0; k < nc; ++k) A[(size_t)r * p + 1 + k] = ((double)F[(size_t)r * nc + k] - mean[k]) / sc[k];
+    }
+    std::vector<double> x;
+    rc = lstsq_mgs2(n_cfg, p, A, y, x);
+    if (rc) return rc;
+    std::vector<double> coef(p);
+    double a0 = x[0];
+    for (int k = 0; k < nc; ++k) {
+        coef[1 + k] = x[1 + k] / sc[k];
+        a0 -= coef[1 + k] * mean[k];
+    }
+    coef[0] = a0;
+    double ym = 0.0;
+    for (int r = 0; r < n_cfg; ++r) ym += y[r];
+    ym /= n_cfg;
+    double ssr = 0.0, sst = 0.0;
+    for (int r = 0; r < n_cfg; ++r) {
+        double yh = coef[0];
+        for (int k = 0; k < nc; ++k) yh += coef[1 + k] * (double)F[(size_t)r * nc + k];
+        ssr += (y[r] - yh) * (y[r] - yh);
+        sst += (y[r] - ym) * (y[r] - ym);
+    }
+    const double beta = c->p.beta;
+    for (int k = 0; k < nc; ++k) J[k] = -coef[1 + k] / beta;
+    const double e0 = -coef[0] / beta;
+    if (E0) *E0 = e0;
+    if (r2) *r2 = sst > 0.0 ? 1.0 - ssr / sst : 1.0;
+    return sldqmc_set_effective_model(c, nc, c->h_n_off, c->h_offsets, J, e0);
+}
+
+int sldqmc_eff_sweeps(sldqmc_ctx *c, int8_t *s, int n_sweeps, uint64_t seed, uint32_t step, int dir,
+                      long long *n_accept)
+{
+    if (!c || !c->have_model || !s || n_sweeps < 0 || (dir != 0 && dir != 1)) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    if (!host_field_ok(s, V)) return SLDQMC_ERR_ARG;
+    if (cudaMemcpyAsync(c->d_s_one, s, (size_t)V, cudaMemcpyHostToDevice, c->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    long long *cnt = c->d_stats + 4 * (size_t)c->cap;
+    cudaMemsetAsync(cnt, 0, sizeof(long long) * 2, c->st);
+    launch_eff_sweeps(c, c->d_s_one, 1, n_sweeps, seed, step, dir, cnt, cnt + 1);
+    std::vector<int8_t> tmp(V);
+    long long h[2];
+    if (cudaMemcpyAsync(tmp.data(), c->d_s_one, (size_t)V, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        return SLDQMC_ERR_CUDA;
+    int rc = sync_and_flag(c);
+    if (rc) return rc;
+    memcpy(s, tmp.data(), (size_t)V);
+    if (n_accept) *n_accept = h[0];
+    return SLDQMC_OK;
+}
+
+int sldqmc_cumulative_batch_dev(sldqmc_ctx *c, int8_t *d_s, double *d_logw, int B, int n_eff, uint64_t seed,
+                                uint32_t step0, int n_steps, int *d_accepts, double *d_log_r)
+{
+    if (!c || !c->have_model || B < 1 || B > c->cap || !d_s || !d_logw || n_eff < 0 || n_steps < 0)
+        return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    launch_check_field(c, d_s, V * B);
+    int8_t *sp = c->d_s_tmp;
+    int *accepted = c->d_sg_tmp;  // B ints of scratch (2*cap available)
+    for (int k = 0; k < n_steps; ++k) {
+        const uint32_t step = step0 + (uint32_t)k;
+        cudaMemcpyAsync(sp, d_s, (size_t)(V * B), cudaMemcpyDeviceToDevice, c->st);
+        launch_eff_sweeps(c, sp, B, n_eff, seed, step, -1, nullptr, nullptr);
+        launch_features(c, d_s, B, c->d_feat0);
+        launch_features(c, sp, B, c->d_feat1);
+        int rc = log_weight_run(c, sp, B, c->d_ld_tmp);
+        if (rc) return rc;
+        launch_cumulative_accept(c, c->d_ld_tmp, d_logw, c->d_feat0, c->d_feat1, seed, step, B, accepted,
+                                 d_accepts, d_log_r, nullptr);
+        launch_commit(c, d_s, sp, accepted, B);
+    }
+    return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
+}
+
+int sldqmc_cumulative_update(sldqmc_ctx *c, int8_t *s, double *logw, int n_eff, uint64_t seed, uint32_t step,
+                             int *accepted, double *log_r)
+{
+    if (!c || !c->have_model || !s || !logw || n_eff < 0) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    if (!host_field_ok(s, V)) return SLDQMC_ERR_ARG;
+    int8_t *ds = c->d_s_one;
+    double *dl = c->d_ld_tmp2;
+    int *dacc = c->d_sg_tmp + c->cap;
+    double *dlr = c->d_ld_tmp2 + 1;
+    if (cudaMemcpyAsync(ds, s, (size_t)V, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(dl, logw, sizeof(double), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+        return SLDQMC_ERR_CUDA;
+    cudaMemsetAsync(dacc, 0, sizeof(int), c->st);
+    int rc = sldqmc_cumulative_batch_dev(c, ds, dl, 1, n_eff, seed, step, 1, dacc, dlr);
+    if (rc) return rc;
+    std::vector<int8_t> tmp(V);
+    double hl[2];
+    int ha;
+    if (cudaMemcpyAsync(tmp.data(), ds, (size_t)V, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(hl, dl, sizeof(hl), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(&ha, dacc, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        return SLDQMC_ERR_CUDA;
+    rc = sync_and_flag(c);
+    if (rc) return rc;
+    memcpy(s, tmp.data(), (size_t)V);
+    *logw = hl[0];
+    if (accepted) *accepted = ha;
+    if (log_r) *log_r = hl[1];
+    return SLDQMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,555 @@
+// stab.cu -- FP64 kernels of the stabilised determinant: pre-pivoted
+// Cholesky-QR re-factorisation of the running U D V product, and the
+// blocked LU finalisation det(1 + U D V) = det(U) det(D_b) det(M_mid).
+//
+// The paper uses the numerically stable B-chain evaluation of DQMC (the
+// scheme of Loh et al. it cites in "Basics of DQMC") without spelling it
+// out.  On GB300 the stabilisation is FP64 work on a ~1.1 TFLOP/s pipe, so
+// it is arranged as GEMM-shaped batched work with small panel kernels:
+//
+//   X = B_block .. U  (the block's slice products),
+//   sort the columns of X diag(D) by norm (pre-pivoting, permutation P),
+//   X P = Q R by Cholesky-QR applied twice (Gram matrix, Cholesky, a
+//   triangular solve; the second pass restores orthogonality to O(eps)),
+//   U <- Q,  D <- |diag R| * D_P,  V <- D^{-1} R D_P P^T V.
+//
+// Cholesky-QR needs kappa(X)^2 * eps < 1; the block products are applied
+// to an orthonormal U and hold the field's scales in D, so
+// kappa(X) <= exp(n_wrap * dtau * (8t + 2 xi)), checked by the host.
+// Every matrix is stored row-major; the chain works on X^T so that columns
+// of X are contiguous rows.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.h"
+
+namespace sldqmc {
+
+// ---------------------------------------------------------------- helpers
+__global__ void k_init_udv(double *Ut, double *V, long long nn, int N, double *D, int *sgn,
+                           double *logacc, int cap)
+{
+    const int b = blockIdx.y;
+    const long long off = (long long)b * nn;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(e / N), j = (int)(e % N);
+        double v = (i == j) ? 1.0 : 0.0;
+        Ut[off + e] = v;
+        V[off + e] = v;
+        if (j == 0) D[(long long)b * N + i] = 1.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sgn[b] = 1;
+        sgn[cap + b] = 1;
+        logacc[b] = 0.0;
+    }
+}
+
+// Sort the columns of X diag(D) by decreasing norm (bitonic network in
+// shared memory).  key_j = sqrt(W_jj) D_j where W = X^T X.  Padding keys
+// -1, -2, ... keep the pads in place so the swap-count parity is the
+// parity of the real permutation.  perm[k] = column at position k.
+__global__ void k_sort_pivot(const double *W, long long sW, int ldw, const double *D, int N,
+                             int Npad, int *perm, double *Dp, int *sgn)
+{
+    extern __shared__ unsigned char smem_raw[];
+    double *key = reinterpret_cast<double *>(smem_raw);
+    int *idx = reinterpret_cast<int *>(key + Npad);
+    __shared__ int par;
+    const int b = blockIdx.x;
+    const double *Wb = W + (long long)b * sW;
+    const double *Db = D + (long long)b * N;
+    if (threadIdx.x == 0) par = 0;
+    for (int j = threadIdx.x; j < Npad; j += blockDim.x) {
+        key[j] = (j < N) ? sqrt(Wb[(long long)j * ldw + j]) * Db[j] : -(1.0 + (double)(j - N));
+        idx[j] = j;
+    }
+    __syncthreads();
+    int swaps = 0;
+    for (int k = 2; k <= Npad; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < Npad; t += blockDim.x) {
+                int u = t ^ j;
+                if (u > t) {
+                    bool desc = (t & k) == 0;
+                    double a = key[t], c = key[u];
+                    bool sw = desc ? (a < c) : (a > c);
+                    if (sw) {
+                        key[t] = c; key[u] = a;
+                        int q = idx[t]; idx[t] = idx[u]; idx[u] = q;
+                        swaps ^= 1;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    if (swaps) atomicXor(&par, 1);
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        perm[(long long)b * N + j] = idx[j];
+        Dp[(long long)b * N + j] = Db[idx[j]];
+    }
+    if (threadIdx.x == 0 && par) sgn[b] = -sgn[b];
+}
+
+// Wc[a][c] = W[p_a][p_c] for c >= a (W holds its upper triangle) and
+// Y[a][:] = Xt[p_a][:]  (the columns of X P as rows).
+__global__ void k_gather_pivot(const double *W, long long sW, const double *Xt, double *Wc, double *Y,
+                               long long nn, int N, int ldw, const int *perm)
+{
+    const int b = blockIdx.z;
+    const int a = blockIdx.y;
+    const int *p = perm + (long long)b * N;
+    const int pa = p[a];
+    const double *Wb = W + (long long)b * sW;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        Y[(long long)b * nn + (long long)a * N + c] = Xt[(long long)b * nn + (long long)pa * N + c];
+        if (c >= a) {
+            int pc = p[c];
+            int r0 = pa < pc ? pa : pc, c0 = pa < pc ? pc : pa;
+            Wc[(long long)b * nn + (long long)a * N + c] = Wb[(long long)r0 * ldw + c0];
+        }
+    }
+}
+
+// One block row of the stacked Cholesky-QR: factor the kb x kb diagonal
+// block W_kk = R_kk^T R_kk (in shared memory, every CTA redundantly), then
+// solve R_kk^T y = w for each column: W-columns right of the block give
+// R's block row, Y-columns give Q^T's block row (in place).
+template <int KB>
+__global__ void __launch_bounds__(128) k_chol_panel(const double *W, long long sW, int ldw, double *Y,
+                                                    long long sY, double *R, long long sR, int N,
+                                                    int k0, int kb, int *flag)
+{
+    __shared__ double Rk[KB][KB + 1];
+    const int b = blockIdx.y;
+    const double *Wb = W + (long long)b * sW;
+    for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
+        int r = e / KB, c = e % KB;
+        double v = 0.0;
+        if (r < kb && c < kb) {
+            if (c >= r) v = Wb[(long long)(k0 + r) * ldw + k0 + c];
+        } else if (r == c) {
+            v = 1.0;
+        }
+        Rk[r][c] = v;
+    }
+    __syncthreads();
+    for (int j = 0; j < KB; ++j) {
+        if (threadIdx.x == 0) {
+            double d = Rk[j][j];
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (j < kb) atomicOr(flag, FLAG_NUMERICAL);
+                d = 1.0;
+            }
+            Rk[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        for (int c = j + 1 + threadIdx.x; c < KB; c += blockDim.x) Rk[j][c] /= Rk[j][j];
+        __syncthreads();
+        for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
+            int r = e / KB, c = e % KB;
+            if (r > j && c >= r) Rk[r][c] -= Rk[j][r] * Rk[j][c];
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0) {
+        double *Rb = R + (long long)b * sR;
+        for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+            int r = e / kb, c = e % kb;
+            Rb[(long long)(k0 + r) * N + k0 + c] = (c >= r) ? Rk[r][c] : 0.0;
+        }
+    }
+    const int nW = N - (k0 + kb);
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const double *src;
+    double *dst;
+    long long lds, ldd;
+    int c;
+    if (col < nW) {
+        c = k0 + kb + col;
+        src = Wb; lds = ldw;
+        dst = R + (long long)b * sR; ldd = N;
+    } else if (col < nW + N) {
+        c = col - nW;
+        src = Y + (long long)b * sY; lds = N;
+        dst = Y + (long long)b * sY; ldd = N;
+    } else {
+        return;
+    }
+    double w[KB];
+#pragma unroll
+    for (int r = 0; r < KB; ++r) w[r] = (r < kb) ? src[(long long)(k0 + r) * lds + c] : 0.0;
+#pragma unroll
+    for (int r = 0; r < KB; ++r) {
+        double acc = w[r];
+#pragma unroll
+        for (int l = 0; l < r; ++l) acc -= Rk[l][r] * w[l];
+        w[r] = acc / Rk[r][r];
+    }
+#pragma unroll
+    for (int r = 0; r < KB; ++r)
+        if (r < kb) dst[(long long)(k0 + r) * ldd + c] = w[r];
+}
+
+// D_new[k] = R_kk * D_p[k]  (R from Cholesky has a positive diagonal).
+__global__ void k_new_D(const double *R, long long nn, int N, const double *Dp, double *D, int *flag)
+{
+    const int b = blockIdx.y;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        double v = R[(long long)b * nn + (long long)k * N + k] * Dp[(long long)b * N + k];
+        if (!(v > 0.0) || !isfinite(v)) {
+            atomicOr(flag, FLAG_NUMERICAL);
+            v = 1.0;
+        }
+        D[(long long)b * N + k] = v;
+    }
+}
+
+// Vg[a][:] = D_p[a] * V[p_a][:]
+__global__ void k_gather_V(const double *V, double *Vg, long long nn, int N, const int *perm,
+                           const double *Dp)
+{
+    const int b = blockIdx.z, a = blockIdx.y;
+    const int pa = perm[(long long)b * N + a];
+    const double s = Dp[(long long)b * N + a];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+        Vg[(long long)b * nn + (long long)a * N + c] = s * V[(long long)b * nn + (long long)pa * N + c];
+}
+
+// M_mid = D_b^{-1} U^T + D_s V, written with row stride ldo; when rhs, the
+// right-hand side D_b^{-1} U^T of the Green's function follows in columns
+// N..2N-1.  D_b = max(D,1), D_s = min(D,1).
+__global__ void k_mmid(const double *Ut, const double *V, const double *D, double *Out, long long nn,
+                       int N, int ldo, int rhs)
+{
+    const int b = blockIdx.z, i = blockIdx.y;
+    const double d = D[(long long)b * N + i];
+    const double db = d > 1.0 ? d : 1.0, ds = d > 1.0 ? 1.0 : d;
+    const double *u = Ut + (long long)b * nn + (long long)i * N;
+    const double *v = V + (long long)b * nn + (long long)i * N;
+    double *o = Out + (long long)b * N * ldo + (long long)i * ldo;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        double uu = u[j] / db;
+        o[j] = uu + ds * v[j];
+        if (rhs) o[N + j] = uu;
+    }
+}
+
+// Panel of the right-looking blocked LU with partial pivoting (one CTA per
+// matrix).  Row interchanges are applied across the full row width ncols.
+__global__ void __launch_bounds__(1024) k_lu_panel(double *A, long long sA, int lda, int N, int ncols,
+                                                   int k0, int kb, int *piv, double *logacc,
+                                                   int *lusgn, int *flag)
+{
+    const int b = blockIdx.x;
+    double *Ab = A + (long long)b * sA;
+    __shared__ double wv[32];
+    __shared__ int wi[32];
+    __shared__ int s_p;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = k0; j < k0 + kb; ++j) {
+        double best = -1.0;
+        int bi = N;
+        for (int i = j + threadIdx.x; i < N; i += blockDim.x) {
+            double v = fabs(Ab[(long long)i * lda + j]);
+            if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_down_sync(0xffffffffu, best, o);
+            int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bv = wv[0];
+            int bidx = wi[0];
+            for (int w = 1; w < nw; ++w)
+                if (wv[w] > bv || (wv[w] == bv && wi[w] < bidx)) { bv = wv[w]; bidx = wi[w]; }
+            s_p = bidx < N ? bidx : j;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != j)
+            for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+                double t = Ab[(long long)j * lda + c];
+                Ab[(long long)j * lda + c] = Ab[(long long)p * lda + c];
+                Ab[(long long)p * lda + c] = t;
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            piv[(long long)b * N + j] = p;
+            double v = Ab[(long long)j * lda + j];
+            int sg = (p != j) ? -1 : 1;
+            if (v == 0.0 || !isfinite(v)) {
+                atomicOr(flag, FLAG_NUMERICAL);
+                v = 1.0;
+                Ab[(long long)j * lda + j] = 1.0;
+            }
+            if (v < 0.0) sg = -sg;
+            logacc[b] += log(fabs(v));
+            lusgn[b] *= sg;
+        }
+        __syncthreads();
+        const double v = Ab[(long long)j * lda + j];
+        for (int i = j + 1 + threadIdx.x; i < N; i += blockDim.x) Ab[(long long)i * lda + j] /= v;
+        __syncthreads();
+        const int w = k0 + kb - j - 1;
+        if (w > 0) {
+            const long long tot = (long long)(N - j - 1) * w;
+            for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+                int i = j + 1 + (int)(e / w), c = j + 1 + (int)(e % w);
+                Ab[(long long)i * lda + c] -= Ab[(long long)i * lda + j] * Ab[(long long)j * lda + c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// U12 = L11^{-1} A12 for the block row k0..k0+kb (L11 unit lower).
+template <int KB>
+__global__ void __launch_bounds__(128) k_lu_trsm_row(double *A, long long sA, int lda, int ncols, int k0, int kb)
+{
+    __shared__ double Lk[KB][KB + 1];
+    const int b = blockIdx.y;
+    double *Ab = A + (long long)b * sA;
+    for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
+        int r = e / KB, c = e % KB;
+        Lk[r][c] = (r < kb && c < r) ? Ab[(long long)(k0 + r) * lda + k0 + c] : 0.0;
+    }
+    __syncthreads();
+    const int c = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    double w[KB];
+#pragma unroll
+    for (int r = 0; r < KB; ++r) w[r] = (r < kb) ? Ab[(long long)(k0 + r) * lda + c] : 0.0;
+#pragma unroll
+    for (int r = 0; r < KB; ++r) {
+        double acc = w[r];
+#pragma unroll
+        for (int l = 0; l < r; ++l) acc -= Lk[r][l] * w[l];
+        w[r] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < KB; ++r)
+        if (r < kb) Ab[(long long)(k0 + r) * lda + c] = w[r];
+}
+
+// X_k = U_kk^{-1} Y_k for the block row k0..k0+kb of the right-hand side
+// held in columns N..2N-1 (back substitution of the Green's function).
+template <int KB>
+__global__ void __launch_bounds__(128) k_trsm_upper_rhs(double *A, long long sA, int lda, int N, int k0, int kb)
+{
+    __shared__ double Uk[KB][KB + 1];
+    const int b = blockIdx.y;
+    double *Ab = A + (long long)b * sA;
+    for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
+        int r = e / KB, c = e % KB;
+        double v = 0.0;
+        if (r < kb && c < kb && c >= r) v = Ab[(long long)(k0 + r) * lda + k0 + c];
+        else if (r == c) v = 1.0;
+        Uk[r][c] = v;
+    }
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double w[KB];
+#pragma unroll
+    for (int r = 0; r < KB; ++r) w[r] = (r < kb) ? Ab[(long long)(k0 + r) * lda + N + c] : 0.0;
+#pragma unroll
+    for (int r = KB - 1; r >= 0; --r) {
+        double acc = w[r];
+#pragma unroll
+        for (int l = r + 1; l < KB; ++l) acc -= Uk[r][l] * w[l];
+        w[r] = acc / Uk[r][r];
+    }
+#pragma unroll
+    for (int r = 0; r < KB; ++r)
+        if (r < kb) Ab[(long long)(k0 + r) * lda + N + c] = w[r];
+}
+
+// log|det(1 + U D V)| = sum log D_b + log|det M_mid|, sign = det(U) sign * LU sign.
+__global__ void k_finalize(const double *D, int N, const double *logacc, const int *sgn, int cap,
+                           double *ld_out, int *sign_out, double scale, int accumulate)
+{
+    const int b = blockIdx.x;
+    __shared__ double part[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double d = D[(long long)b * N + i];
+        if (d > 1.0) s += log(d);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        double ld = t + logacc[b];
+        int sg = sgn[b] * sgn[cap + b];
+        if (accumulate) {
+            ld_out[b] += scale * ld;
+        } else {
+            ld_out[b] = scale * ld;
+            if (sign_out) sign_out[b] = sg;
+        }
+    }
+}
+
+__global__ void k_copy_rhs(const double *A, long long sA, int lda, int N, double *G)
+{
+    const int b = blockIdx.z, i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x)
+        G[(long long)b * N * N + (long long)i * N + j] = A[(long long)b * sA + (long long)i * lda + N + j];
+}
+
+// ------------------------------------------------------------ launchers
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+void stab_set_limits(int Npad)
+{
+    size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
+    if (sh > 48 * 1024) cudaFuncSetAttribute(k_sort_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+}
+
+void launch_init_udv(sldqmc_ctx *c, double *Ut, double *V, int B)
+{
+    dim3 grid(cdiv(c->nn, 256) < 64 ? cdiv(c->nn, 256) : 64, B);
+    k_init_udv<<<grid, 256, 0, c->st>>>(Ut, V, c->nn, c->N, c->d_D, c->d_sgn, c->d_logacc, c->cap);
+    c->launches++;
+}
+
+static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double *R, int B)
+{
+    const int N = c->N;
+    const long long nn = c->nn;
+    cudaMemsetAsync(R, 0, sizeof(double) * nn * B, c->st);
+    for (int k0 = 0; k0 < N; k0 += 32) {
+        int kb = N - k0 < 32 ? N - k0 : 32;
+        int nW = N - (k0 + kb);
+        dim3 grid(cdiv(nW + N, 128), B);
+        k_chol_panel<32><<<grid, 128, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
+        c->launches++;
+        if (nW > 0) {
+            // W[k0+kb:, k0+kb:] -= R_blk^T R_blk   (upper triangle only)
+            GemmF64 g = gemm_desc(nW, nW, kb, R + (long long)k0 * N + k0 + kb, N, nn,
+                                  R + (long long)k0 * N + k0 + kb, N, nn,
+                                  W + (long long)(k0 + kb) * N + k0 + kb, N, sW, B);
+            g.alpha = -1.0; g.beta = 1.0; g.c_upper = 1;
+            gemm_f64(g, true, false, c->st);
+            // Y[k0+kb:, :] -= R_blk^T Qt_blk
+            GemmF64 h = gemm_desc(nW, N, kb, R + (long long)k0 * N + k0 + kb, N, nn,
+                                  Y + (long long)k0 * N, N, nn, Y + (long long)(k0 + kb) * N, N, nn, B);
+            h.alpha = -1.0; h.beta = 1.0;
+            gemm_f64(h, true, false, c->st);
+            c->launches += 2;
+        }
+    }
+}
+
+// Re-factorise X (given as Xt = X^T) against the running D and V.
+// On return: the new U^T is in *Y (caller swaps buffers), D and V updated.
+void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B)
+{
+    const int N = c->N;
+    const long long nn = c->nn;
+    double *W = c->buf[4];
+    double *R1 = c->buf[6], *R2 = c->buf[7], *Vg = c->buf[8], *V = c->buf[1];
+    // W = Xt Xt^T (upper triangle)
+    GemmF64 g = gemm_desc(N, N, N, Xt, N, nn, Xt, N, nn, W, N, 2 * nn, B);
+    g.c_upper = 1;
+    gemm_f64(g, false, true, c->st);
+    int Npad = 1;
+    while (Npad < N) Npad <<= 1;
+    size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
+    k_sort_pivot<<<B, 1024, sh, c->st>>>(W, 2 * nn, N, c->d_D, N, Npad, c->d_perm, c->d_Dp, c->d_sgn);
+    dim3 gg(cdiv(N, 256), N, B);
+    k_gather_pivot<<<gg, 256, 0, c->st>>>(W, 2 * nn, Xt, Wc, Y, nn, N, N, c->d_perm);
+    c->launches += 3;
+    chol_pass(c, Wc, nn, Y, R1, B);
+    // second pass: W = Q1^T Q1 (as Y Y^T), upper triangle
+    GemmF64 g2 = gemm_desc(N, N, N, Y, N, nn, Y, N, nn, W, N, 2 * nn, B);
+    g2.c_upper = 1;
+    gemm_f64(g2, false, true, c->st);
+    c->launches++;
+    chol_pass(c, W, 2 * nn, Y, R2, B);
+    // R = R2 R1 into Xt's (now dead) buffer
+    GemmF64 g3 = gemm_desc(N, N, N, R2, N, nn, R1, N, nn, Xt, N, nn, B);
+    g3.a_upper = 1;
+    gemm_f64(g3, false, false, c->st);
+    dim3 gd(cdiv(N, 256), B);
+    k_new_D<<<gd, 256, 0, c->st>>>(Xt, nn, N, c->d_Dp, c->d_D, c->d_flag);
+    k_gather_V<<<gg, 256, 0, c->st>>>(V, Vg, nn, N, c->d_perm, c->d_Dp);
+    // V = D^{-1} R Vg
+    GemmF64 g4 = gemm_desc(N, N, N, Xt, N, nn, Vg, N, nn, V, N, nn, B);
+    g4.a_upper = 1;
+    g4.ms = c->d_D; g4.sMs = N; g4.ms_recip = 1;
+    gemm_f64(g4, false, false, c->st);
+    c->launches += 4;
+}
+
+// Final determinant (and optionally G) from the running U^T, D, V.
+void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign, double *d_G,
+              double scale, int accumulate)
+{
+    const int N = c->N;
+    const long long nn = c->nn;
+    const int rhs = d_G != nullptr;
+    const int lda = rhs ? 2 * N : N;
+    const int ncols = lda;
+    double *A = c->buf[4];  // 2*nn per item
+    dim3 gm(cdiv(N, 256), N, B);
+    k_mmid<<<gm, 256, 0, c->st>>>(Ut, c->buf[1], c->d_D, A, nn, N, lda, rhs);
+    c->launches++;
+    // note: k_mmid writes item b at offset b*N*lda; with lda = N the items
+    // are packed at stride nn, with lda = 2N at stride 2nn.
+    const long long sItem = (long long)N * lda;
+    for (int k0 = 0; k0 < N; k0 += 32) {
+        int kb = N - k0 < 32 ? N - k0 : 32;
+        k_lu_panel<<<B, 1024, 0, c->st>>>(A, sItem, lda, N, ncols, k0, kb, c->d_piv, c->d_logacc,
+                                          c->d_sgn + c->cap, c->d_flag);
+        c->launches++;
+        int rest = ncols - (k0 + kb);
+        if (rest > 0) {
+            dim3 gt(cdiv(rest, 128), B);
+            k_lu_trsm_row<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, ncols, k0, kb);
+            c->launches++;
+            int m2 = N - (k0 + kb);
+            if (m2 > 0) {
+                GemmF64 g = gemm_desc(m2, rest, kb, A + (long long)(k0 + kb) * lda + k0, lda, sItem,
+                                      A + (long long)k0 * lda + k0 + kb, lda, sItem,
+                                      A + (long long)(k0 + kb) * lda + k0 + kb, lda, sItem, B);
+                g.alpha = -1.0; g.beta = 1.0;
+                gemm_f64(g, false, false, c->st);
+                c->launches++;
+            }
+        }
+    }
+    if (rhs) {
+        int nblk = (N + 31) / 32;
+        for (int kbi = nblk - 1; kbi >= 0; --kbi) {
+            int k0 = kbi * 32;
+            int kb = N - k0 < 32 ? N - k0 : 32;
+            dim3 gt(cdiv(N, 128), B);
+            k_trsm_upper_rhs<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, N, k0, kb);
+            c->launches++;
+            if (k0 > 0) {
+                GemmF64 g = gemm_desc(k0, N, kb, A + k0, lda, sItem, A + (long long)k0 * lda + N, lda,
+                                      sItem, A + N, lda, sItem, B);
+                g.alpha = -1.0; g.beta = 1.0;
+                gemm_f64(g, false, false, c->st);
+                c->launches++;
+            }
+        }
+        dim3 gc(cdiv(N, 256), N, B);
+        k_copy_rhs<<<gc, 256, 0, c->st>>>(A, sItem, lda, N, d_G);
+        c->launches++;
+    }
+    k_finalize<<<B, 256, 0, c->st>>>(c->d_D, N, c->d_logacc, c->d_sgn, c->cap, d_ld, d_sign, scale,
+                                     accumulate);
+    c->launches++;
+}
+
+}  // namespace sldqmc
