@@ -350,7 +350,7 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     // Cholesky-QR of one block needs kappa(X)^2 eps << 1; kappa(X) is
     // bounded by exp(n_wrap dtau (8|t| + 2|xi|)).
     const double logk = (double)std::min<long long>(p->n_wrap, M) * p->dtau * (8.0 * fabs(p->t) + 2.0 * fabs(p->xi));
-    if (logk > 14.0) return SLDQMC_ERR_UNSUPPORTED;
+    if (logk > 16.0) return SLDQMC_ERR_UNSUPPORTED;
 
     sldqmc_ctx *c = (sldqmc_ctx *)calloc(1, sizeof(sldqmc_ctx));
     if (!c) return SLDQMC_ERR_OOM;

@@ -1,15 +1,462 @@
-// tc_gemm.cu -- tensor-core slice products (3xTF32 / BF16); placeholder
-// until the tcgen05 kernels land: the mixed modes report UNSUPPORTED.
+// tc_gemm.cu -- tensor-core slice products for the mixed-precision modes.
+//
+// Inside one stabilisation block the running product is X^T <- X^T E
+// diag(d_next), with E = exp(-dtau K) (symmetric) and d the field scale of
+// the next slice (B_tau = E diag(exp(eta dtau xi s_tau))).  Both operands are
+// K-major, so the product maps directly onto tcgen05.mma:
+//
+//   3xTF32: A = A_hi + A_lo, B = B_hi + B_lo (TF32-rounded parts), and
+//           A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, three MMAs accumulated in
+//           FP32 in tensor memory;
+//   BF16:   one kind::f16 MMA with BF16 operands, FP32 accumulation.
+//
+// One CTA computes a 128 x 128 output tile: warp 0 drives TMA (128-byte
+// swizzled boxes, mbarrier completion), warp 1 issues the MMAs from one
+// thread, and all four warps drain the accumulator with tcgen05.ld and apply
+// the next slice's column scaling while re-splitting the result into the
+// operand format of the next product (or FP64 for the stabilisation at the
+// end of the block).  Every mbarrier wait is bounded; a wait that runs out
+// raises the context's timeout flag and the CTA frees its tensor memory and
+// exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
 
 namespace sldqmc {
-int tc_prepare(sldqmc_ctx *) { return SLDQMC_ERR_UNSUPPORTED; }
-void tc_release(sldqmc_ctx *) {}
-void tc_convert_E(sldqmc_ctx *) {}
-void tc_chain_block(sldqmc_ctx *, const double *, const int8_t *, int, double, double, const int *, int,
-                    double *, double *, double *)
+
+namespace {
+
+constexpr int BM = 128, BN = 128;
+constexpr int TILE_BYTES = BM * 128;  // one operand part of one stage: 128 rows x 128 bytes
+
+struct TcArgs {
+    int N, ldp, nk;
+    float *out_hi, *out_lo;
+    __nv_bfloat16 *out_bf;
+    double *out_f64;
+    long long s_out, s_f64;
+    const int8_t *s_n;
+    long long sSn;
+    float cu, cd;
+    int *flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after 2^22 polls (well over a second), raising the
+// timeout flag instead of spinning forever.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *flag)
+{
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(flag, FLAG_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand stored as 128-byte
+// rows with the 128-byte swizzle (8-row atoms of 1024 bytes).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+    d |= (uint64_t)1u << 16;                   // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset: 8 rows x 128 bytes
+    d |= (uint64_t)1u << 46;                   // descriptor version
+    d |= (uint64_t)2u << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format)
+{
+    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    if (MODE == 0)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+              const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, TcArgs a)
+{
+    constexpr int NPART = MODE == 0 ? 2 : 1;
+    constexpr int STAGE_BYTES = 2 * NPART * TILE_BYTES;
+    constexpr int STAGES = MODE == 0 ? 3 : 4;
+    constexpr int KSTEPS = 4;  // 128-byte row / 32 bytes per MMA K-step (8 TF32 or 16 BF16)
+    constexpr uint32_t IDESC = instr_desc(MODE == 0 ? 2u : 1u);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(base + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, b = blockIdx.z;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < a.nk; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, a.flag)) break;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            uint8_t *st = base + s * STAGE_BYTES;
+            const int k0 = kb * (128 / (MODE == 0 ? 4 : 2));
+            tma_load_3d(st, &tA0, k0, m0, b, &full[s]);
+            if (NPART == 2) tma_load_3d(st + TILE_BYTES, &tA1, k0, m0, b, &full[s]);
+            tma_load_2d(st + NPART * TILE_BYTES, &tB0, k0, n0, &full[s]);
+            if (NPART == 2) tma_load_2d(st + 3 * TILE_BYTES, &tB1, k0, n0, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        bool ok = true;
+        for (int kb = 0; kb < a.nk && ok; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(&full[s], (kb / STAGES) & 1, a.flag)) { ok = false; break; }
+            fence_after();
+            const uint32_t sa = smem_u32(base + s * STAGE_BYTES);
+#pragma unroll
+            for (int k = 0; k < KSTEPS; ++k) {
+                const uint32_t off = k * 32;
+                if (MODE == 0) {
+                    const uint64_t ah = smem_desc(sa + off), al = smem_desc(sa + TILE_BYTES + off);
+                    const uint64_t bh = smem_desc(sa + 2 * TILE_BYTES + off), bl = smem_desc(sa + 3 * TILE_BYTES + off);
+                    mma<0>(tmem, ah, bh, IDESC, (kb | k) != 0);
+                    mma<0>(tmem, ah, bl, IDESC, 1u);
+                    mma<0>(tmem, al, bh, IDESC, 1u);
+                } else {
+                    mma<1>(tmem, smem_desc(sa + off), smem_desc(sa + TILE_BYTES + off), IDESC, (kb | k) != 0);
+                }
+            }
+            mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(done);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(done, 0, a.flag);
+    fence_after();
+    const int row = warp * 32 + lane;
+    const int m = m0 + row;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+        if (!ok || m >= a.N) continue;
+        const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int n = n0 + c0 + j;
+            if (n >= a.N) break;
+            float v = __uint_as_float(r[j]);
+            if (sn) v *= (sn[n] > 0 ? a.cu : a.cd);
+            if (a.out_f64) {
+                a.out_f64[(long long)b * a.s_f64 + (long long)m * a.N + n] = (double)v;
+            } else if (MODE == 0) {
+                const float hi = to_tf32(v);
+                const long long o = (long long)b * a.s_out + (long long)m * a.ldp + n;
+                a.out_hi[o] = hi;
+                a.out_lo[o] = to_tf32(v - hi);
+            } else {
+                a.out_bf[(long long)b * a.s_out + (long long)m * a.ldp + n] = __float2bfloat16_rn(v);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+// Operand of the first product of a block: Ut diag(d_first), split.
+template <int MODE>
+__global__ void k_tc_prep(const double *Ut, long long nn, int N, int ldp, const int8_t *s_k, long long sSk, double cu,
+                          double cd, float *hi, float *lo, __nv_bfloat16 *bf, long long s_out)
+{
+    const int b = blockIdx.z, m = blockIdx.y;
+    const int8_t *sk = s_k ? s_k + (long long)b * sSk : nullptr;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        double v = Ut[(long long)b * nn + (long long)m * N + k];
+        if (sk) v *= (sk[k] > 0 ? cu : cd);
+        const long long o = (long long)b * s_out + (long long)m * ldp + k;
+        if (MODE == 0) {
+            const float h = to_tf32((float)v);
+            hi[o] = h;
+            lo[o] = to_tf32((float)(v - (double)h));
+        } else {
+            bf[o] = __float2bfloat16_rn((float)v);
+        }
+    }
+}
+
+struct TcWs {
+    int ldp;
+    size_t part_elems;  // per operand part: cap * N * ldp
+    float *opf[2][2];   // [buffer][hi/lo]
+    __nv_bfloat16 *opb[2];
+    float *Ehi, *Elo;
+    __nv_bfloat16 *Ebf;
+    CUtensorMap mapA[2][2];  // [buffer][part]
+    CUtensorMap mapB[2];     // [part]
+    void *mem;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+bool encode(CUtensorMap *map, void *ptr, bool bf16, int rank, int ldp, int rows, int batch)
+{
+    auto fn = get_encode();
+    if (!fn) return false;
+    const int esz = bf16 ? 2 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)ldp, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)ldp * esz, (cuuint64_t)ldp * rows * esz};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)BM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
+                    ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int MODE>
+constexpr size_t smem_bytes()
+{
+    return (size_t)(MODE == 0 ? 3 : 4) * 2 * (MODE == 0 ? 2 : 1) * TILE_BYTES + 1024 + 256;
+}
+
+}  // namespace
+
+int tc_prepare(sldqmc_ctx *c)
+{
+    if (c->N < BM) return SLDQMC_ERR_UNSUPPORTED;  // tensor-core tiles are 128 x 128
+    TcWs *w = new TcWs();
+    c->tc_ws = w;
+    const int N = c->N;
+    w->ldp = (N + 63) / 64 * 64;
+    const bool bf = c->p.prec == SLDQMC_BF16;
+    w->part_elems = (size_t)c->cap * N * w->ldp;
+    const size_t esz = bf ? 2 : 4;
+    const size_t parts = bf ? 2 : 4;              // operand buffers
+    const size_t eparts = bf ? 1 : 2;             // E copies
+    const size_t bytes = esz * (parts * w->part_elems + eparts * (size_t)N * w->ldp);
+    if (cudaMalloc(&w->mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        w->mem = nullptr;
+        return SLDQMC_ERR_OOM;
+    }
+    cudaMemset(w->mem, 0, bytes);  // zero pads: columns N..ldp-1 are never written
+    uint8_t *q = (uint8_t *)w->mem;
+    if (!bf) {
+        for (int i = 0; i < 2; ++i)
+            for (int p = 0; p < 2; ++p) {
+                w->opf[i][p] = (float *)q;
+                q += esz * w->part_elems;
+            }
+        w->Ehi = (float *)q;
+        q += esz * (size_t)N * w->ldp;
+        w->Elo = (float *)q;
+        for (int i = 0; i < 2; ++i)
+            for (int p = 0; p < 2; ++p)
+                if (!encode(&w->mapA[i][p], w->opf[i][p], false, 3, w->ldp, N, c->cap)) return SLDQMC_ERR_CUDA;
+        if (!encode(&w->mapB[0], w->Ehi, false, 2, w->ldp, N, 1) || !encode(&w->mapB[1], w->Elo, false, 2, w->ldp, N, 1))
+            return SLDQMC_ERR_CUDA;
+    } else {
+        for (int i = 0; i < 2; ++i) {
+            w->opb[i] = (__nv_bfloat16 *)q;
+            q += esz * w->part_elems;
+        }
+        w->Ebf = (__nv_bfloat16 *)q;
+        for (int i = 0; i < 2; ++i) {
+            if (!encode(&w->mapA[i][0], w->opb[i], true, 3, w->ldp, N, c->cap)) return SLDQMC_ERR_CUDA;
+            w->mapA[i][1] = w->mapA[i][0];
+        }
+        if (!encode(&w->mapB[0], w->Ebf, true, 2, w->ldp, N, 1)) return SLDQMC_ERR_CUDA;
+        w->mapB[1] = w->mapB[0];
+    }
+    cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<0>());
+    cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1>());
+    return SLDQMC_OK;
+}
+
+void tc_release(sldqmc_ctx *c)
+{
+    TcWs *w = (TcWs *)c->tc_ws;
+    if (!w) return;
+    cudaFree(w->mem);
+    delete w;
+    c->tc_ws = nullptr;
+}
+
+void tc_convert_E(sldqmc_ctx *c)
+{
+    TcWs *w = (TcWs *)c->tc_ws;
+    const int N = c->N;
+    dim3 g((N + 255) / 256, N, 1);
+    if (c->p.prec == SLDQMC_BF16)
+        k_tc_prep<1><<<g, 256, 0, c->st>>>(c->d_E, c->nn, N, w->ldp, nullptr, 0, 1.0, 1.0, nullptr, nullptr, w->Ebf, 0);
+    else
+        k_tc_prep<0><<<g, 256, 0, c->st>>>(c->d_E, c->nn, N, w->ldp, nullptr, 0, 1.0, 1.0, w->Ehi, w->Elo, nullptr, 0);
+    c->launches++;
+}
+
+// X^T = Ut D_{s0} E D_{s1} E ... D_{s_{nb-1}} E for one block; result (FP64)
+// in Xt_out.
+void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, double cu, double cd,
+                    const int *slices, int nb, double *Xt_out, double *, double *)
+{
+    TcWs *w = (TcWs *)c->tc_ws;
+    const int N = c->N, M = c->M;
+    const bool bf = c->p.prec == SLDQMC_BF16;
+    const long long sS = (long long)M * N;
+    const long long s_out = (long long)N * w->ldp;
+    dim3 gp((N + 255) / 256, N, B);
+    if (bf)
+        k_tc_prep<1><<<gp, 256, 0, c->st>>>(Ut, c->nn, N, w->ldp, d_s + (long long)slices[0] * N, sS, cu, cd, nullptr,
+                                            nullptr, w->opb[0], s_out);
+    else
+        k_tc_prep<0><<<gp, 256, 0, c->st>>>(Ut, c->nn, N, w->ldp, d_s + (long long)slices[0] * N, sS, cu, cd,
+                                            w->opf[0][0], w->opf[0][1], nullptr, s_out);
+    c->launches++;
+    dim3 grid((N + BN - 1) / BN, (N + BM - 1) / BM, B);
+    for (int j = 0; j < nb; ++j) {
+        const int src = j & 1, dst = src ^ 1;
+        TcArgs a{};
+        a.N = N;
+        a.ldp = w->ldp;
+        a.nk = w->ldp / (bf ? 64 : 32);
+        a.s_out = s_out;
+        a.s_f64 = c->nn;
+        a.flag = c->d_flag;
+        if (j == nb - 1) {
+            a.out_f64 = Xt_out;
+        } else {
+            a.s_n = d_s + (long long)slices[j + 1] * N;
+            a.sSn = sS;
+            a.cu = (float)cu;
+            a.cd = (float)cd;
+            if (bf) a.out_bf = w->opb[dst];
+            else { a.out_hi = w->opf[dst][0]; a.out_lo = w->opf[dst][1]; }
+        }
+        if (bf)
+            k_tc_gemm<1><<<grid, 128, smem_bytes<1>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
+                                                                w->mapB[1], a);
+        else
+            k_tc_gemm<0><<<grid, 128, smem_bytes<0>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
+                                                                w->mapB[1], a);
+        c->launches++;
+    }
+}
+
 }  // namespace sldqmc

@@ -63,7 +63,7 @@ def test_weight_matches_oracle(Lx, Ly, mu, beta, dtau, nw, kind):
 
 def test_negative_sign_configurations():
     m = O.Model(2, 2, mu=-1.5, xi=6.0, beta=3.0, dtau=0.25, n_wrap=1)
-    with _ctx(m, 4, max_batch=4) as ctx:
+    with _ctx(m, 2, max_batch=4) as ctx:
         fields = np.stack([uniform_field(seed, m.M, m.N) for seed in (4, 28, 0, 1)])
         ld, sg = ctx.weight_batch(fields, 1)
         ref = [O.weight(m, f, 1) for f in fields]
