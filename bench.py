@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the self-learning DQMC hot path on GB300.
+
+Workload (the configuration the headline metric is quoted on): SLDQMC on a
+16x16 lattice, t=1, mu=-0.5, xi=1, beta=8, dtau=0.05 (M=160), n_wrap=10,
+bare Ising weight J=1, h=2.774; effective action with J1/J2/J3 (space) and
+J_tau couplings, fitted (Eq. 3) on local-DQMC configurations of an 8x8
+lattice at the same couplings and transferred to 16x16, as the paper does
+with its L=8 fit.
+
+One step = one cumulative update (steps iii+iv) of B independent chains:
+one sweep of N*M effective-model flips per chain, the exact log weight of
+every proposal (two flavours -> 2B fermion-weight evaluations through the
+stabilised B-chain) and the Eq. 4 acceptance.  The metric is fermion-weight
+evaluations per second (single-flavour det(1+B) evaluations) with the
+slice products in split-TF32 (mixed) precision; the FP64-product path and
+decorrelated samples/s are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own chains (weak scaling, no data-path
+collective); the timed region is bracketed by a barrier and a device
+synchronisation and the time is the maximum over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WL = dict(L=16, t=1.0, mu=-0.5, xi=1.0, beta=8.0, dtau=0.05, n_wrap=10, J=1.0, h=2.774)
+CLASSES = [[(1, 0, 0), (0, 1, 0)], [(1, 1, 0), (1, -1, 0)], [(2, 0, 0), (0, 2, 0)], [(0, 0, 1)]]
+METRIC = "fermion-weight evals/s and decorrelated samples/s, mixed vs FP64, 1 GB300"
+UNIT = "weight evals/s"
+NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}  # TFLOP/s, dense, per GPU
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def workload_name():
+    return ("SLDQMC cumulative update, 16x16 lattice, beta=8, dtau=0.05 (M=160), mu=-0.5, xi=1, "
+            "n_wrap=10, J1/J2/J3/Jtau effective action")
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    src = "fallback"
+    vals = dict(FALLBACK)
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            flat = {}
+
+            def walk(o):
+                for k, v in o.items():
+                    if isinstance(v, dict):
+                        walk(v)
+                    else:
+                        flat[k] = v
+            walk(d)
+            if "hbm_gbs" in flat:
+                vals["hbm_gbs"] = float(flat["hbm_gbs"])
+            if "bf16_tflops" in flat:
+                vals["bf16_tflops"] = float(flat["bf16_tflops"])
+            src = "measured"
+        except Exception:
+            pass
+    vals["fp64_tflops"] = vals["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+    vals["tf32_tflops"] = vals["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
+    vals["source"] = src
+    return vals
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_record(kernel_class):
+    """Per-launch DRAM traffic of a kernel class from a committed ncu summary,
+    valid only while the kernel's source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path)).get(kernel_class)
+        if not d:
+            return None
+        src = open(os.path.join(ROOT, "paper_1612_03804_gb300", "csrc", d["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != d["sha"]:
+            return None
+        return d
+    except Exception:
+        return None
+
+
+def oracle_weight_sample(seed=1):
+    """One single-flavour weight evaluation of the workload by the FP64 CPU
+    oracle (as it stands, with the workload's n_wrap)."""
+    from oracle import oracle as O
+    from paper_1612_03804_gb300.inputs import uniform_field
+    m = O.Model(WL["L"], WL["L"], t=WL["t"], mu=WL["mu"], xi=WL["xi"], beta=WL["beta"], dtau=WL["dtau"],
+                n_wrap=WL["n_wrap"], J=WL["J"], h=WL["h"])
+    s = uniform_field(seed, m.M, m.N)
+    t0 = time.perf_counter()
+    O.weight(m, s, -1)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    for w in range(args.warmup):
+        oracle_weight_sample(100 + w)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle_weight_sample(200 + k)
+    T = time.perf_counter() - t0
+    value = args.steps / T
+    sample = "one single-flavour weight evaluation (16x16, M=160, n_wrap=10) per step, FP64 CPU oracle"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_name(), "global_batch": 1, "seq_len": 160,
+                                           "parallelism": "cpu-1-thread"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def train_effective_model(torch, sldqmc, args, dev_seed):
+    """Steps i-ii: local DQMC on 8x8 at the workload couplings, then the Eq. 3 fit."""
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    Bt = args.train_chains
+    ctx8 = sldqmc.Context(8, 8, t=WL["t"], mu=WL["mu"], xi=WL["xi"], beta=WL["beta"], dtau=WL["dtau"],
+                          n_wrap=WL["n_wrap"], J=WL["J"], h=WL["h"], prec="fp64", max_batch=Bt)
+    s = torch.from_numpy(batch_uniform(dev_seed, Bt, ctx8.M, ctx8.N)).cuda()
+    ctx8.local_sweep_batch_dev(s, dev_seed, 0, args.thermalize, want_stats=False)
+    cfgs = []
+    sweep = args.thermalize
+    while len(cfgs) * Bt < args.train_configs:
+        ctx8.local_sweep_batch_dev(s, dev_seed, sweep, 1, want_stats=False)
+        sweep += 1
+        cfgs.append(s.cpu().numpy().copy())
+    import numpy as np
+    cfgs = np.concatenate(cfgs)[: args.train_configs]
+    ctx8.set_effective_model(CLASSES, np.zeros(len(CLASSES)))
+    J, E0, r2 = ctx8.fit_effective_action(cfgs)
+    ctx8.close()
+    return J, E0, r2, len(cfgs)
+
+
+def steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, step0, K, mags=None):
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for k in range(K):
+        ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, step0 + k, 1, d_acc)
+        if mags is not None:
+            mags[k] = d_s.sum(dim=(1, 2), dtype=torch.int64)
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_1612_03804_gb300 import sldqmc
+    from paper_1612_03804_gb300.analysis import tau_int
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    sldqmc.load()
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t_setup = time.perf_counter()
+    J, E0, r2, ncfg = train_effective_model(torch, sldqmc, args, 7000 + rank)
+    t_setup = time.perf_counter() - t_setup
+    B = args.batch
+    seed = 123456789 + (rank << 20)
+
+    def make_ctx(prec):
+        c = sldqmc.Context(WL["L"], WL["L"], t=WL["t"], mu=WL["mu"], xi=WL["xi"], beta=WL["beta"],
+                           dtau=WL["dtau"], n_wrap=WL["n_wrap"], J=WL["J"], h=WL["h"], prec=prec, max_batch=B)
+        c.set_effective_model(CLASSES, J, E0)
+        return c
+
+    ctx = make_ctx(args.prec)
+    V = ctx.V
+    d_s = torch.from_numpy(batch_uniform(5000 + rank, B, ctx.M, ctx.N)).cuda()
+    d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
+    d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+    ctx.log_weight_batch_dev(d_s, d_lw)
+    ctx.sync()
+    # warm-up (also thermalises the chains under the cumulative update)
+    for w in range(args.warmup):
+        ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, w, 1, d_acc)
+    ctx.sync()
+    d_acc.zero_()
+    mags = torch.zeros((args.steps, B), dtype=torch.int64, device="cuda")
+    sampler = ClockSampler(local)
+    sampler.start()
+    n0 = ctx.kernel_launches()
+    barrier_sync()
+    T = steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, args.warmup, args.steps, mags)
+    barrier_sync()
+    launches = ctx.kernel_launches() - n0
+    clocks = sampler.stop()
+    ctx.sync()
+    Tmax = max_over_ranks(T)
+    units = 2 * B * args.steps * world
+    value = units / Tmax
+    accept_rate = float(d_acc.sum().item()) / (B * args.steps)
+    # decorrelation: magnetisation series over a longer (untimed) run
+    extra = args.tau_steps
+    mags_all = [mags.cpu().numpy()]
+    if extra > 0:
+        more = torch.zeros((extra, B), dtype=torch.int64, device="cuda")
+        steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, args.warmup + args.steps, extra, more)
+        mags_all.append(more.cpu().numpy())
+    series = np.concatenate(mags_all).astype(np.float64)
+    tau, window = tau_int(series)
+    samples_per_s = (B * world * args.steps / Tmax) / tau
+
+    # roofline: a profiled pass (CUDA events around every launch)
+    ctx.profile(True)
+    ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, args.profile_steps, d_acc)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    pk = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    rec = prof[dom]
+    if dom == "gemm_tc":
+        tflops = rec["flops"] / (rec["ms"] * 1e-3) / 1e12
+        peak = pk["tf32_tflops"] if args.prec == "3xtf32" else pk["bf16_tflops"]
+        bound, unit, achieved = "tensor", "TFLOP/s", tflops
+    elif dom == "gemm_f64":
+        bound, unit, achieved, peak = "alu", "TFLOP/s", rec["flops"] / (rec["ms"] * 1e-3) / 1e12, pk["fp64_tflops"]
+    else:
+        bound, unit, achieved, peak = "alu", "TFLOP/s", None, pk["fp64_tflops"]
+    tr = traffic_record(dom)
+    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": tr["bytes_per_launch"] if tr else None,
+                "peak_source": f"{pk['source']} (fp64 = bf16 x 1.25/2250 nominal ratio)",
+                "launches": rec["launches"], "ms_per_launch": rec["ms"] / max(rec["launches"], 1),
+                "share": rec["ms"] / sum(v["ms"] for v in prof.values()),
+                "breakdown_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+
+    # FP64-product path on the same workload
+    fp64 = None
+    if not args.skip_fp64:
+        c64 = make_ctx("fp64")
+        d_s64 = d_s.clone()
+        d_lw64 = torch.zeros(B, dtype=torch.float64, device="cuda")
+        c64.log_weight_batch_dev(d_s64, d_lw64)
+        c64.cumulative_batch_dev(d_s64, d_lw64, 1, seed, 0, 1, d_acc)
+        c64.sync()
+        K64 = max(2, args.steps // 3)
+        barrier_sync()
+        T64 = steps_timed(torch, c64, d_s64, d_lw64, d_acc, seed, 1, K64)
+        barrier_sync()
+        T64 = max_over_ranks(T64)
+        fp64 = {"value": 2 * B * K64 * world / T64, "unit": UNIT, "steps": K64, "ms_per_step": 1e3 * T64 / K64}
+        c64.close()
+
+    # end to end through the host-buffer C ABI call (copies inside the timed region)
+    h_s = torch.empty((B, ctx.M, ctx.N), dtype=torch.int8).pin_memory()
+    h_s.copy_(d_s.cpu())
+    h_lw = torch.empty(B, dtype=torch.float64).pin_memory()
+    h_lw.copy_(d_lw.cpu())
+    h_acc = np.zeros(B, dtype=np.int32)
+    hs, hl = h_s.numpy(), h_lw.numpy()
+    Ke = max(2, args.steps // 2)
+    barrier_sync()
+    t0 = time.perf_counter()
+    for k in range(Ke):
+        ctx.cumulative_batch(hs, hl, 1, seed, 2 * 10 ** 6 + k, 1, h_acc)
+    torch.cuda.synchronize()
+    Te = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": 2 * B * Ke * world / Te, "unit": UNIT, "h2d_bytes_per_step": B * V + 8 * B,
+           "d2h_bytes_per_step": B * V + 8 * B + 4 * B}
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        from oracle import oracle as O
+        O.build()
+        t1 = oracle_weight_sample(1)
+        cpu = {"value": 1.0 / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one single-flavour weight evaluation (16x16, M=160, n_wrap=10, uniform random field) "
+                         "by the FP64 CPU oracle, one host thread"}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * Tmax / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "tf32x2/fp32-acc products, f64 stabilisation" if args.prec == "3xtf32" else args.prec,
+               "data": "synthetic (seeded random fields; effective model fitted on seeded local-DQMC runs)",
+               "config": {"workload": workload_name(), "global_batch": B * world, "seq_len": ctx.M,
+                          "lattice": f"{WL['L']}x{WL['L']}", "chains_per_gpu": B, "precision": args.prec,
+                          "parallelism": f"replicas x{world}", "l2": "working set > L2 (no flush)",
+                          "fit": {"lattice": "8x8", "configs": ncfg, "J": [float(x) for x in J],
+                                  "E0": E0, "r2": r2}, "setup_s": round(t_setup, 2)},
+               "fp64": fp64, "decorrelated_samples_per_s": samples_per_s, "tau_int": tau,
+               "tau_window": window, "accept_rate": accept_rate,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+               "gpu_launches": launches}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--prec", default="3xtf32", choices=["3xtf32", "bf16", "fp64"])
+    ap.add_argument("--train-configs", type=int, default=2000)
+    ap.add_argument("--train-chains", type=int, default=64)
+    ap.add_argument("--thermalize", type=int, default=20)
+    ap.add_argument("--tau-steps", type=int, default=30)
+    ap.add_argument("--profile-steps", type=int, default=1)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

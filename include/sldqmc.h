@@ -59,7 +59,9 @@ extern "C" {
  * Monte Carlo decision are FP64 in all modes. */
 typedef enum {
     SLDQMC_FP64 = 0,   /* FP64 FMA products */
-    SLDQMC_3XTF32 = 1, /* split-TF32 tensor-core products (3 MMAs), FP32 accumulate */
+    SLDQMC_3XTF32 = 1, /* split-TF32 tensor-core products: the running product in two TF32
+                          parts, exp(-dtau K) in three (five MMAs per K-step), FP32
+                          accumulation spread over eight tensor-memory accumulators */
     SLDQMC_BF16 = 2    /* BF16 tensor-core products, FP32 accumulate */
 } sldqmc_prec;
 
@@ -189,12 +191,35 @@ int sldqmc_cumulative_batch_dev(sldqmc_ctx *ctx, int8_t *d_s, double *d_logw, in
                                 uint64_t seed, uint32_t step0, int n_steps, int *d_accepts,
                                 double *d_log_r);
 
+/* Host-buffer form of sldqmc_cumulative_batch_dev (synchronous): copies
+ * s (B*M*N) and logw (B) in, runs n_steps updates, copies s, logw and the
+ * per-chain accept counts (accepts: B ints, added to) back.  B <= max_batch. */
+int sldqmc_cumulative_batch(sldqmc_ctx *ctx, int8_t *s, double *logw, int B, int n_eff, uint64_t seed,
+                            uint32_t step0, int n_steps, int *accepts);
+
 /* log omega = log phi + 2 ld(+1) + 2 ld(-1) for B configurations on device
  * buffers (the exact weight a cumulative update needs). */
 int sldqmc_log_weight_batch_dev(sldqmc_ctx *ctx, const int8_t *d_s, int B, double *d_logw);
 
 /* Number of this library's kernels launched on the context since create. */
 long long sldqmc_kernel_launches(const sldqmc_ctx *ctx);
+
+/* Kernel classes for the timing hooks below. */
+#define SLDQMC_KC_GEMM_F64 0   /* FP64 GEMM (slice products in FP64 mode, Gram, trailing updates) */
+#define SLDQMC_KC_GEMM_TC 1    /* tensor-core slice products (3xTF32 / BF16) */
+#define SLDQMC_KC_PANEL_F64 2  /* FP64 panel kernels (Cholesky, LU, triangular solves, pivot sort) */
+#define SLDQMC_KC_EFF 3        /* effective-model sweeps */
+#define SLDQMC_KC_LOCAL 4      /* local-update flips */
+#define SLDQMC_KC_OTHER 5      /* everything else */
+#define SLDQMC_KC_COUNT 6
+
+/* Timing hooks (off by default): when on, every launch on the context's
+ * stream is bracketed by CUDA events and tagged with its class and its
+ * algorithmic FP64/tensor flops.  sldqmc_profile_read synchronises the
+ * stream and returns, per class, the launch count, the summed event time
+ * (ms) and the summed algorithmic flops, then clears the record. */
+int sldqmc_profile_enable(sldqmc_ctx *ctx, int on);
+int sldqmc_profile_read(sldqmc_ctx *ctx, long long *launches, double *ms, double *flops);
 
 #ifdef __cplusplus
 }

@@ -156,6 +156,16 @@ GemmF64 gemm_desc(int M, int N, int K, const double *A, long long lda, long long
     return g;
 }
 
+double gemm_flops(const GemmF64 &g)
+{
+    const double M = g.M, N = g.N, K = g.K;
+    double f;
+    if (g.c_upper) f = K * M * (M + 1.0);       // upper triangle of a square C
+    else if (g.a_upper) f = N * K * (K + 1.0);  // triangular A (square)
+    else f = 2.0 * M * N * K;
+    return f * g.batch;
+}
+
 void gemm_f64(const GemmF64 &g, bool TA, bool TB, cudaStream_t st)
 {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;

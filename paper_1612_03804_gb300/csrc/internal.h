@@ -6,6 +6,8 @@
 
 #include <vector>
 
+struct sldqmc_ctx;
+
 #include "sldqmc.h"
 
 namespace sldqmc {
@@ -50,6 +52,8 @@ struct GemmF64 {
 };
 
 void gemm_f64(const GemmF64 &g, bool TA, bool TB, cudaStream_t st);
+// Algorithmic flops of a GEMM description (triangles counted once).
+double gemm_flops(const GemmF64 &g);
 GemmF64 gemm_desc(int M, int N, int K, const double *A, long long lda, long long sA,
                   const double *B, long long ldb, long long sB, double *C, long long ldc,
                   long long sC, int batch);
@@ -57,6 +61,25 @@ GemmF64 gemm_desc(int M, int N, int K, const double *A, long long lda, long long
 // Mixed-precision slice GEMM (tensor cores, tcgen05): C = A * E with the
 // same scale options as the FP64 GEMM's chain use.  Defined in tc_gemm.cu.
 struct ChainTC;
+
+// Event-bracketed timing of launches (sldqmc_profile_*).
+struct ProfRec {
+    cudaEvent_t a, b;
+    int cls;
+    double flops;
+};
+struct Prof {
+    bool on = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    int open_cls = -1;
+    double open_flops = 0.0;
+};
+void prof_begin(sldqmc_ctx *c, int cls, double flops);
+void prof_end(sldqmc_ctx *c);
+// Launch an FP64 GEMM on the context's stream (counted and, when on, timed).
+void gemm_ctx(sldqmc_ctx *c, const GemmF64 &g, bool TA, bool TB);
 
 }  // namespace sldqmc
 
@@ -99,4 +122,5 @@ struct sldqmc_ctx {
     long long *d_feat0, *d_feat1;
     double *d_Jdev;
     int *d_offdev, *d_noffdev;
+    sldqmc::Prof *prof;
 };

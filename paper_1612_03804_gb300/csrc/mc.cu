@@ -375,7 +375,9 @@ void launch_local_flips(sldqmc_ctx *c, double *Gp, double *Gm, int8_t *d_s, int 
     a.dtxi = c->p.dtau * c->p.xi; a.dtauJ = c->dtauJ; a.Kt = c->Ktau; a.stats = stats;
     size_t sh = sizeof(double) * 4 * (size_t)c->N;
     int nt = c->N * c->N >= 512 ? 512 : 256;
+    prof_begin(c, SLDQMC_KC_LOCAL, 0.0);
     k_local_flips<<<B, nt, sh, c->st>>>(a);
+    prof_end(c);
     c->launches++;
 }
 
@@ -403,6 +405,7 @@ void launch_eff_sweeps(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t
 {
     const long long V = (long long)c->N * c->M;
     const int nt = 1024;
+    prof_begin(c, SLDQMC_KC_EFF, 0.0);
     if (V <= 200 * 1024) {
         k_eff_sweeps<true><<<B, nt, (size_t)V, c->st>>>(d_s, c->p.Lx, c->p.Ly, c->M, c->p.beta,
                                                         c->n_class, c->d_col_start, c->d_col_sites,
@@ -413,6 +416,7 @@ void launch_eff_sweeps(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t
                                                  c->d_col_start, c->d_col_sites, c->n_colors, n_sweeps,
                                                  seed, step, dir, n_accept, n_margin);
     }
+    prof_end(c);
     c->launches++;
 }
 

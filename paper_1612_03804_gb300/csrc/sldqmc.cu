@@ -45,6 +45,43 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
 
 using namespace sldqmc;
 
+namespace sldqmc {
+
+void prof_begin(sldqmc_ctx *c, int cls, double flops)
+{
+    Prof *p = c->prof;
+    if (!p || !p->on) return;
+    while (p->pool.size() < p->used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { p->on = false; return; }
+        p->pool.push_back(e);
+    }
+    cudaEvent_t a = p->pool[p->used], b = p->pool[p->used + 1];
+    p->used += 2;
+    cudaEventRecord(a, c->st);
+    p->recs.push_back(ProfRec{a, b, cls, flops});
+    p->open_cls = cls;
+}
+
+void prof_end(sldqmc_ctx *c)
+{
+    Prof *p = c->prof;
+    if (!p || !p->on || p->open_cls < 0) return;
+    cudaEventRecord(p->recs.back().b, c->st);
+    p->open_cls = -1;
+}
+
+void gemm_ctx(sldqmc_ctx *c, const GemmF64 &g, bool TA, bool TB)
+{
+    const bool timed = c->prof && c->prof->on;
+    if (timed) prof_begin(c, SLDQMC_KC_GEMM_F64, gemm_flops(g));
+    gemm_f64(g, TA, TB, c->st);
+    if (timed) prof_end(c);
+    c->launches++;
+}
+
+}  // namespace sldqmc
+
 namespace {
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -163,8 +200,7 @@ int weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, int tau0, doubl
                 g.cu = cu; g.cd = cd;
                 if (j == 0) { g.s_k = d_s + (long long)slice * N; g.sSk = (long long)M * N; }
                 if (j < nb - 1) { g.s_n = d_s + (long long)((tau0 + m + j + 1) % M) * N; g.sSn = (long long)M * N; }
-                gemm_f64(g, false, false, c->st);
-                c->launches++;
+                gemm_ctx(c, g, false, false);
                 cur = outs[o];
                 o ^= 1;
             }
@@ -320,6 +356,10 @@ void sldqmc_destroy(sldqmc_ctx *c)
     if (!c) return;
     cudaStreamSynchronize(c->st);
     tc_release(c);
+    if (c->prof) {
+        for (cudaEvent_t e : c->prof->pool) cudaEventDestroy(e);
+        delete c->prof;
+    }
     cudaFree(c->d_flag);
     cudaFree(c->d_K);
     cudaFree(c->buf[0]);
@@ -368,6 +408,7 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     }
     c->dtauJ = p->dtau * p->J_ising;
     c->Ktau = -0.5 * log(tanh(p->dtau * p->h));
+    c->prof = new Prof();
     int rc = SLDQMC_OK;
     const size_t nn = (size_t)c->nn, cap = (size_t)c->cap;
     if ((rc = dalloc(&c->d_flag, 1))) goto fail;
@@ -574,10 +615,9 @@ static int fresh_gt(sldqmc_ctx *c, const int8_t *d_s, int B, int tau1, double *d
         int rc = weight_run(c, d_s, B, f == 0 ? 1 : -1, tau1 % c->M, c->d_ld_tmp2, nullptr, Gt, 1.0, 0);
         if (rc) return rc;
         GemmF64 g = gemm_desc(N, N, N, c->d_Einv, N, 0, Gt, N, nn, T, N, nn, B);
-        gemm_f64(g, false, false, c->st);
+        gemm_ctx(c, g, false, false);
         GemmF64 h = gemm_desc(N, N, N, T, N, nn, c->d_E, N, 0, dst[f], N, nn, B);
-        gemm_f64(h, false, false, c->st);
-        c->launches += 2;
+        gemm_ctx(c, h, false, false);
     }
     return SLDQMC_OK;
 }
@@ -595,12 +635,11 @@ static void wrap_gt(sldqmc_ctx *c, const int8_t *d_s, int B, int tau, double *sr
         GemmF64 g = gemm_desc(N, N, N, src[f], N, nn, c->d_Einv, N, 0, T, N, nn, B);
         g.s_n = d_s + (long long)tau * N; g.sSn = (long long)M * N;
         g.cu = 1.0 / cu; g.cd = 1.0 / cd;
-        gemm_f64(g, false, false, c->st);
+        gemm_ctx(c, g, false, false);
         GemmF64 h = gemm_desc(N, N, N, c->d_E, N, 0, T, N, nn, dst[f], N, nn, B);
         h.s_m = d_s + (long long)tau * N; h.sSm = (long long)M * N;
         h.cu = cu; h.cd = cd;
-        gemm_f64(h, false, false, c->st);
-        c->launches += 2;
+        gemm_ctx(c, h, false, false);
     }
 }
 
@@ -888,6 +927,57 @@ int sldqmc_cumulative_update(sldqmc_ctx *c, int8_t *s, double *logw, int n_eff, 
     *logw = hl[0];
     if (accepted) *accepted = ha;
     if (log_r) *log_r = hl[1];
+    return SLDQMC_OK;
+}
+
+int sldqmc_cumulative_batch(sldqmc_ctx *c, int8_t *s, double *logw, int B, int n_eff, uint64_t seed, uint32_t step0,
+                            int n_steps, int *accepts)
+{
+    if (!c || !c->have_model || !s || !logw || B < 1 || B > c->cap || n_eff < 0 || n_steps < 0) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    if (!host_field_ok(s, V * B)) return SLDQMC_ERR_ARG;
+    int8_t *ds = c->d_s_one;
+    double *dl = c->d_ld_tmp2;
+    int *dacc = c->d_sg_tmp + c->cap;
+    if (cudaMemcpyAsync(ds, s, (size_t)(V * B), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(dl, logw, sizeof(double) * B, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+        return SLDQMC_ERR_CUDA;
+    cudaMemsetAsync(dacc, 0, sizeof(int) * B, c->st);
+    int rc = sldqmc_cumulative_batch_dev(c, ds, dl, B, n_eff, seed, step0, n_steps, dacc, nullptr);
+    if (rc) return rc;
+    std::vector<int> ha(B);
+    if (cudaMemcpyAsync(s, ds, (size_t)(V * B), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(logw, dl, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(ha.data(), dacc, sizeof(int) * B, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        return SLDQMC_ERR_CUDA;
+    rc = sync_and_flag(c);
+    if (rc) return rc;
+    if (accepts)
+        for (int b = 0; b < B; ++b) accepts[b] += ha[b];
+    return SLDQMC_OK;
+}
+
+int sldqmc_profile_enable(sldqmc_ctx *c, int on)
+{
+    if (!c || !c->prof) return SLDQMC_ERR_ARG;
+    c->prof->on = on != 0;
+    return SLDQMC_OK;
+}
+
+int sldqmc_profile_read(sldqmc_ctx *c, long long *launches, double *ms, double *flops)
+{
+    if (!c || !c->prof || !launches || !ms || !flops) return SLDQMC_ERR_ARG;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    for (int k = 0; k < SLDQMC_KC_COUNT; ++k) { launches[k] = 0; ms[k] = 0.0; flops[k] = 0.0; }
+    for (const ProfRec &r : c->prof->recs) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return SLDQMC_ERR_CUDA;
+        launches[r.cls] += 1;
+        ms[r.cls] += t;
+        flops[r.cls] += r.flops;
+    }
+    c->prof->recs.clear();
+    c->prof->used = 0;
     return SLDQMC_OK;
 }
 

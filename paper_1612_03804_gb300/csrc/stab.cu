@@ -430,7 +430,9 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
         int kb = N - k0 < 32 ? N - k0 : 32;
         int nW = N - (k0 + kb);
         dim3 grid(cdiv(nW + N, 128), B);
+        prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
         k_chol_panel<32><<<grid, 128, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
+        prof_end(c);
         c->launches++;
         if (nW > 0) {
             // W[k0+kb:, k0+kb:] -= R_blk^T R_blk   (upper triangle only)
@@ -438,13 +440,12 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
                                   R + (long long)k0 * N + k0 + kb, N, nn,
                                   W + (long long)(k0 + kb) * N + k0 + kb, N, sW, B);
             g.alpha = -1.0; g.beta = 1.0; g.c_upper = 1;
-            gemm_f64(g, true, false, c->st);
+            gemm_ctx(c, g, true, false);
             // Y[k0+kb:, :] -= R_blk^T Qt_blk
             GemmF64 h = gemm_desc(nW, N, kb, R + (long long)k0 * N + k0 + kb, N, nn,
                                   Y + (long long)k0 * N, N, nn, Y + (long long)(k0 + kb) * N, N, nn, B);
             h.alpha = -1.0; h.beta = 1.0;
-            gemm_f64(h, true, false, c->st);
-            c->launches += 2;
+            gemm_ctx(c, h, true, false);
         }
     }
 }
@@ -460,25 +461,26 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B)
     // W = Xt Xt^T (upper triangle)
     GemmF64 g = gemm_desc(N, N, N, Xt, N, nn, Xt, N, nn, W, N, 2 * nn, B);
     g.c_upper = 1;
-    gemm_f64(g, false, true, c->st);
+    gemm_ctx(c, g, false, true);
     int Npad = 1;
     while (Npad < N) Npad <<= 1;
     size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
+    prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
     k_sort_pivot<<<B, 1024, sh, c->st>>>(W, 2 * nn, N, c->d_D, N, Npad, c->d_perm, c->d_Dp, c->d_sgn);
+    prof_end(c);
     dim3 gg(cdiv(N, 256), N, B);
     k_gather_pivot<<<gg, 256, 0, c->st>>>(W, 2 * nn, Xt, Wc, Y, nn, N, N, c->d_perm);
-    c->launches += 3;
+    c->launches += 2;
     chol_pass(c, Wc, nn, Y, R1, B);
     // second pass: W = Q1^T Q1 (as Y Y^T), upper triangle
     GemmF64 g2 = gemm_desc(N, N, N, Y, N, nn, Y, N, nn, W, N, 2 * nn, B);
     g2.c_upper = 1;
-    gemm_f64(g2, false, true, c->st);
-    c->launches++;
+    gemm_ctx(c, g2, false, true);
     chol_pass(c, W, 2 * nn, Y, R2, B);
     // R = R2 R1 into Xt's (now dead) buffer
     GemmF64 g3 = gemm_desc(N, N, N, R2, N, nn, R1, N, nn, Xt, N, nn, B);
     g3.a_upper = 1;
-    gemm_f64(g3, false, false, c->st);
+    gemm_ctx(c, g3, false, false);
     dim3 gd(cdiv(N, 256), B);
     k_new_D<<<gd, 256, 0, c->st>>>(Xt, nn, N, c->d_Dp, c->d_D, c->d_flag);
     k_gather_V<<<gg, 256, 0, c->st>>>(V, Vg, nn, N, c->d_perm, c->d_Dp);
@@ -486,8 +488,8 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B)
     GemmF64 g4 = gemm_desc(N, N, N, Xt, N, nn, Vg, N, nn, V, N, nn, B);
     g4.a_upper = 1;
     g4.ms = c->d_D; g4.sMs = N; g4.ms_recip = 1;
-    gemm_f64(g4, false, false, c->st);
-    c->launches += 4;
+    gemm_ctx(c, g4, false, false);
+    c->launches += 2;
 }
 
 // Final determinant (and optionally G) from the running U^T, D, V.
@@ -508,13 +510,17 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
     const long long sItem = (long long)N * lda;
     for (int k0 = 0; k0 < N; k0 += 32) {
         int kb = N - k0 < 32 ? N - k0 : 32;
+        prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
         k_lu_panel<<<B, 1024, 0, c->st>>>(A, sItem, lda, N, ncols, k0, kb, c->d_piv, c->d_logacc,
                                           c->d_sgn + c->cap, c->d_flag);
+        prof_end(c);
         c->launches++;
         int rest = ncols - (k0 + kb);
         if (rest > 0) {
             dim3 gt(cdiv(rest, 128), B);
+            prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
             k_lu_trsm_row<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, ncols, k0, kb);
+            prof_end(c);
             c->launches++;
             int m2 = N - (k0 + kb);
             if (m2 > 0) {
@@ -522,8 +528,7 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
                                       A + (long long)k0 * lda + k0 + kb, lda, sItem,
                                       A + (long long)(k0 + kb) * lda + k0 + kb, lda, sItem, B);
                 g.alpha = -1.0; g.beta = 1.0;
-                gemm_f64(g, false, false, c->st);
-                c->launches++;
+                gemm_ctx(c, g, false, false);
             }
         }
     }
@@ -533,14 +538,15 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
             int k0 = kbi * 32;
             int kb = N - k0 < 32 ? N - k0 : 32;
             dim3 gt(cdiv(N, 128), B);
+            prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
             k_trsm_upper_rhs<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, N, k0, kb);
+            prof_end(c);
             c->launches++;
             if (k0 > 0) {
                 GemmF64 g = gemm_desc(k0, N, kb, A + k0, lda, sItem, A + (long long)k0 * lda + N, lda,
                                       sItem, A + N, lda, sItem, B);
                 g.alpha = -1.0; g.beta = 1.0;
-                gemm_f64(g, false, false, c->st);
-                c->launches++;
+                gemm_ctx(c, g, false, false);
             }
         }
         dim3 gc(cdiv(N, 256), N, B);

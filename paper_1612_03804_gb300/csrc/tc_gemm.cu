@@ -5,15 +5,25 @@
 // the next slice (B_tau = E diag(exp(eta dtau xi s_tau))).  Both operands are
 // K-major, so the product maps directly onto tcgen05.mma:
 //
-//   3xTF32: A = A_hi + A_lo, B = B_hi + B_lo (TF32-rounded parts), and
-//           A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, three MMAs accumulated in
-//           FP32 in tensor memory;
-//   BF16:   one kind::f16 MMA with BF16 operands, FP32 accumulation.
+//   split TF32 ("3xTF32" mode): the running product is split in two TF32
+//           parts A = A_h + A_l; E, which every slice reuses, in three
+//           (E_h + E_m + E_l) so that its representation error (systematic
+//           across slices) falls to 2^-33; A E ~ A_h E_h + A_h E_m + A_l E_h
+//           + A_h E_l + A_l E_m, five kind::tf32 MMAs per K-step;
+//   BF16:   one kind::f16 MMA with BF16 operands.
 //
-// One CTA computes a 128 x 128 output tile: warp 0 drives TMA (128-byte
+// The tensor cores accumulate in FP32 with a rounding that is not
+// round-to-nearest, so the error of one accumulator grows with the number
+// of MMAs it receives.  Each CTA therefore spreads its K-steps round-robin
+// over several accumulators in tensor memory (8 x 64 columns) and adds them
+// in the epilogue; in split-TF32 mode the leading A_h E_h products use seven
+// of them and the four small correction products share the eighth.
+//
+// One CTA computes a 128 x 64 output tile: warp 0 drives TMA (128-byte
 // swizzled boxes, mbarrier completion), warp 1 issues the MMAs from one
-// thread, and all four warps drain the accumulator with tcgen05.ld and apply
-// the next slice's column scaling while re-splitting the result into the
+// thread, and all four warps drain the accumulators with tcgen05.ld and
+// apply the next slice's column scaling (as a float pair, so that the scale
+// constant adds no systematic error) while re-splitting the result into the
 // operand format of the next product (or FP64 for the stabilisation at the
 // end of the block).  Every mbarrier wait is bounded; a wait that runs out
 // raises the context's timeout flag and the CTA frees its tensor memory and
@@ -29,8 +39,10 @@ namespace sldqmc {
 
 namespace {
 
-constexpr int BM = 128, BN = 128;
-constexpr int TILE_BYTES = BM * 128;  // one operand part of one stage: 128 rows x 128 bytes
+constexpr int BM = 128, BN = 64, NACC = 8;
+constexpr int TILE_A = BM * 128;  // one A part of one stage: 128 rows x 128 bytes
+constexpr int TILE_B = BN * 128;  // one B part of one stage: 64 rows x 128 bytes
+constexpr int TMEM_COLS = BN * NACC;
 
 struct TcArgs {
     int N, ldp, nk;
@@ -40,7 +52,7 @@ struct TcArgs {
     long long s_out, s_f64;
     const int8_t *s_n;
     long long sSn;
-    float cu, cd;
+    float cu_h, cu_l, cd_h, cd_l;  // scale constants as float pairs
     int *flag;
 };
 
@@ -109,7 +121,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 128.
+// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 64.
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format)
 {
     return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -158,13 +170,18 @@ __device__ __forceinline__ float to_tf32(float x)
 }
 
 template <int MODE>
+__host__ __device__ constexpr int stages() { return MODE == 0 ? 3 : 5; }
+template <int MODE>
+__host__ __device__ constexpr int stage_bytes() { return MODE == 0 ? 2 * TILE_A + 3 * TILE_B : TILE_A + TILE_B; }
+
+template <int MODE>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
-              const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, TcArgs a)
+              const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
+              const __grid_constant__ CUtensorMap tB2, TcArgs a)
 {
-    constexpr int NPART = MODE == 0 ? 2 : 1;
-    constexpr int STAGE_BYTES = 2 * NPART * TILE_BYTES;
-    constexpr int STAGES = MODE == 0 ? 3 : 4;
+    constexpr int STAGE_BYTES = stage_bytes<MODE>();
+    constexpr int STAGES = stages<MODE>();
     constexpr int KSTEPS = 4;  // 128-byte row / 32 bytes per MMA K-step (8 TF32 or 16 BF16)
     constexpr uint32_t IDESC = instr_desc(MODE == 0 ? 2u : 1u);
 
@@ -188,7 +205,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(BN)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -205,9 +222,14 @@ __global__ void __launch_bounds__(128, 1)
             uint8_t *st = base + s * STAGE_BYTES;
             const int k0 = kb * (128 / (MODE == 0 ? 4 : 2));
             tma_load_3d(st, &tA0, k0, m0, b, &full[s]);
-            if (NPART == 2) tma_load_3d(st + TILE_BYTES, &tA1, k0, m0, b, &full[s]);
-            tma_load_2d(st + NPART * TILE_BYTES, &tB0, k0, n0, &full[s]);
-            if (NPART == 2) tma_load_2d(st + 3 * TILE_BYTES, &tB1, k0, n0, &full[s]);
+            if (MODE == 0) {
+                tma_load_3d(st + TILE_A, &tA1, k0, m0, b, &full[s]);
+                tma_load_2d(st + 2 * TILE_A, &tB0, k0, n0, &full[s]);
+                tma_load_2d(st + 2 * TILE_A + TILE_B, &tB1, k0, n0, &full[s]);
+                tma_load_2d(st + 2 * TILE_A + 2 * TILE_B, &tB2, k0, n0, &full[s]);
+            } else {
+                tma_load_2d(st + TILE_A, &tB0, k0, n0, &full[s]);
+            }
         }
     } else if (warp == 1 && lane == 0) {
         bool ok = true;
@@ -219,14 +241,24 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
             for (int k = 0; k < KSTEPS; ++k) {
                 const uint32_t off = k * 32;
+                const int g = kb * KSTEPS + k;
                 if (MODE == 0) {
-                    const uint64_t ah = smem_desc(sa + off), al = smem_desc(sa + TILE_BYTES + off);
-                    const uint64_t bh = smem_desc(sa + 2 * TILE_BYTES + off), bl = smem_desc(sa + 3 * TILE_BYTES + off);
-                    mma<0>(tmem, ah, bh, IDESC, (kb | k) != 0);
-                    mma<0>(tmem, ah, bl, IDESC, 1u);
-                    mma<0>(tmem, al, bh, IDESC, 1u);
+                    // A_h E_h round-robin over accumulators 0..6; the four small
+                    // correction products all go to accumulator 7, where their
+                    // rounding is relative to a sum 2^-11 smaller.
+                    const uint32_t acc_main = tmem + (uint32_t)((g % (NACC - 1)) * BN);
+                    const uint32_t acc_small = tmem + (uint32_t)((NACC - 1) * BN);
+                    const uint64_t ah = smem_desc(sa + off), al = smem_desc(sa + TILE_A + off);
+                    const uint32_t sb = sa + 2 * TILE_A + off;
+                    const uint64_t eh = smem_desc(sb), em = smem_desc(sb + TILE_B), el = smem_desc(sb + 2 * TILE_B);
+                    mma<0>(acc_main, ah, eh, IDESC, g < NACC - 1 ? 0u : 1u);
+                    mma<0>(acc_small, ah, em, IDESC, g == 0 ? 0u : 1u);
+                    mma<0>(acc_small, al, eh, IDESC, 1u);
+                    mma<0>(acc_small, ah, el, IDESC, 1u);
+                    mma<0>(acc_small, al, em, IDESC, 1u);
                 } else {
-                    mma<1>(tmem, smem_desc(sa + off), smem_desc(sa + TILE_BYTES + off), IDESC, (kb | k) != 0);
+                    const uint32_t acc_t = tmem + (uint32_t)((g % NACC) * BN);
+                    mma<1>(acc_t, smem_desc(sa + off), smem_desc(sa + TILE_A + off), IDESC, g < NACC ? 0u : 1u);
                 }
             }
             mma_commit(&empty[s]);
@@ -239,33 +271,55 @@ __global__ void __launch_bounds__(128, 1)
     fence_after();
     const int row = warp * 32 + lane;
     const int m = m0 + row;
+    // accumulators that received at least one MMA
+    const int ksteps = a.nk * KSTEPS;
+    const uint32_t used_mask = MODE == 0 ? (((1u << (ksteps < NACC - 1 ? ksteps : NACC - 1)) - 1u) | (1u << (NACC - 1)))
+                                         : ((1u << (ksteps < NACC ? ksteps : NACC)) - 1u);
+    const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
     for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        for (int q = 0; q < NACC; ++q) {
+            if (!((used_mask >> q) & 1u)) continue;
+            uint32_t r[16];
+            tmem_ld16(lane_base + (uint32_t)(q * BN), r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
+        }
         if (!ok || m >= a.N) continue;
-        const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
             if (n >= a.N) break;
-            float v = __uint_as_float(r[j]);
-            if (sn) v *= (sn[n] > 0 ? a.cu : a.cd);
             if (a.out_f64) {
-                a.out_f64[(long long)b * a.s_f64 + (long long)m * a.N + n] = (double)v;
-            } else if (MODE == 0) {
-                const float hi = to_tf32(v);
-                const long long o = (long long)b * a.s_out + (long long)m * a.ldp + n;
+                a.out_f64[(long long)b * a.s_f64 + (long long)m * a.N + n] = (double)v[j];
+                continue;
+            }
+            // y = v * d with d = dh + dl: yh = fl(v dh), ye = the rounding error of that
+            // product (exact by FMA) plus v dl.
+            float yh = v[j], ye = 0.0f;
+            if (sn) {
+                const bool up = sn[n] > 0;
+                const float dh = up ? a.cu_h : a.cd_h, dl = up ? a.cu_l : a.cd_l;
+                yh = v[j] * dh;
+                ye = fmaf(v[j], dh, -yh) + v[j] * dl;
+            }
+            const long long o = (long long)b * a.s_out + (long long)m * a.ldp + n;
+            if (MODE == 0) {
+                const float hi = to_tf32(yh);
                 a.out_hi[o] = hi;
-                a.out_lo[o] = to_tf32(v - hi);
+                a.out_lo[o] = to_tf32((yh - hi) + ye);
             } else {
-                a.out_bf[(long long)b * a.s_out + (long long)m * a.ldp + n] = __float2bfloat16_rn(v);
+                a.out_bf[o] = __float2bfloat16_rn(yh + ye);
             }
         }
     }
     fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
 // Operand of the first product of a block: Ut diag(d_first), split.
@@ -294,10 +348,10 @@ struct TcWs {
     size_t part_elems;  // per operand part: cap * N * ldp
     float *opf[2][2];   // [buffer][hi/lo]
     __nv_bfloat16 *opb[2];
-    float *Ehi, *Elo;
+    float *Ep[3];            // E split in three TF32 parts
     __nv_bfloat16 *Ebf;
     CUtensorMap mapA[2][2];  // [buffer][part]
-    CUtensorMap mapB[2];     // [part]
+    CUtensorMap mapB[3];     // [part]
     void *mem;
 };
 
@@ -315,14 +369,14 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
     return fn;
 }
 
-bool encode(CUtensorMap *map, void *ptr, bool bf16, int rank, int ldp, int rows, int batch)
+bool encode(CUtensorMap *map, void *ptr, bool bf16, int rank, int ldp, int rows, int batch, int box_rows)
 {
     auto fn = get_encode();
     if (!fn) return false;
     const int esz = bf16 ? 2 : 4;
     cuuint64_t dims[3] = {(cuuint64_t)ldp, (cuuint64_t)rows, (cuuint64_t)batch};
     cuuint64_t strides[2] = {(cuuint64_t)ldp * esz, (cuuint64_t)ldp * rows * esz};
-    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)BM, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
                     ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -333,7 +387,24 @@ bool encode(CUtensorMap *map, void *ptr, bool bf16, int rank, int ldp, int rows,
 template <int MODE>
 constexpr size_t smem_bytes()
 {
-    return (size_t)(MODE == 0 ? 3 : 4) * 2 * (MODE == 0 ? 2 : 1) * TILE_BYTES + 1024 + 256;
+    return (size_t)stages<MODE>() * stage_bytes<MODE>() + 1024 + 256;
+}
+
+// E = E_h + E_m + E_l, each part TF32-rounded.
+__global__ void k_split_E3(const double *E, int N, int ldp, float *h, float *mid, float *l)
+{
+    const int m = blockIdx.y;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        const double v = E[(long long)m * N + k];
+        const float a = to_tf32((float)v);
+        const double r1 = v - (double)a;
+        const float b2 = to_tf32((float)r1);
+        const float c3 = to_tf32((float)(r1 - (double)b2));
+        const long long o = (long long)m * ldp + k;
+        h[o] = a;
+        mid[o] = b2;
+        l[o] = c3;
+    }
 }
 
 }  // namespace
@@ -349,7 +420,7 @@ int tc_prepare(sldqmc_ctx *c)
     w->part_elems = (size_t)c->cap * N * w->ldp;
     const size_t esz = bf ? 2 : 4;
     const size_t parts = bf ? 2 : 4;              // operand buffers
-    const size_t eparts = bf ? 1 : 2;             // E copies
+    const size_t eparts = bf ? 1 : 3;             // E copies
     const size_t bytes = esz * (parts * w->part_elems + eparts * (size_t)N * w->ldp);
     if (cudaMalloc(&w->mem, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -364,14 +435,15 @@ int tc_prepare(sldqmc_ctx *c)
                 w->opf[i][p] = (float *)q;
                 q += esz * w->part_elems;
             }
-        w->Ehi = (float *)q;
-        q += esz * (size_t)N * w->ldp;
-        w->Elo = (float *)q;
+        for (int p = 0; p < 3; ++p) {
+            w->Ep[p] = (float *)q;
+            q += esz * (size_t)N * w->ldp;
+        }
         for (int i = 0; i < 2; ++i)
             for (int p = 0; p < 2; ++p)
-                if (!encode(&w->mapA[i][p], w->opf[i][p], false, 3, w->ldp, N, c->cap)) return SLDQMC_ERR_CUDA;
-        if (!encode(&w->mapB[0], w->Ehi, false, 2, w->ldp, N, 1) || !encode(&w->mapB[1], w->Elo, false, 2, w->ldp, N, 1))
-            return SLDQMC_ERR_CUDA;
+                if (!encode(&w->mapA[i][p], w->opf[i][p], false, 3, w->ldp, N, c->cap, BM)) return SLDQMC_ERR_CUDA;
+        for (int p = 0; p < 3; ++p)
+            if (!encode(&w->mapB[p], w->Ep[p], false, 2, w->ldp, N, 1, BN)) return SLDQMC_ERR_CUDA;
     } else {
         for (int i = 0; i < 2; ++i) {
             w->opb[i] = (__nv_bfloat16 *)q;
@@ -379,11 +451,11 @@ int tc_prepare(sldqmc_ctx *c)
         }
         w->Ebf = (__nv_bfloat16 *)q;
         for (int i = 0; i < 2; ++i) {
-            if (!encode(&w->mapA[i][0], w->opb[i], true, 3, w->ldp, N, c->cap)) return SLDQMC_ERR_CUDA;
+            if (!encode(&w->mapA[i][0], w->opb[i], true, 3, w->ldp, N, c->cap, BM)) return SLDQMC_ERR_CUDA;
             w->mapA[i][1] = w->mapA[i][0];
         }
-        if (!encode(&w->mapB[0], w->Ebf, true, 2, w->ldp, N, 1)) return SLDQMC_ERR_CUDA;
-        w->mapB[1] = w->mapB[0];
+        if (!encode(&w->mapB[0], w->Ebf, true, 2, w->ldp, N, 1, BN)) return SLDQMC_ERR_CUDA;
+        w->mapB[1] = w->mapB[2] = w->mapB[0];
     }
     cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<0>());
     cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1>());
@@ -407,7 +479,7 @@ void tc_convert_E(sldqmc_ctx *c)
     if (c->p.prec == SLDQMC_BF16)
         k_tc_prep<1><<<g, 256, 0, c->st>>>(c->d_E, c->nn, N, w->ldp, nullptr, 0, 1.0, 1.0, nullptr, nullptr, w->Ebf, 0);
     else
-        k_tc_prep<0><<<g, 256, 0, c->st>>>(c->d_E, c->nn, N, w->ldp, nullptr, 0, 1.0, 1.0, w->Ehi, w->Elo, nullptr, 0);
+        k_split_E3<<<g, 256, 0, c->st>>>(c->d_E, N, w->ldp, w->Ep[0], w->Ep[1], w->Ep[2]);
     c->launches++;
 }
 
@@ -444,17 +516,21 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
         } else {
             a.s_n = d_s + (long long)slices[j + 1] * N;
             a.sSn = sS;
-            a.cu = (float)cu;
-            a.cd = (float)cd;
+            a.cu_h = (float)cu;
+            a.cu_l = (float)(cu - (double)a.cu_h);
+            a.cd_h = (float)cd;
+            a.cd_l = (float)(cd - (double)a.cd_h);
             if (bf) a.out_bf = w->opb[dst];
             else { a.out_hi = w->opf[dst][0]; a.out_lo = w->opf[dst][1]; }
         }
+        prof_begin(c, SLDQMC_KC_GEMM_TC, 2.0 * (double)N * N * N * B);
         if (bf)
             k_tc_gemm<1><<<grid, 128, smem_bytes<1>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
-                                                                w->mapB[1], a);
+                                                                w->mapB[1], w->mapB[2], a);
         else
             k_tc_gemm<0><<<grid, 128, smem_bytes<0>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
-                                                                w->mapB[1], a);
+                                                                w->mapB[1], w->mapB[2], a);
+        prof_end(c);
         c->launches++;
     }
 }

@@ -85,6 +85,9 @@ def load(path=None):
         "sldqmc_cumulative_batch_dev": ([vp, vp, vp, i, i, u64, u32, i, vp, vp], i),
         "sldqmc_log_weight_batch_dev": ([vp, vp, i, vp], i),
         "sldqmc_kernel_launches": ([vp], ctypes.c_longlong),
+        "sldqmc_cumulative_batch": ([vp, vp, vp, i, i, u64, u32, i, vp], i),
+        "sldqmc_profile_enable": ([vp, i], i),
+        "sldqmc_profile_read": ([vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -268,6 +271,26 @@ class Context:
         _chk(load().sldqmc_cumulative_batch_dev(self.h, _tp(d_s), _tp(d_logw), int(d_s.shape[0]), int(n_eff),
                                                 ctypes.c_uint64(seed), ctypes.c_uint32(step0), int(n_steps),
                                                 _tp(d_accepts), _tp(d_log_r)), "cumulative_batch_dev")
+
+    def cumulative_batch(self, s, logw, n_eff, seed, step0, n_steps, accepts):
+        """Host buffers (numpy, updated in place): s (B,M,N) int8, logw (B,), accepts (B,) int32."""
+        _chk(load().sldqmc_cumulative_batch(self.h, _p(s), _p(logw), int(s.shape[0]), int(n_eff),
+                                            ctypes.c_uint64(seed), ctypes.c_uint32(step0), int(n_steps),
+                                            _p(accepts)), "cumulative_batch")
+
+    KERNEL_CLASSES = ("gemm_f64", "gemm_tc", "panel_f64", "eff_sweep", "local_flips", "other")
+
+    def profile(self, on):
+        _chk(load().sldqmc_profile_enable(self.h, int(bool(on))), "profile_enable")
+
+    def profile_read(self):
+        n = len(self.KERNEL_CLASSES)
+        la = np.zeros(n, dtype=np.int64)
+        ms = np.zeros(n)
+        fl = np.zeros(n)
+        _chk(load().sldqmc_profile_read(self.h, _p(la), _p(ms), _p(fl)), "profile_read")
+        return {k: dict(launches=int(la[i]), ms=float(ms[i]), flops=float(fl[i]))
+                for i, k in enumerate(self.KERNEL_CLASSES)}
 
     def sync(self):
         _chk(load().sldqmc_sync(self.h), "sync")
