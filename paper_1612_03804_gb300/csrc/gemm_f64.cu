@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g)
 
     int kbeg = 0;
     if (g.a_upper) kbeg = (m0 / BK) * BK;
-    const int K = g.K;
+    int K = g.K;
+    if (g.b_upper && n0 + BN < K) K = n0 + BN;
 
     double ra[4], rb[4];
     auto load = [&](int k0) {
@@ -161,6 +162,7 @@ double gemm_flops(const GemmF64 &g)
     const double M = g.M, N = g.N, K = g.K;
     double f;
     if (g.c_upper) f = K * M * (M + 1.0);       // upper triangle of a square C
+    else if (g.a_upper && g.b_upper) f = K * (K + 1.0) * (K + 2.0) / 3.0;  // upper x upper
     else if (g.a_upper) f = N * K * (K + 1.0);  // triangular A (square)
     else f = 2.0 * M * N * K;
     return f * g.batch;

@@ -47,6 +47,7 @@ struct GemmF64 {
     long long sMs;
     int ms_recip;
     int a_upper;
+    int b_upper;  // op(B) upper triangular (op(B)[k][n] = 0 for k > n): skip those k
     int c_upper;
     int batch;
 };

@@ -16,7 +16,7 @@
 namespace sldqmc {
 // stab.cu
 void launch_init_udv(sldqmc_ctx *c, double *Ut, double *V, int B);
-void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B);
+void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B, int passes);
 void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign, double *d_G,
               double scale, int accumulate);
 // mc.cu
@@ -211,7 +211,7 @@ int weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, int tau0, doubl
             tc_chain_block(c, Ut, d_s, B, cu, cd, slices.data(), nb, X1, X2, Yb);
             Xt = X1;
         }
-        stabilize(c, Xt, Ut, Yb, B);
+        stabilize(c, Xt, Ut, Yb, B, m + nb >= M ? 2 : 1);
         std::swap(Ut, Yb);
     }
     finalize(c, Ut, B, d_ld, d_sign, d_G, scale, accumulate);

@@ -452,7 +452,11 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
 
 // Re-factorise X (given as Xt = X^T) against the running D and V.
 // On return: the new U^T is in *Y (caller swaps buffers), D and V updated.
-void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B)
+// passes = 1: one Cholesky-QR pass, Q orthogonal to O(kappa(X)^2 eps).  The
+// U D V representation stays exact whatever the orthogonality of U; only the
+// final U must be orthogonal to working precision (the finalisation uses
+// U^T as U^{-1}), so the last block of a chain takes passes = 2.
+void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B, int passes)
 {
     const int N = c->N;
     const long long nn = c->nn;
@@ -472,20 +476,24 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B)
     k_gather_pivot<<<gg, 256, 0, c->st>>>(W, 2 * nn, Xt, Wc, Y, nn, N, N, c->d_perm);
     c->launches += 2;
     chol_pass(c, Wc, nn, Y, R1, B);
-    // second pass: W = Q1^T Q1 (as Y Y^T), upper triangle
-    GemmF64 g2 = gemm_desc(N, N, N, Y, N, nn, Y, N, nn, W, N, 2 * nn, B);
-    g2.c_upper = 1;
-    gemm_ctx(c, g2, false, true);
-    chol_pass(c, W, 2 * nn, Y, R2, B);
-    // R = R2 R1 into Xt's (now dead) buffer
-    GemmF64 g3 = gemm_desc(N, N, N, R2, N, nn, R1, N, nn, Xt, N, nn, B);
-    g3.a_upper = 1;
-    gemm_ctx(c, g3, false, false);
+    const double *R = R1;
+    if (passes == 2) {
+        // second pass: W = Q1^T Q1 (as Y Y^T), upper triangle; Q = Q1 R2^{-1}, R = R2 R1
+        GemmF64 g2 = gemm_desc(N, N, N, Y, N, nn, Y, N, nn, W, N, 2 * nn, B);
+        g2.c_upper = 1;
+        gemm_ctx(c, g2, false, true);
+        chol_pass(c, W, 2 * nn, Y, R2, B);
+        GemmF64 g3 = gemm_desc(N, N, N, R2, N, nn, R1, N, nn, Xt, N, nn, B);
+        g3.a_upper = 1;
+        g3.b_upper = 1;
+        gemm_ctx(c, g3, false, false);
+        R = Xt;
+    }
     dim3 gd(cdiv(N, 256), B);
-    k_new_D<<<gd, 256, 0, c->st>>>(Xt, nn, N, c->d_Dp, c->d_D, c->d_flag);
+    k_new_D<<<gd, 256, 0, c->st>>>(R, nn, N, c->d_Dp, c->d_D, c->d_flag);
     k_gather_V<<<gg, 256, 0, c->st>>>(V, Vg, nn, N, c->d_perm, c->d_Dp);
     // V = D^{-1} R Vg
-    GemmF64 g4 = gemm_desc(N, N, N, Xt, N, nn, Vg, N, nn, V, N, nn, B);
+    GemmF64 g4 = gemm_desc(N, N, N, R, N, nn, Vg, N, nn, V, N, nn, B);
     g4.a_upper = 1;
     g4.ms = c->d_D; g4.sMs = N; g4.ms_recip = 1;
     gemm_ctx(c, g4, false, false);
