@@ -173,6 +173,13 @@ int sldqmc_fit_effective_action(sldqmc_ctx *ctx, const int8_t *cfgs, const doubl
 int sldqmc_eff_sweeps(sldqmc_ctx *ctx, int8_t *s, int n_sweeps, uint64_t seed, uint32_t step,
                       int dir, long long *n_accept);
 
+/* Batched effective-model sweeps on device buffers (stream-ordered): chain
+ * b of d_s (B*M*N) uses key seed + (b << 32); dir = 0/1 fixes the colour
+ * order, dir = -1 draws it per chain from counter (0,0,step,3).
+ * d_accepts: B long longs incremented by the accepted flips (may be NULL). */
+int sldqmc_eff_sweeps_batch_dev(sldqmc_ctx *ctx, int8_t *d_s, int B, int n_sweeps, uint64_t seed,
+                                uint32_t step, int dir, long long *d_accepts);
+
 /* Cumulative update (steps iii + iv, acceptance Eq. 4): proposes C' by
  * n_eff effective sweeps from C (direction bit from Philox counter
  * (0,0,step,3)), evaluates log omega(C') exactly (two flavours, FP64

@@ -874,6 +874,16 @@ int sldqmc_eff_sweeps(sldqmc_ctx *c, int8_t *s, int n_sweeps, uint64_t seed, uin
     return SLDQMC_OK;
 }
 
+int sldqmc_eff_sweeps_batch_dev(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t seed, uint32_t step,
+                                int dir, long long *d_accepts)
+{
+    if (!c || !c->have_model || !d_s || B < 1 || n_sweeps < 0 || dir < -1 || dir > 1) return SLDQMC_ERR_ARG;
+    const long long V = (long long)c->N * c->M;
+    launch_check_field(c, d_s, V * B);
+    launch_eff_sweeps(c, d_s, B, n_sweeps, seed, step, dir, d_accepts, nullptr);
+    return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
+}
+
 int sldqmc_cumulative_batch_dev(sldqmc_ctx *c, int8_t *d_s, double *d_logw, int B, int n_eff, uint64_t seed,
                                 uint32_t step0, int n_steps, int *d_accepts, double *d_log_r)
 {

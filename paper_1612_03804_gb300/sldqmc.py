@@ -87,6 +87,7 @@ def load(path=None):
         "sldqmc_kernel_launches": ([vp], ctypes.c_longlong),
         "sldqmc_cumulative_batch": ([vp, vp, vp, i, i, u64, u32, i, vp], i),
         "sldqmc_profile_enable": ([vp, i], i),
+        "sldqmc_eff_sweeps_batch_dev": ([vp, vp, i, i, u64, u32, i, vp], i),
         "sldqmc_profile_read": ([vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
@@ -266,6 +267,11 @@ class Context:
                                                  ctypes.c_uint64(sweep0), int(n_sweeps),
                                                  st if want_stats else None), "local_sweep_batch_dev")
         return [x.as_dict() for x in st] if want_stats else None
+
+    def eff_sweeps_batch_dev(self, d_s, n_sweeps, seed, step, direction=-1, d_accepts=None):
+        _chk(load().sldqmc_eff_sweeps_batch_dev(self.h, _tp(d_s), int(d_s.shape[0]), int(n_sweeps),
+                                                ctypes.c_uint64(seed), ctypes.c_uint32(step), int(direction),
+                                                _tp(d_accepts)), "eff_sweeps_batch_dev")
 
     def cumulative_batch_dev(self, d_s, d_logw, n_eff, seed, step0, n_steps, d_accepts, d_log_r=None):
         _chk(load().sldqmc_cumulative_batch_dev(self.h, _tp(d_s), _tp(d_logw), int(d_s.shape[0]), int(n_eff),

@@ -153,3 +153,25 @@ def test_cumulative_batch_dev_equals_single_chains():
         np.testing.assert_array_equal(out[b], s)
         assert acc[b] == na
         assert abs(lw_out[b] - lw) <= 1e-9 * abs(lw)
+
+
+def test_eff_sweeps_batch_dev_matches_oracle():
+    import torch
+    m = O.Model(6, 4, beta=2.0, dtau=0.1)
+    fields = batch_uniform(21, 3, m.M, m.N)
+    seed, step = 31, 5
+    with _ctx(m, 10, max_batch=3) as ctx:
+        ctx.set_effective_model(CLASSES, J_EFF)
+        d_s = torch.from_numpy(fields).cuda()
+        d_acc = torch.zeros(3, dtype=torch.int64, device="cuda")
+        ctx.eff_sweeps_batch_dev(d_s, 2, seed, step, -1, d_acc)
+        ctx.sync()
+        out = d_s.cpu().numpy()
+        acc = d_acc.cpu().numpy()
+    for b in range(3):
+        key = seed + (b << 32)
+        direction = int(O.lib().or_random_word(key, 0, 0, step, 3)) & 1
+        so, na, mg = O.eff_sweeps(m, fields[b], CLASSES, J_EFF, 2, seed=key, step=step, direction=direction)
+        assert mg == 0
+        np.testing.assert_array_equal(out[b], so)
+        assert acc[b] == na
