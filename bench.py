@@ -8,6 +8,11 @@ J_tau couplings, fitted (Eq. 3) on local-DQMC configurations of an 8x8
 lattice at the same couplings and transferred to 16x16, as the paper does
 with its L=8 fit.
 
+Training (untimed): 8x8 chains are pre-thermalised by effective sweeps of
+the bare Ising action, run 20 local-DQMC sweeps, then contribute one
+configuration per sweep until 2000 are collected.  The 16x16 chains start in
+equilibrium of the fitted H_eff (300 effective sweeps) before the warm-up.
+
 One step = one cumulative update (steps iii+iv) of B independent chains:
 one sweep of N*M effective-model flips per chain, the exact log weight of
 every proposal (two flavours -> 2B fermion-weight evaluations through the
@@ -187,13 +192,26 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def bare_couplings():
+    """The bare Ising action log phi as an effective model over the same classes:
+    -beta H = dtau J f_1 + K_tau f_tau, K_tau = -ln tanh(dtau h) / 2."""
+    import math
+    kt = -0.5 * math.log(math.tanh(WL["dtau"] * WL["h"]))
+    return [-WL["dtau"] * WL["J"] / WL["beta"], 0.0, 0.0, -kt / WL["beta"]]
+
+
 def train_effective_model(torch, sldqmc, args, dev_seed):
-    """Steps i-ii: local DQMC on 8x8 at the workload couplings, then the Eq. 3 fit."""
+    """Steps i-ii: local DQMC on 8x8 at the workload couplings (started from
+    configurations pre-thermalised under the bare Ising action), then the Eq. 3 fit."""
+    import numpy as np
     from paper_1612_03804_gb300.inputs import batch_uniform
     Bt = args.train_chains
     ctx8 = sldqmc.Context(8, 8, t=WL["t"], mu=WL["mu"], xi=WL["xi"], beta=WL["beta"], dtau=WL["dtau"],
                           n_wrap=WL["n_wrap"], J=WL["J"], h=WL["h"], prec="fp64", max_batch=Bt)
     s = torch.from_numpy(batch_uniform(dev_seed, Bt, ctx8.M, ctx8.N)).cuda()
+    ctx8.set_effective_model(CLASSES, np.array(bare_couplings()))
+    for k in range(args.bare_sweeps):
+        ctx8.eff_sweeps_batch_dev(s, 1, dev_seed, k, -1)
     ctx8.local_sweep_batch_dev(s, dev_seed, 0, args.thermalize, want_stats=False)
     cfgs = []
     sweep = args.thermalize
@@ -203,7 +221,6 @@ def train_effective_model(torch, sldqmc, args, dev_seed):
         cfgs.append(s.cpu().numpy().copy())
     import numpy as np
     cfgs = np.concatenate(cfgs)[: args.train_configs]
-    ctx8.set_effective_model(CLASSES, np.zeros(len(CLASSES)))
     J, E0, r2 = ctx8.fit_effective_action(cfgs)
     ctx8.close()
     return J, E0, r2, len(cfgs)
@@ -272,9 +289,13 @@ def run_ours(args):
     d_s = torch.from_numpy(batch_uniform(5000 + rank, B, ctx.M, ctx.N)).cuda()
     d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
     d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+    # start the chains in equilibrium of H_eff (cheap effective sweeps), where
+    # the fitted model is accurate, then compute their exact log weights
+    for k in range(args.eff_thermalize):
+        ctx.eff_sweeps_batch_dev(d_s, 1, seed ^ 0x5A5A, k, -1)
     ctx.log_weight_batch_dev(d_s, d_lw)
     ctx.sync()
-    # warm-up (also thermalises the chains under the cumulative update)
+    # warm-up cumulative updates
     for w in range(args.warmup):
         ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, w, 1, d_acc)
     ctx.sync()
@@ -404,6 +425,8 @@ def main():
     ap.add_argument("--train-configs", type=int, default=2000)
     ap.add_argument("--train-chains", type=int, default=64)
     ap.add_argument("--thermalize", type=int, default=20)
+    ap.add_argument("--bare-sweeps", type=int, default=200)
+    ap.add_argument("--eff-thermalize", type=int, default=300)
     ap.add_argument("--tau-steps", type=int, default=30)
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--skip-fp64", action="store_true")
