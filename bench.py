@@ -273,7 +273,10 @@ def run_ours(args):
         return float(t.item())
 
     t_setup = time.perf_counter()
-    J, E0, r2, ncfg = train_effective_model(torch, sldqmc, args, 7000 + rank)
+    if args.no_train:
+        J, E0, r2, ncfg = bare_couplings(), 0.0, None, 0
+    else:
+        J, E0, r2, ncfg = train_effective_model(torch, sldqmc, args, 7000 + rank)
     t_setup = time.perf_counter() - t_setup
     B = args.batch
     seed = 123456789 + (rank << 20)
@@ -430,6 +433,8 @@ def main():
     ap.add_argument("--tau-steps", type=int, default=30)
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--no-train", action="store_true",
+                    help="use the bare Ising couplings as H_eff (no local-DQMC training; for profiling runs)")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
