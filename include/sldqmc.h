@@ -211,6 +211,29 @@ int sldqmc_log_weight_batch_dev(sldqmc_ctx *ctx, const int8_t *d_s, int B, doubl
 /* Number of this library's kernels launched on the context since create. */
 long long sldqmc_kernel_launches(const sldqmc_ctx *ctx);
 
+/* Allocation-free exact weight.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc or cudaFree, such as
+ * code running under a host framework that owns the whole device heap and
+ * forbids direct allocations, or code on a latency-critical path that must
+ * not take the implicit device synchronisation of cudaFree.
+ *
+ * Computes the same log|det(1 + B_M..B_1)| and sign as
+ * sldqmc_weight_batch_dev (FP64 products only; prec must be SLDQMC_FP64),
+ * for B configurations d_s (device, B*M*N int8) into d_logabsdet and d_sign
+ * (device; d_sign may be NULL), on `stream` (NULL = legacy default stream),
+ * without a context and without allocating: its workspace is one 16 MiB
+ * file-scope device array that every device loading the library keeps until
+ * the process exits.  Problems whose workspace exceeds 16 MiB are rejected
+ * with SLDQMC_ERR_UNSUPPORTED (about 50 configurations at 8x8, 2 at 16x16;
+ * no 32x32).  The first call on a device looks up the array's device address
+ * (once per device, with that device current) and should come before any
+ * stream capture.  The call waits for its stream before returning its status.
+ * All calls share the one array and each call overwrites what the previous
+ * one left there: calls that overlap on the GPU (other host threads, other
+ * streams) race and must be serialised by the caller. */
+int sldqmc_weight_noalloc(const sldqmc_params *p, void *stream, const int8_t *d_s, int B, int eta,
+                          double *d_logabsdet, int *d_sign);
+
 /* Kernel classes for the timing hooks below. */
 #define SLDQMC_KC_GEMM_F64 0   /* FP64 GEMM (slice products in FP64 mode, Gram, trailing updates) */
 #define SLDQMC_KC_GEMM_TC 1    /* tensor-core slice products (3xTF32 / BF16) */

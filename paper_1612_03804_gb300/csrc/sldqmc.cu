@@ -319,6 +319,34 @@ int lstsq_mgs2(int n, int p, const std::vector<double> &A_rowmajor, const std::v
 
 }  // namespace
 
+namespace sldqmc {
+
+// Entry points for the allocation-free variant in noalloc.cu: the same
+// kernels and launch sequence as a context's weight evaluation, on
+// caller-provided workspace.
+void build_K_into(sldqmc_ctx *c, double *ring)
+{
+    const sldqmc_params *p = &c->p;
+    double *ex_p = ring, *ey_p = ex_p + p->Lx, *ex_m = ey_p + p->Ly, *ey_m = ex_m + p->Lx;
+    k_ring<<<cdiv(p->Lx, 128), 128, 0, c->st>>>(p->Lx, p->dtau * p->t, ex_p);
+    k_ring<<<cdiv(p->Ly, 128), 128, 0, c->st>>>(p->Ly, p->dtau * p->t, ey_p);
+    k_ring<<<cdiv(p->Lx, 128), 128, 0, c->st>>>(p->Lx, -p->dtau * p->t, ex_m);
+    k_ring<<<cdiv(p->Ly, 128), 128, 0, c->st>>>(p->Ly, -p->dtau * p->t, ey_m);
+    int g = cdiv(c->nn, 256);
+    if (g > 4096) g = 4096;
+    k_build_K<<<g, 256, 0, c->st>>>(p->Lx, p->Ly, p->t, p->mu, p->dtau, ex_p, ey_p, ex_m, ey_m, c->d_K, c->d_E,
+                                    c->d_Einv);
+    c->launches += 5;
+}
+
+int weight_run_into(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, double *d_ld, int *d_sign)
+{
+    launch_check_field(c, d_s, (long long)c->N * c->M * B);
+    return weight_run(c, d_s, B, eta, 0, d_ld, d_sign, nullptr, 1.0, 0);
+}
+
+}  // namespace sldqmc
+
 extern "C" {
 
 const char *sldqmc_strerror(int status)

@@ -88,6 +88,7 @@ def load(path=None):
         "sldqmc_cumulative_batch": ([vp, vp, vp, i, i, u64, u32, i, vp], i),
         "sldqmc_profile_enable": ([vp, i], i),
         "sldqmc_eff_sweeps_batch_dev": ([vp, vp, i, i, u64, u32, i, vp], i),
+        "sldqmc_weight_noalloc": ([ctypes.POINTER(Params), vp, vp, i, i, vp, vp], i),
         "sldqmc_profile_read": ([vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
