@@ -2,7 +2,8 @@
 """Benchmark of the self-learning DQMC hot path on GB300.
 
 Workload (the configuration the headline metric is quoted on): SLDQMC on a
-16x16 lattice, t=1, mu=-0.5, xi=1, beta=8, dtau=0.05 (M=160), n_wrap=10,
+16x16 lattice, t=1, mu=-0.5, xi=1, beta=8, dtau=0.05 (M=160), n_wrap from the
+autotuner (paper_1612_03804_gb300/tune.py),
 bare Ising weight J=1, h=2.774; effective action with J1/J2/J3 (space) and
 J_tau couplings, fitted (Eq. 3) on local-DQMC configurations of an 8x8
 lattice at the same couplings and transferred to 16x16, as the paper does
@@ -50,7 +51,7 @@ FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 def workload_name():
     return ("SLDQMC cumulative update, 16x16 lattice, beta=8, dtau=0.05 (M=160), mu=-0.5, xi=1, "
-            "n_wrap=10, J1/J2/J3/Jtau effective action")
+            "J1/J2/J3/Jtau effective action")
 
 
 def env_rank():
@@ -226,18 +227,25 @@ def train_effective_model(torch, sldqmc, args, dev_seed):
     return J, E0, r2, len(cfgs)
 
 
-def steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, step0, K, mags=None):
+def steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, step0, K):
     st = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for k in range(K):
         ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, step0 + k, 1, d_acc)
-        if mags is not None:
-            mags[k] = d_s.sum(dim=(1, 2), dtype=torch.int64)
     e1.record(st)
     e1.synchronize()
     return e0.elapsed_time(e1) / 1e3
+
+
+def magnetisation_series(torch, ctx, d_s, d_lw, d_acc, seed, step0, K):
+    """|total magnetisation| of every chain after each of K further (untimed) steps."""
+    out = torch.zeros((K, d_s.shape[0]), dtype=torch.float32, device="cuda")
+    for k in range(K):
+        ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, step0 + k, 1, d_acc)
+        out[k] = d_s.float().sum(dim=(1, 2)).abs()
+    return out.cpu().numpy()
 
 
 def run_ours(args):
@@ -280,10 +288,19 @@ def run_ours(args):
     t_setup = time.perf_counter() - t_setup
     B = args.batch
     seed = 123456789 + (rank << 20)
+    nwrap = {}
+    tune_log = {}
+    for prec in {args.prec, "fp64"}:
+        if args.n_wrap == "auto":
+            from paper_1612_03804_gb300.tune import autotune_nwrap
+            nwrap[prec], res = autotune_nwrap(WL["L"], WL["beta"], WL["dtau"], WL["mu"], prec, t=WL["t"], xi=WL["xi"])
+            tune_log[prec] = [[r[0], round(r[1], 2), r[2]] for r in res]
+        else:
+            nwrap[prec] = int(args.n_wrap)
 
     def make_ctx(prec):
         c = sldqmc.Context(WL["L"], WL["L"], t=WL["t"], mu=WL["mu"], xi=WL["xi"], beta=WL["beta"],
-                           dtau=WL["dtau"], n_wrap=WL["n_wrap"], J=WL["J"], h=WL["h"], prec=prec, max_batch=B)
+                           dtau=WL["dtau"], n_wrap=nwrap[prec], J=WL["J"], h=WL["h"], prec=prec, max_batch=B)
         c.set_effective_model(CLASSES, J, E0)
         return c
 
@@ -303,12 +320,11 @@ def run_ours(args):
         ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, w, 1, d_acc)
     ctx.sync()
     d_acc.zero_()
-    mags = torch.zeros((args.steps, B), dtype=torch.int64, device="cuda")
     sampler = ClockSampler(local)
     sampler.start()
     n0 = ctx.kernel_launches()
     barrier_sync()
-    T = steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, args.warmup, args.steps, mags)
+    T = steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, args.warmup, args.steps)
     barrier_sync()
     launches = ctx.kernel_launches() - n0
     clocks = sampler.stop()
@@ -317,16 +333,14 @@ def run_ours(args):
     units = 2 * B * args.steps * world
     value = units / Tmax
     accept_rate = float(d_acc.sum().item()) / (B * args.steps)
-    # decorrelation: magnetisation series over a longer (untimed) run
-    extra = args.tau_steps
-    mags_all = [mags.cpu().numpy()]
-    if extra > 0:
-        more = torch.zeros((extra, B), dtype=torch.int64, device="cuda")
-        steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, args.warmup + args.steps, extra, more)
-        mags_all.append(more.cpu().numpy())
-    series = np.concatenate(mags_all).astype(np.float64)
-    tau, window = tau_int(series)
-    samples_per_s = (B * world * args.steps / Tmax) / tau
+    # decorrelation: |magnetisation| series over a longer untimed run
+    tau, window = None, None
+    samples_per_s = None
+    if args.tau_steps > 0:
+        series = magnetisation_series(torch, ctx, d_s, d_lw, d_acc, seed, args.warmup + args.steps,
+                                      args.tau_steps).astype(np.float64)
+        tau, window = tau_int(series)
+        samples_per_s = (B * world * args.steps / Tmax) / tau
 
     # roofline: a profiled pass (CUDA events around every launch)
     ctx.profile(True)
@@ -407,7 +421,7 @@ def run_ours(args):
                           "fit": {"lattice": "8x8", "configs": ncfg, "J": [float(x) for x in J],
                                   "E0": E0, "r2": r2}, "setup_s": round(t_setup, 2)},
                "fp64": fp64, "decorrelated_samples_per_s": samples_per_s, "tau_int": tau,
-               "tau_window": window, "accept_rate": accept_rate,
+               "tau_window": window, "tau_observable": "|sum s| per chain", "accept_rate": accept_rate,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                "gpu_launches": launches}
         print(json.dumps(out), flush=True)
@@ -430,7 +444,8 @@ def main():
     ap.add_argument("--thermalize", type=int, default=20)
     ap.add_argument("--bare-sweeps", type=int, default=200)
     ap.add_argument("--eff-thermalize", type=int, default=300)
-    ap.add_argument("--tau-steps", type=int, default=30)
+    ap.add_argument("--tau-steps", type=int, default=60)
+    ap.add_argument("--n-wrap", default="auto", help="stabilisation interval, or 'auto' for the autotuner")
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-train", action="store_true",

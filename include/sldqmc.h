@@ -204,6 +204,26 @@ int sldqmc_cumulative_batch_dev(sldqmc_ctx *ctx, int8_t *d_s, double *d_logw, in
 int sldqmc_cumulative_batch(sldqmc_ctx *ctx, int8_t *s, double *logw, int B, int n_eff, uint64_t seed,
                             uint32_t step0, int n_steps, int *accepts);
 
+/* Batched uneven chains in one CUDA graph.  Captures one cumulative update
+ * of every member -- context ctxs[i] (its own lattice, beta, precision and
+ * n_wrap) with chains d_s[i] (B[i]*M_i*N_i), cached log weights d_logw[i]
+ * and accept counters d_accepts[i] -- into a single graph whose branches run
+ * concurrently on streams of their own, forked from and joined to `stream`
+ * (NULL: the graph creates a stream).  Each member keeps a device step
+ * counter starting at step0 that the graph advances, so every replay is the
+ * next step of every chain, identical to sldqmc_cumulative_batch_dev with
+ * seeds[i] and steps step0, step0+1, ...  While a graph exists its members
+ * must not be used elsewhere concurrently. */
+typedef struct sldqmc_graph sldqmc_graph;
+int sldqmc_graph_create(sldqmc_ctx *const *ctxs, int n, int8_t *const *d_s, double *const *d_logw, const int *B,
+                        int n_eff, const uint64_t *seeds, int *const *d_accepts, uint32_t step0, void *stream,
+                        sldqmc_graph **out);
+/* Replays the graph n_steps times on its stream (stream-ordered). */
+int sldqmc_graph_launch(sldqmc_graph *g, int n_steps);
+/* Waits for the graph's stream; returns the first error flag of any member. */
+int sldqmc_graph_sync(sldqmc_graph *g);
+void sldqmc_graph_destroy(sldqmc_graph *g);
+
 /* log omega = log phi + 2 ld(+1) + 2 ld(-1) for B configurations on device
  * buffers (the exact weight a cumulative update needs). */
 int sldqmc_log_weight_batch_dev(sldqmc_ctx *ctx, const int8_t *d_s, int B, double *d_logw);

@@ -124,4 +124,6 @@ struct sldqmc_ctx {
     double *d_Jdev;
     int *d_offdev, *d_noffdev;
     sldqmc::Prof *prof;
+    const uint32_t *step_dev;  // when set (graph capture), kernels read the MC step from here
+    uint32_t *d_step;          // this context's device step counter
 };

@@ -222,8 +222,10 @@ __global__ void __launch_bounds__(1024) k_eff_sweeps(int8_t *s_all, int Lx, int 
                                                      int n_class, const int *col_start,
                                                      const int *col_sites, int n_colors, int n_sweeps,
                                                      uint64_t seed, uint32_t step, int dir_fixed,
-                                                     long long *n_accept, long long *n_margin)
+                                                     long long *n_accept, long long *n_margin,
+                                                     const uint32_t *d_step)
 {
+    if (d_step) step = *d_step;  // graph replays read the step from device memory
     const int b = blockIdx.x;
     const int N = Lx * Ly;
     const int V = N * M;
@@ -318,8 +320,10 @@ __global__ void k_features(const int8_t *s_all, int Lx, int Ly, int M, int n_cla
 //   log r = [lw1 - lw0] - [-beta sum_c J_c (f1_c - f0_c)],  accept iff log u < log r.
 __global__ void k_cumulative_accept(const double *lw1, double *lw0, const long long *f0, const long long *f1,
                                     int n_class, double beta, uint64_t seed, uint32_t step, int B,
-                                    int *accepted, int *accept_count, double *log_r, long long *margin)
+                                    int *accepted, int *accept_count, double *log_r, long long *margin,
+                                    const uint32_t *d_step)
 {
+    if (d_step) step = *d_step;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     double acc = 0.0;
@@ -410,11 +414,11 @@ void launch_eff_sweeps(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t
         k_eff_sweeps<true><<<B, nt, (size_t)V, c->st>>>(d_s, c->p.Lx, c->p.Ly, c->M, c->p.beta,
                                                         c->n_class, c->d_col_start, c->d_col_sites,
                                                         c->n_colors, n_sweeps, seed, step, dir,
-                                                        n_accept, n_margin);
+                                                        n_accept, n_margin, c->step_dev);
     } else {
         k_eff_sweeps<false><<<B, nt, 0, c->st>>>(d_s, c->p.Lx, c->p.Ly, c->M, c->p.beta, c->n_class,
                                                  c->d_col_start, c->d_col_sites, c->n_colors, n_sweeps,
-                                                 seed, step, dir, n_accept, n_margin);
+                                                 seed, step, dir, n_accept, n_margin, c->step_dev);
     }
     prof_end(c);
     c->launches++;
@@ -431,7 +435,8 @@ void launch_cumulative_accept(sldqmc_ctx *c, const double *lw1, double *lw0, con
                               int *accept_count, double *log_r, long long *margin)
 {
     k_cumulative_accept<<<cdiv(B, 128), 128, 0, c->st>>>(lw1, lw0, f0, f1, c->n_class, c->p.beta, seed,
-                                                        step, B, accepted, accept_count, log_r, margin);
+                                                        step, B, accepted, accept_count, log_r, margin,
+                                                        c->step_dev);
     c->launches++;
 }
 
@@ -440,6 +445,14 @@ void launch_commit(sldqmc_ctx *c, int8_t *d_s, const int8_t *d_sp, const int *ac
     const long long V = (long long)c->N * c->M;
     dim3 g(cdiv(V, 256) < 64 ? cdiv(V, 256) : 64, B);
     k_commit<<<g, 256, 0, c->st>>>(d_s, d_sp, accepted, V);
+    c->launches++;
+}
+
+__global__ void k_step_advance(uint32_t *d_step) { *d_step += 1u; }
+
+void launch_step_advance(sldqmc_ctx *c, uint32_t *d_step)
+{
+    k_step_advance<<<1, 1, 0, c->st>>>(d_step);
     c->launches++;
 }
 

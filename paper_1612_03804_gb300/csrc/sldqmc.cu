@@ -34,6 +34,7 @@ void launch_cumulative_accept(sldqmc_ctx *c, const double *lw1, double *lw0, con
                               int *accept_count, double *log_r, long long *margin);
 void launch_commit(sldqmc_ctx *c, int8_t *d_s, const int8_t *d_sp, const int *accepted, int B);
 void set_eff_smem_limits();
+void launch_step_advance(sldqmc_ctx *c, uint32_t *d_step);
 void stab_set_limits(int Npad);
 // tc_gemm.cu
 void tc_convert_E(sldqmc_ctx *c);
@@ -317,6 +318,27 @@ int lstsq_mgs2(int n, int p, const std::vector<double> &A_rowmajor, const std::v
     return SLDQMC_OK;
 }
 
+// One cumulative update (steps iii + iv) of B chains, stream-ordered: copy,
+// effective sweeps, features, exact log weight of the proposal, Eq. 4
+// acceptance, commit.
+int cumulative_step(sldqmc_ctx *c, int8_t *d_s, double *d_logw, int B, int n_eff, uint64_t seed, uint32_t step,
+                    int *d_accepts, double *d_log_r)
+{
+    const long long V = (long long)c->N * c->M;
+    int8_t *sp = c->d_s_tmp;
+    int *accepted = c->d_sg_tmp;  // B ints of scratch (2*cap available)
+    cudaMemcpyAsync(sp, d_s, (size_t)(V * B), cudaMemcpyDeviceToDevice, c->st);
+    launch_eff_sweeps(c, sp, B, n_eff, seed, step, -1, nullptr, nullptr);
+    launch_features(c, d_s, B, c->d_feat0);
+    launch_features(c, sp, B, c->d_feat1);
+    int rc = log_weight_run(c, sp, B, c->d_ld_tmp);
+    if (rc) return rc;
+    launch_cumulative_accept(c, c->d_ld_tmp, d_logw, c->d_feat0, c->d_feat1, seed, step, B, accepted, d_accepts,
+                             d_log_r, nullptr);
+    launch_commit(c, d_s, sp, accepted, B);
+    return SLDQMC_OK;
+}
+
 }  // namespace
 
 namespace sldqmc {
@@ -400,6 +422,7 @@ void sldqmc_destroy(sldqmc_ctx *c)
     cudaFree(c->d_col_start);
     cudaFree(c->d_col_sites);
     cudaFree(c->d_feat0);
+    cudaFree(c->d_step);
     free(c);
 }
 
@@ -919,19 +942,9 @@ int sldqmc_cumulative_batch_dev(sldqmc_ctx *c, int8_t *d_s, double *d_logw, int 
         return SLDQMC_ERR_ARG;
     const long long V = (long long)c->N * c->M;
     launch_check_field(c, d_s, V * B);
-    int8_t *sp = c->d_s_tmp;
-    int *accepted = c->d_sg_tmp;  // B ints of scratch (2*cap available)
     for (int k = 0; k < n_steps; ++k) {
-        const uint32_t step = step0 + (uint32_t)k;
-        cudaMemcpyAsync(sp, d_s, (size_t)(V * B), cudaMemcpyDeviceToDevice, c->st);
-        launch_eff_sweeps(c, sp, B, n_eff, seed, step, -1, nullptr, nullptr);
-        launch_features(c, d_s, B, c->d_feat0);
-        launch_features(c, sp, B, c->d_feat1);
-        int rc = log_weight_run(c, sp, B, c->d_ld_tmp);
+        int rc = cumulative_step(c, d_s, d_logw, B, n_eff, seed, step0 + (uint32_t)k, d_accepts, d_log_r);
         if (rc) return rc;
-        launch_cumulative_accept(c, c->d_ld_tmp, d_logw, c->d_feat0, c->d_feat1, seed, step, B, accepted,
-                                 d_accepts, d_log_r, nullptr);
-        launch_commit(c, d_s, sp, accepted, B);
     }
     return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
 }
@@ -993,6 +1006,132 @@ int sldqmc_cumulative_batch(sldqmc_ctx *c, int8_t *s, double *logw, int B, int n
     if (accepts)
         for (int b = 0; b < B; ++b) accepts[b] += ha[b];
     return SLDQMC_OK;
+}
+
+}  // extern "C"
+
+struct sldqmc_graph {
+    std::vector<sldqmc_ctx *> ctxs;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    cudaStream_t origin = nullptr;
+    bool own_origin = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+void sldqmc_graph_destroy(sldqmc_graph *g)
+{
+    if (!g) return;
+    if (g->origin) cudaStreamSynchronize(g->origin);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    for (cudaEvent_t e : g->events) cudaEventDestroy(e);
+    for (cudaStream_t s : g->streams) cudaStreamDestroy(s);
+    if (g->own_origin && g->origin) cudaStreamDestroy(g->origin);
+    delete g;
+}
+
+int sldqmc_graph_create(sldqmc_ctx *const *ctxs, int n, int8_t *const *d_s, double *const *d_logw, const int *B,
+                        int n_eff, const uint64_t *seeds, int *const *d_accepts, uint32_t step0, void *stream,
+                        sldqmc_graph **out)
+{
+    if (!ctxs || n < 1 || !d_s || !d_logw || !B || !seeds || !d_accepts || !out || n_eff < 0) return SLDQMC_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        sldqmc_ctx *c = ctxs[i];
+        if (!c || !c->have_model || !d_s[i] || !d_logw[i] || !d_accepts[i] || B[i] < 1 || B[i] > c->cap)
+            return SLDQMC_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return SLDQMC_ERR_ARG;  // one member per context: members own their workspace
+    }
+    sldqmc_graph *g = new sldqmc_graph();
+    int rc = SLDQMC_OK;
+    g->origin = (cudaStream_t)stream;
+    if (!g->origin) {
+        if (cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking) != cudaSuccess) { delete g; return SLDQMC_ERR_CUDA; }
+        g->own_origin = true;
+    }
+    for (int i = 0; i < n; ++i) {
+        sldqmc_ctx *c = ctxs[i];
+        g->ctxs.push_back(c);
+        if (!c->d_step) {
+            rc = dalloc(&c->d_step, 1);
+            if (rc) { sldqmc_graph_destroy(g); return rc; }
+        }
+        if (cudaMemcpy(c->d_step, &step0, sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+            sldqmc_graph_destroy(g);
+            return SLDQMC_ERR_CUDA;
+        }
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { sldqmc_graph_destroy(g); return SLDQMC_ERR_CUDA; }
+        g->streams.push_back(st);
+    }
+    for (int k = 0; k < n + 1; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { sldqmc_graph_destroy(g); return SLDQMC_ERR_CUDA; }
+        g->events.push_back(e);
+    }
+    for (int i = 0; i < n; ++i) cudaStreamSynchronize(ctxs[i]->st);
+    if (cudaStreamBeginCapture(g->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        sldqmc_graph_destroy(g);
+        return SLDQMC_ERR_CUDA;
+    }
+    cudaEventRecord(g->events[0], g->origin);
+    for (int i = 0; i < n && !rc; ++i) {
+        sldqmc_ctx *c = ctxs[i];
+        cudaStream_t saved = c->st;
+        const bool prof_on = c->prof && c->prof->on;
+        if (prof_on) c->prof->on = false;
+        c->st = g->streams[i];
+        c->step_dev = c->d_step;
+        cudaStreamWaitEvent(c->st, g->events[0], 0);
+        launch_check_field(c, d_s[i], (long long)c->N * c->M * B[i]);
+        rc = cumulative_step(c, d_s[i], d_logw[i], B[i], n_eff, seeds[i], step0, d_accepts[i], nullptr);
+        launch_step_advance(c, c->d_step);
+        cudaEventRecord(g->events[i + 1], c->st);
+        cudaStreamWaitEvent(g->origin, g->events[i + 1], 0);
+        c->st = saved;
+        c->step_dev = nullptr;
+        if (prof_on) c->prof->on = true;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e1 = cudaStreamEndCapture(g->origin, &graph);
+    g->graph = graph;
+    if (rc || e1 != cudaSuccess || !graph) {
+        cudaGetLastError();
+        sldqmc_graph_destroy(g);
+        return rc ? rc : SLDQMC_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        sldqmc_graph_destroy(g);
+        return SLDQMC_ERR_CUDA;
+    }
+    *out = g;
+    return SLDQMC_OK;
+}
+
+int sldqmc_graph_launch(sldqmc_graph *g, int n_steps)
+{
+    if (!g || n_steps < 0) return SLDQMC_ERR_ARG;
+    for (int k = 0; k < n_steps; ++k)
+        if (cudaGraphLaunch(g->exec, g->origin) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    return SLDQMC_OK;
+}
+
+int sldqmc_graph_sync(sldqmc_graph *g)
+{
+    if (!g) return SLDQMC_ERR_ARG;
+    if (cudaStreamSynchronize(g->origin) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    int rc = SLDQMC_OK;
+    for (sldqmc_ctx *c : g->ctxs) {
+        int r = sync_and_flag(c);
+        if (r && !rc) rc = r;
+    }
+    return rc;
 }
 
 int sldqmc_profile_enable(sldqmc_ctx *c, int on)

@@ -89,6 +89,10 @@ def load(path=None):
         "sldqmc_profile_enable": ([vp, i], i),
         "sldqmc_eff_sweeps_batch_dev": ([vp, vp, i, i, u64, u32, i, vp], i),
         "sldqmc_weight_noalloc": ([ctypes.POINTER(Params), vp, vp, i, i, vp, vp], i),
+        "sldqmc_graph_create": ([vp, i, vp, vp, vp, i, vp, vp, u32, vp, ctypes.POINTER(vp)], i),
+        "sldqmc_graph_launch": ([vp, i], i),
+        "sldqmc_graph_sync": ([vp], i),
+        "sldqmc_graph_destroy": ([vp], None),
         "sldqmc_profile_read": ([vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
@@ -304,3 +308,42 @@ class Context:
 
     def kernel_launches(self):
         return int(load().sldqmc_kernel_launches(self.h))
+
+
+class Graph:
+    """Uneven chain groups in one CUDA graph (sldqmc_graph_*): one cumulative
+    update of every member per replay, branches on separate streams."""
+
+    def __init__(self, members, n_eff, step0=0, stream=None):
+        """members: list of (Context, d_s, d_logw, d_accepts, seed) with torch CUDA tensors."""
+        L = load()
+        n = len(members)
+        self._keep = members
+        P = ctypes.c_void_p * n
+        ctxs = P(*[m[0].h for m in members])
+        ds = P(*[m[1].data_ptr() for m in members])
+        dl = P(*[m[2].data_ptr() for m in members])
+        da = P(*[m[3].data_ptr() for m in members])
+        Bs = (ctypes.c_int * n)(*[int(m[1].shape[0]) for m in members])
+        seeds = (ctypes.c_uint64 * n)(*[int(m[4]) for m in members])
+        h = ctypes.c_void_p()
+        _chk(L.sldqmc_graph_create(ctxs, n, ds, dl, Bs, int(n_eff), seeds, da, ctypes.c_uint32(step0),
+                                   ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)), "graph_create")
+        self.h = h
+
+    def launch(self, n_steps=1):
+        _chk(load().sldqmc_graph_launch(self.h, int(n_steps)), "graph_launch")
+
+    def sync(self):
+        _chk(load().sldqmc_graph_sync(self.h), "graph_sync")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sldqmc_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
