@@ -156,6 +156,21 @@ def traffic_record(kernel_class):
         return None
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Max of a per-rank scalar over all ranks (timing: the slowest rank sets the time)."""
+    import torch
+    if dist is None or not dist.is_initialized():
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank, world, t_max):
+    """Whole-job throughput: every rank processed units_per_rank in at most t_max."""
+    return units_per_rank * world / t_max
+
+
 def oracle_weight_sample(seed=1):
     """One single-flavour weight evaluation of the workload by the FP64 CPU
     oracle (as it stands, with the workload's n_wrap)."""
@@ -273,12 +288,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x):
+        return max_over_ranks(x, dist, "cuda")
 
     t_setup = time.perf_counter()
     if args.no_train:
@@ -329,9 +340,8 @@ def run_ours(args):
     launches = ctx.kernel_launches() - n0
     clocks = sampler.stop()
     ctx.sync()
-    Tmax = max_over_ranks(T)
-    units = 2 * B * args.steps * world
-    value = units / Tmax
+    Tmax = rank_max(T)
+    value = weak_scaling_value(2 * B * args.steps, world, Tmax)
     accept_rate = float(d_acc.sum().item()) / (B * args.steps)
     # decorrelation: |magnetisation| series of a separate set of chains (fewer
     # chains, more steps; the per-chain dynamics does not depend on the batch)
@@ -387,7 +397,7 @@ def run_ours(args):
         barrier_sync()
         T64 = steps_timed(torch, c64, d_s64, d_lw64, d_acc, seed, 1, K64)
         barrier_sync()
-        T64 = max_over_ranks(T64)
+        T64 = rank_max(T64)
         fp64 = {"value": 2 * B * K64 * world / T64, "unit": UNIT, "steps": K64, "ms_per_step": 1e3 * T64 / K64}
         c64.close()
 
@@ -404,7 +414,7 @@ def run_ours(args):
     for k in range(Ke):
         ctx.cumulative_batch(hs, hl, 1, seed, 2 * 10 ** 6 + k, 1, h_acc)
     torch.cuda.synchronize()
-    Te = max_over_ranks(time.perf_counter() - t0)
+    Te = rank_max(time.perf_counter() - t0)
     e2e = {"value": 2 * B * Ke * world / Te, "unit": UNIT, "h2d_bytes_per_step": B * V + 8 * B,
            "d2h_bytes_per_step": B * V + 8 * B + 4 * B}
 
