@@ -22,11 +22,16 @@ namespace sldqmc {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16;
 
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g)
+// Tile BMt x BNt, BMt*BNt/16 threads, each owning a 4 x 4 register block
+// (rows ty + (BMt/4) i, columns tx + (BNt/4) j).
+template <bool TA, bool TB, int BMt, int BNt>
+__global__ void __launch_bounds__(BMt * BNt / 16) k_gemm_f64(GemmF64 g)
 {
+    constexpr int BM = BMt, BN = BNt, NT = BMt * BNt / 16;
+    constexpr int TXN = BNt / 4, TYN = BMt / 4;
+    constexpr int LA = BMt * BK / NT, LB = BNt * BK / NT;
     const int b = blockIdx.z;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     if (g.c_upper && n0 + BN - 1 < m0) return;  // tile strictly below the diagonal
@@ -39,7 +44,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g)
     __shared__ double Bs[BK][BN + 1];
 
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    const int tx = tid % TXN, ty = tid / TXN;
 
     double acc[4][4];
 #pragma unroll
@@ -52,10 +57,10 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g)
     int K = g.K;
     if (g.b_upper && n0 + BN < K) K = n0 + BN;
 
-    double ra[4], rb[4];
+    double ra[LA], rb[LB];
     auto load = [&](int k0) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < LA; ++e) {
             int idx = tid + NT * e;
             int m, k;
             if (!TA) { m = idx / BK; k = idx % BK; } else { k = idx / BM; m = idx % BM; }
@@ -68,7 +73,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g)
             ra[e] = v;
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < LB; ++e) {
             int idx = tid + NT * e;
             int n, k;
             if (!TB) { k = idx / BN; n = idx % BN; } else { n = idx / BK; k = idx % BK; }
@@ -80,14 +85,14 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g)
     };
     auto store = [&]() {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < LA; ++e) {
             int idx = tid + NT * e;
             int m, k;
             if (!TA) { m = idx / BK; k = idx % BK; } else { k = idx / BM; m = idx % BM; }
             As[k][m] = ra[e];
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < LB; ++e) {
             int idx = tid + NT * e;
             int n, k;
             if (!TB) { k = idx / BN; n = idx % BN; } else { n = idx / BK; k = idx % BK; }
@@ -105,9 +110,9 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g)
         for (int k = 0; k < BK; ++k) {
             double a[4], bb[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + TYN * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx + TXN * j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -120,14 +125,14 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g)
     const int8_t *sm = g.s_m ? g.s_m + (long long)b * g.sSm : nullptr;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        int gm = m0 + ty + 16 * i;
+        int gm = m0 + ty + TYN * i;
         if (gm >= g.M) continue;
         double rsc = 1.0;
         if (ms) rsc = g.ms_recip ? 1.0 / ms[gm] : ms[gm];
         if (sm) rsc *= (sm[gm] > 0 ? g.cu : g.cd);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int gn = n0 + tx + 16 * j;
+            int gn = n0 + tx + TXN * j;
             if (gn >= g.N) continue;
             if (g.c_upper && gn < gm) continue;
             double v = g.alpha * acc[i][j];
@@ -168,14 +173,26 @@ double gemm_flops(const GemmF64 &g)
     return f * g.batch;
 }
 
+template <int BMt, int BNt>
+static void launch_tiles(const GemmF64 &g, bool TA, bool TB, cudaStream_t st)
+{
+    dim3 grid((g.N + BNt - 1) / BNt, (g.M + BMt - 1) / BMt, g.batch);
+    constexpr int NT = BMt * BNt / 16;
+    if (!TA && !TB) k_gemm_f64<false, false, BMt, BNt><<<grid, NT, 0, st>>>(g);
+    else if (!TA && TB) k_gemm_f64<false, true, BMt, BNt><<<grid, NT, 0, st>>>(g);
+    else if (TA && !TB) k_gemm_f64<true, false, BMt, BNt><<<grid, NT, 0, st>>>(g);
+    else k_gemm_f64<true, true, BMt, BNt><<<grid, NT, 0, st>>>(g);
+}
+
 void gemm_f64(const GemmF64 &g, bool TA, bool TB, cudaStream_t st)
 {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
-    if (!TA && !TB) k_gemm_f64<false, false><<<grid, NT, 0, st>>>(g);
-    else if (!TA && TB) k_gemm_f64<false, true><<<grid, NT, 0, st>>>(g);
-    else if (TA && !TB) k_gemm_f64<true, false><<<grid, NT, 0, st>>>(g);
-    else k_gemm_f64<true, true><<<grid, NT, 0, st>>>(g);
+    // 64 x 64 tiles when they give every SM several CTAs, else 32 x 32 tiles:
+    // the FP64 pipe is saturated inside a CTA either way, so what matters is
+    // that no SM idles (triangular operands make tile work uneven).
+    const long long tiles64 = (long long)((g.N + 63) / 64) * ((g.M + 63) / 64) * g.batch;
+    if (tiles64 >= 8LL * 152) launch_tiles<64, 64>(g, TA, TB, st);
+    else launch_tiles<32, 32>(g, TA, TB, st);
 }
 
 }  // namespace sldqmc

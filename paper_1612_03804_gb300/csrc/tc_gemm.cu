@@ -267,15 +267,32 @@ __global__ void __launch_bounds__(128, 1)
     }
     __syncwarp();
 
+    // Column scale constants of this tile (float pairs), staged once.
+    __shared__ float2 sc_tab[BN];
+    if (threadIdx.x < BN) {
+        const int n = n0 + threadIdx.x;
+        float2 d = make_float2(1.0f, 0.0f);
+        if (a.s_n && n < a.N) {
+            const bool up = a.s_n[(long long)b * a.sSn + n] > 0;
+            d = up ? make_float2(a.cu_h, a.cu_l) : make_float2(a.cd_h, a.cd_l);
+        }
+        sc_tab[threadIdx.x] = d;
+    }
     const bool ok = mbar_wait(done, 0, a.flag);
     fence_after();
+    __syncthreads();  // sc_tab visible; the pipeline buffers are free for staging the output
     const int row = warp * 32 + lane;
-    const int m = m0 + row;
     // accumulators that received at least one MMA
     const int ksteps = a.nk * KSTEPS;
     const uint32_t used_mask = MODE == 0 ? (((1u << (ksteps < NACC - 1 ? ksteps : NACC - 1)) - 1u) | (1u << (NACC - 1)))
                                          : ((1u << (ksteps < NACC ? ksteps : NACC)) - 1u);
-    const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
+    constexpr int LD = BN + 1;  // padded row of the staging tiles
+    float *t_hi = reinterpret_cast<float *>(base);
+    float *t_lo = t_hi + BM * LD;
+    double *t_f64 = reinterpret_cast<double *>(base);
+    __nv_bfloat16 *t_bf = reinterpret_cast<__nv_bfloat16 *>(base);
+    const bool f64 = a.out_f64 != nullptr;
+    const bool scale = a.s_n != nullptr;
     for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
 #pragma unroll
@@ -288,31 +305,50 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
         }
-        if (!ok || m >= a.N) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int n = n0 + c0 + j;
-            if (n >= a.N) break;
-            if (a.out_f64) {
-                a.out_f64[(long long)b * a.s_f64 + (long long)m * a.N + n] = (double)v[j];
+            const int c = c0 + j;
+            if (f64) {
+                t_f64[row * LD + c] = (double)v[j];
                 continue;
             }
             // y = v * d with d = dh + dl: yh = fl(v dh), ye = the rounding error of that
             // product (exact by FMA) plus v dl.
             float yh = v[j], ye = 0.0f;
-            if (sn) {
-                const bool up = sn[n] > 0;
-                const float dh = up ? a.cu_h : a.cd_h, dl = up ? a.cu_l : a.cd_l;
-                yh = v[j] * dh;
-                ye = fmaf(v[j], dh, -yh) + v[j] * dl;
+            if (scale) {
+                const float2 d = sc_tab[c];
+                yh = v[j] * d.x;
+                ye = fmaf(v[j], d.x, -yh) + v[j] * d.y;
             }
-            const long long o = (long long)b * a.s_out + (long long)m * a.ldp + n;
             if (MODE == 0) {
                 const float hi = to_tf32(yh);
-                a.out_hi[o] = hi;
-                a.out_lo[o] = to_tf32((yh - hi) + ye);
+                t_hi[row * LD + c] = hi;
+                t_lo[row * LD + c] = to_tf32((yh - hi) + ye);
             } else {
-                a.out_bf[o] = __float2bfloat16_rn(yh + ye);
+                t_bf[row * LD + c] = __float2bfloat16_rn(yh + ye);
+            }
+        }
+    }
+    __syncthreads();
+    // Coalesced stores: each warp writes whole rows of the tile.
+    if (ok) {
+        for (int r = warp; r < BM; r += 4) {
+            const int m = m0 + r;
+            if (m >= a.N) break;
+            for (int c = lane; c < BN; c += 32) {
+                const int n = n0 + c;
+                if (n >= a.N) continue;
+                if (f64) {
+                    a.out_f64[(long long)b * a.s_f64 + (long long)m * a.N + n] = t_f64[r * LD + c];
+                } else {
+                    const long long o = (long long)b * a.s_out + (long long)m * a.ldp + n;
+                    if (MODE == 0) {
+                        a.out_hi[o] = t_hi[r * LD + c];
+                        a.out_lo[o] = t_lo[r * LD + c];
+                    } else {
+                        a.out_bf[o] = t_bf[r * LD + c];
+                    }
+                }
             }
         }
     }
