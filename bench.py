@@ -242,6 +242,57 @@ def train_effective_model(torch, sldqmc, args, dev_seed):
     return J, E0, r2, len(cfgs)
 
 
+def critical_point_context(torch, sldqmc, args, rank):
+    """Decorrelation at the paper's finite-temperature critical point (beta=1,
+    dtau=0.05, M=20, h=2.774, 16x16; fit on 8x8 as in the paper): acceptance and
+    tau_int of |sum s| for 16 chains over args.tau_steps cumulative updates."""
+    import math
+    import numpy as np
+    from paper_1612_03804_gb300.analysis import tau_int
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    wl = dict(WL, beta=1.0)
+    kt = -0.5 * math.log(math.tanh(wl["dtau"] * wl["h"]))
+    bare = np.array([-wl["dtau"] * wl["J"] / wl["beta"], 0.0, 0.0, -kt / wl["beta"]])
+    Bt = args.train_chains
+    c8 = sldqmc.Context(8, 8, t=wl["t"], mu=wl["mu"], xi=wl["xi"], beta=wl["beta"], dtau=wl["dtau"], n_wrap=20,
+                        J=wl["J"], h=wl["h"], prec="fp64", max_batch=Bt)
+    s = torch.from_numpy(batch_uniform(8100 + rank, Bt, c8.M, c8.N)).cuda()
+    c8.set_effective_model(CLASSES, bare)
+    for k in range(args.bare_sweeps):
+        c8.eff_sweeps_batch_dev(s, 1, 81, k, -1)
+    c8.local_sweep_batch_dev(s, 81, 0, args.thermalize, want_stats=False)
+    cfgs, sw = [], args.thermalize
+    while len(cfgs) * Bt < args.train_configs:
+        c8.local_sweep_batch_dev(s, 81, sw, 1, want_stats=False)
+        sw += 1
+        cfgs.append(s.cpu().numpy().copy())
+    J, E0, r2 = c8.fit_effective_action(np.concatenate(cfgs)[: args.train_configs])
+    c8.close()
+    B = min(args.tau_chains, args.batch)
+    ctx = sldqmc.Context(wl["L"], wl["L"], t=wl["t"], mu=wl["mu"], xi=wl["xi"], beta=wl["beta"], dtau=wl["dtau"],
+                         n_wrap=20, J=wl["J"], h=wl["h"], prec=args.prec, max_batch=B)
+    ctx.set_effective_model(CLASSES, J, E0)
+    d_s = torch.from_numpy(batch_uniform(8200 + rank, B, ctx.M, ctx.N)).cuda()
+    for k in range(args.eff_thermalize):
+        ctx.eff_sweeps_batch_dev(d_s, 1, 82, k, -1)
+    d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
+    ctx.log_weight_batch_dev(d_s, d_lw)
+    d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+    for w in range(args.warmup):
+        ctx.cumulative_batch_dev(d_s, d_lw, 1, 83, w, 1, d_acc)
+    d_acc.zero_()
+    t0 = time.perf_counter()
+    series = magnetisation_series(torch, ctx, d_s, d_lw, d_acc, 83, 100, args.tau_steps).astype(np.float64)
+    dt = time.perf_counter() - t0
+    tau, window = tau_int(series)
+    ctx.close()
+    return {"point": "16x16, beta=1, dtau=0.05 (M=20), h=2.774, mu=-0.5 (the paper's critical point), "
+                     f"{B} chains, effective model fitted on 8x8 (R^2={r2:.6f})",
+            "accept_rate": float(d_acc.sum().item()) / (B * args.tau_steps), "tau_int": tau,
+            "tau_window": window, "tau_steps": args.tau_steps,
+            "steps_per_s": args.tau_steps / dt}
+
+
 def steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, step0, K):
     st = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -418,6 +469,10 @@ def run_ours(args):
     e2e = {"value": 2 * B * Ke * world / Te, "unit": UNIT, "h2d_bytes_per_step": B * V + 8 * B,
            "d2h_bytes_per_step": B * V + 8 * B + 4 * B}
 
+    crit = None
+    if args.tau_steps > 0 and not args.no_train and not args.skip_critical:
+        crit = critical_point_context(torch, sldqmc, args, rank)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         from oracle import oracle as O
@@ -441,6 +496,7 @@ def run_ours(args):
                "fp64": fp64, "decorrelated_samples_per_s": samples_per_s, "tau_int": tau,
                "tau_window": window, "tau_observable": "|sum s| per chain",
                "tau_series": {"chains": min(args.tau_chains, B), "steps": args.tau_steps, "note": tau_note}, "accept_rate": accept_rate,
+               "critical_point": crit,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                "gpu_launches": launches}
         print(json.dumps(out), flush=True)
@@ -471,6 +527,7 @@ def main():
     ap.add_argument("--no-train", action="store_true",
                     help="use the bare Ising couplings as H_eff (no local-DQMC training; for profiling runs)")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-critical", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
