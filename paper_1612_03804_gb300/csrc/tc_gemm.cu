@@ -19,13 +19,14 @@
 // in the epilogue; in split-TF32 mode the leading A_h E_h products use seven
 // of them and the four small correction products share the eighth.
 //
-// One CTA computes a 128 x 64 output tile: warp 0 drives TMA (128-byte
-// swizzled boxes, mbarrier completion), warp 1 issues the MMAs from one
-// thread, and all four warps drain the accumulators with tcgen05.ld and
-// apply the next slice's column scaling (as a float pair, so that the scale
-// constant adds no systematic error) while re-splitting the result into the
-// operand format of the next product (or FP64 for the stabilisation at the
-// end of the block).  Every mbarrier wait is bounded; a wait that runs out
+// A persistent CTA per SM walks the 128 x 64 output tiles of the batch:
+// warp 0 drives TMA (128-byte swizzled boxes, mbarrier completion) without
+// stopping at tile boundaries, warp 1 issues the MMAs from one thread, and
+// warps 2-5 drain the accumulators with tcgen05.ld and apply the next
+// slice's column scaling (as a float pair, so that the scale constant adds
+// no systematic error) while re-splitting the result into the operand format
+// of the next product (or FP64 for the stabilisation at the end of the
+// block).  Every mbarrier wait is bounded; a wait that runs out
 // raises the context's timeout flag and the CTA frees its tensor memory and
 // exits.
 #include <cuda.h>
@@ -45,7 +46,7 @@ constexpr int TILE_B = BN * 128;  // one B part of one stage: 64 rows x 128 byte
 constexpr int TMEM_COLS = BN * NACC;
 
 struct TcArgs {
-    int N, ldp, nk;
+    int N, ldp, nk, batch;
     float *out_hi, *out_lo;
     __nv_bfloat16 *out_bf;
     double *out_f64;
@@ -174,8 +175,17 @@ __host__ __device__ constexpr int stages() { return MODE == 0 ? 3 : 5; }
 template <int MODE>
 __host__ __device__ constexpr int stage_bytes() { return MODE == 0 ? 2 * TILE_A + 3 * TILE_B : TILE_A + TILE_B; }
 
+// Persistent kernel: one CTA per SM loops over the 128 x 64 output tiles of
+// the whole batch (tile t = blockIdx.x, blockIdx.x + gridDim.x, ...).
+// Warp 0 (one thread) streams TMA stages continuously across tile
+// boundaries; warp 1 (one thread) issues the MMAs of a tile once the
+// epilogue has handed tensor memory back; warps 2-5 drain the accumulators
+// (TMEM lane quarter = warp % 4), scale, re-split and store with vector
+// stores while the next tile's operands are already loading.
+constexpr int NTHREADS = 192;
+
 template <int MODE>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
               const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
               const __grid_constant__ CUtensorMap tB2, TcArgs a)
@@ -189,18 +199,21 @@ __global__ void __launch_bounds__(128, 1)
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(base + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *done = empty + STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    uint64_t *tmem_full = empty + STAGES;
+    uint64_t *tmem_free = tmem_full + 1;
+    uint32_t *tmem_slot = (uint32_t *)(tmem_free + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, b = blockIdx.z;
+    const int tiles_n = (a.N + BN - 1) / BN, tiles_m = (a.N + BM - 1) / BM;
+    const int tiles = tiles_n * tiles_m * a.batch;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        mbar_init(tmem_full, 1);
+        mbar_init(tmem_free, 128);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -213,145 +226,162 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-
-    if (warp == 0 && lane == 0) {
-        for (int kb = 0; kb < a.nk; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, a.flag)) break;
-            mbar_expect_tx(&full[s], STAGE_BYTES);
-            uint8_t *st = base + s * STAGE_BYTES;
-            const int k0 = kb * (128 / (MODE == 0 ? 4 : 2));
-            tma_load_3d(st, &tA0, k0, m0, b, &full[s]);
-            if (MODE == 0) {
-                tma_load_3d(st + TILE_A, &tA1, k0, m0, b, &full[s]);
-                tma_load_2d(st + 2 * TILE_A, &tB0, k0, n0, &full[s]);
-                tma_load_2d(st + 2 * TILE_A + TILE_B, &tB1, k0, n0, &full[s]);
-                tma_load_2d(st + 2 * TILE_A + 2 * TILE_B, &tB2, k0, n0, &full[s]);
-            } else {
-                tma_load_2d(st + TILE_A, &tB0, k0, n0, &full[s]);
-            }
-        }
-    } else if (warp == 1 && lane == 0) {
-        bool ok = true;
-        for (int kb = 0; kb < a.nk && ok; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(&full[s], (kb / STAGES) & 1, a.flag)) { ok = false; break; }
-            fence_after();
-            const uint32_t sa = smem_u32(base + s * STAGE_BYTES);
-#pragma unroll
-            for (int k = 0; k < KSTEPS; ++k) {
-                const uint32_t off = k * 32;
-                const int g = kb * KSTEPS + k;
-                if (MODE == 0) {
-                    // A_h E_h round-robin over accumulators 0..6; the four small
-                    // correction products all go to accumulator 7, where their
-                    // rounding is relative to a sum 2^-11 smaller.
-                    const uint32_t acc_main = tmem + (uint32_t)((g % (NACC - 1)) * BN);
-                    const uint32_t acc_small = tmem + (uint32_t)((NACC - 1) * BN);
-                    const uint64_t ah = smem_desc(sa + off), al = smem_desc(sa + TILE_A + off);
-                    const uint32_t sb = sa + 2 * TILE_A + off;
-                    const uint64_t eh = smem_desc(sb), em = smem_desc(sb + TILE_B), el = smem_desc(sb + 2 * TILE_B);
-                    mma<0>(acc_main, ah, eh, IDESC, g < NACC - 1 ? 0u : 1u);
-                    mma<0>(acc_small, ah, em, IDESC, g == 0 ? 0u : 1u);
-                    mma<0>(acc_small, al, eh, IDESC, 1u);
-                    mma<0>(acc_small, ah, el, IDESC, 1u);
-                    mma<0>(acc_small, al, em, IDESC, 1u);
-                } else {
-                    const uint32_t acc_t = tmem + (uint32_t)((g % NACC) * BN);
-                    mma<1>(acc_t, smem_desc(sa + off), smem_desc(sa + TILE_A + off), IDESC, g < NACC ? 0u : 1u);
-                }
-            }
-            mma_commit(&empty[s]);
-        }
-        if (ok) mma_commit(done);
-    }
-    __syncwarp();
-
-    // Column scale constants of this tile (float pairs), staged once.
-    __shared__ float2 sc_tab[BN];
-    if (threadIdx.x < BN) {
-        const int n = n0 + threadIdx.x;
-        float2 d = make_float2(1.0f, 0.0f);
-        if (a.s_n && n < a.N) {
-            const bool up = a.s_n[(long long)b * a.sSn + n] > 0;
-            d = up ? make_float2(a.cu_h, a.cu_l) : make_float2(a.cd_h, a.cd_l);
-        }
-        sc_tab[threadIdx.x] = d;
-    }
-    const bool ok = mbar_wait(done, 0, a.flag);
-    fence_after();
-    __syncthreads();  // sc_tab visible; the pipeline buffers are free for staging the output
-    const int row = warp * 32 + lane;
-    // accumulators that received at least one MMA
     const int ksteps = a.nk * KSTEPS;
-    const uint32_t used_mask = MODE == 0 ? (((1u << (ksteps < NACC - 1 ? ksteps : NACC - 1)) - 1u) | (1u << (NACC - 1)))
-                                         : ((1u << (ksteps < NACC ? ksteps : NACC)) - 1u);
-    constexpr int LD = BN + 1;  // padded row of the staging tiles
-    float *t_hi = reinterpret_cast<float *>(base);
-    float *t_lo = t_hi + BM * LD;
-    double *t_f64 = reinterpret_cast<double *>(base);
-    __nv_bfloat16 *t_bf = reinterpret_cast<__nv_bfloat16 *>(base);
-    const bool f64 = a.out_f64 != nullptr;
-    const bool scale = a.s_n != nullptr;
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-        for (int q = 0; q < NACC; ++q) {
-            if (!((used_mask >> q) & 1u)) continue;
-            uint32_t r[16];
-            tmem_ld16(lane_base + (uint32_t)(q * BN), r);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int c = c0 + j;
-            if (f64) {
-                t_f64[row * LD + c] = (double)v[j];
-                continue;
-            }
-            // y = v * d with d = dh + dl: yh = fl(v dh), ye = the rounding error of that
-            // product (exact by FMA) plus v dl.
-            float yh = v[j], ye = 0.0f;
-            if (scale) {
-                const float2 d = sc_tab[c];
-                yh = v[j] * d.x;
-                ye = fmaf(v[j], d.x, -yh) + v[j] * d.y;
-            }
-            if (MODE == 0) {
-                const float hi = to_tf32(yh);
-                t_hi[row * LD + c] = hi;
-                t_lo[row * LD + c] = to_tf32((yh - hi) + ye);
-            } else {
-                t_bf[row * LD + c] = __float2bfloat16_rn(yh + ye);
-            }
-        }
-    }
-    __syncthreads();
-    // Coalesced stores: each warp writes whole rows of the tile.
-    if (ok) {
-        for (int r = warp; r < BM; r += 4) {
-            const int m = m0 + r;
-            if (m >= a.N) break;
-            for (int c = lane; c < BN; c += 32) {
-                const int n = n0 + c;
-                if (n >= a.N) continue;
-                if (f64) {
-                    a.out_f64[(long long)b * a.s_f64 + (long long)m * a.N + n] = t_f64[r * LD + c];
-                } else {
-                    const long long o = (long long)b * a.s_out + (long long)m * a.ldp + n;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;  // global k-block counter of this CTA
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
+                const int n0 = tn * BN, m0 = tm * BM;
+                for (int kb = 0; kb < a.nk; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, a.flag)) { ok = false; break; }
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    uint8_t *st = base + s * STAGE_BYTES;
+                    const int k0 = kb * (128 / (MODE == 0 ? 4 : 2));
+                    tma_load_3d(st, &tA0, k0, m0, b, &full[s]);
                     if (MODE == 0) {
-                        a.out_hi[o] = t_hi[r * LD + c];
-                        a.out_lo[o] = t_lo[r * LD + c];
+                        tma_load_3d(st + TILE_A, &tA1, k0, m0, b, &full[s]);
+                        tma_load_2d(st + 2 * TILE_A, &tB0, k0, n0, &full[s]);
+                        tma_load_2d(st + 2 * TILE_A + TILE_B, &tB1, k0, n0, &full[s]);
+                        tma_load_2d(st + 2 * TILE_A + 2 * TILE_B, &tB2, k0, n0, &full[s]);
                     } else {
-                        a.out_bf[o] = t_bf[r * LD + c];
+                        tma_load_2d(st + TILE_A, &tB0, k0, n0, &full[s]);
                     }
                 }
             }
         }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, ti = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++ti) {
+                // the epilogue must have drained the previous tile's accumulators
+                if (ti > 0 && !mbar_wait(tmem_free, (ti - 1) & 1, a.flag)) { ok = false; break; }
+                fence_after();
+                for (int kb = 0; kb < a.nk; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(&full[s], (it / STAGES) & 1, a.flag)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t sa = smem_u32(base + s * STAGE_BYTES);
+#pragma unroll
+                    for (int k = 0; k < KSTEPS; ++k) {
+                        const uint32_t off = k * 32;
+                        const int g = kb * KSTEPS + k;
+                        if (MODE == 0) {
+                            // A_h E_h round-robin over accumulators 0..6; the four small
+                            // correction products all go to accumulator 7, where their
+                            // rounding is relative to a sum 2^-11 smaller.
+                            const uint32_t acc_main = tmem + (uint32_t)((g % (NACC - 1)) * BN);
+                            const uint32_t acc_small = tmem + (uint32_t)((NACC - 1) * BN);
+                            const uint64_t ah = smem_desc(sa + off), al = smem_desc(sa + TILE_A + off);
+                            const uint32_t sb = sa + 2 * TILE_A + off;
+                            const uint64_t eh = smem_desc(sb), em = smem_desc(sb + TILE_B),
+                                           el = smem_desc(sb + 2 * TILE_B);
+                            mma<0>(acc_main, ah, eh, IDESC, g < NACC - 1 ? 0u : 1u);
+                            mma<0>(acc_small, ah, em, IDESC, g == 0 ? 0u : 1u);
+                            mma<0>(acc_small, al, eh, IDESC, 1u);
+                            mma<0>(acc_small, ah, el, IDESC, 1u);
+                            mma<0>(acc_small, al, em, IDESC, 1u);
+                        } else {
+                            const uint32_t acc_t = tmem + (uint32_t)((g % NACC) * BN);
+                            mma<1>(acc_t, smem_desc(sa + off), smem_desc(sa + TILE_A + off), IDESC,
+                                   g < NACC ? 0u : 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(tmem_full);
+            }
+        }
+    } else {
+        // epilogue warps 2..5
+        const int q4 = warp & 3;
+        const int row = q4 * 32 + lane;
+        const uint32_t used_mask = MODE == 0
+                                       ? (((1u << (ksteps < NACC - 1 ? ksteps : NACC - 1)) - 1u) | (1u << (NACC - 1)))
+                                       : ((1u << (ksteps < NACC ? ksteps : NACC)) - 1u);
+        int ti = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
+            const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
+            const int n0 = tn * BN, m0 = tm * BM;
+            const int m = m0 + row;
+            const bool ok = mbar_wait(tmem_full, ti & 1, a.flag);
+            fence_after();
+            const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+                const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c0;
+                for (int q = 0; q < NACC; ++q) {
+                    if (!((used_mask >> q) & 1u)) continue;
+                    uint32_t r[16];
+                    tmem_ld16(lane_base + (uint32_t)(q * BN), r);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
+                }
+                if (!ok || m >= a.N) continue;
+                const int nb = n0 + c0;
+                if (nb >= a.N) continue;
+                const bool full16 = nb + 16 <= a.N;
+                if (a.out_f64) {
+                    double *o = a.out_f64 + (long long)b * a.s_f64 + (long long)m * a.N + nb;
+                    if (full16 && (a.N & 1) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 2)
+                            *reinterpret_cast<double2 *>(o + j) = make_double2((double)v[j], (double)v[j + 1]);
+                    } else {
+                        for (int j = 0; j < 16 && nb + j < a.N; ++j) o[j] = (double)v[j];
+                    }
+                    continue;
+                }
+                float hi[16], lo[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    // y = v * d with d = dh + dl: yh = fl(v dh), ye = the rounding error of
+                    // that product (exact by FMA) plus v dl.
+                    float yh = v[j], ye = 0.0f;
+                    if (sn) {
+                        const bool up = (nb + j < a.N) && sn[nb + j] > 0;
+                        const float dh = up ? a.cu_h : a.cd_h, dl = up ? a.cu_l : a.cd_l;
+                        yh = v[j] * dh;
+                        ye = fmaf(v[j], dh, -yh) + v[j] * dl;
+                    }
+                    if (MODE == 0) {
+                        hi[j] = to_tf32(yh);
+                        lo[j] = to_tf32((yh - hi[j]) + ye);
+                    } else {
+                        hi[j] = yh + ye;
+                    }
+                }
+                const long long o = (long long)b * a.s_out + (long long)m * a.ldp + nb;
+                if (MODE == 0) {
+                    if (full16) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4) {
+                            *reinterpret_cast<float4 *>(a.out_hi + o + j) = make_float4(hi[j], hi[j + 1], hi[j + 2], hi[j + 3]);
+                            *reinterpret_cast<float4 *>(a.out_lo + o + j) = make_float4(lo[j], lo[j + 1], lo[j + 2], lo[j + 3]);
+                        }
+                    } else {
+                        for (int j = 0; j < 16 && nb + j < a.N; ++j) {
+                            a.out_hi[o + j] = hi[j];
+                            a.out_lo[o + j] = lo[j];
+                        }
+                    }
+                } else {
+                    for (int j = 0; j < 16 && nb + j < a.N; ++j) a.out_bf[o + j] = __float2bfloat16_rn(hi[j]);
+                }
+            }
+            // hand the accumulators back to the MMA thread
+            fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_free)) : "memory");
+            if (!ok) break;  // a wait ran out: the flag is raised, stop instead of waiting per tile
+        }
     }
+    __syncwarp();
     fence_before();
     __syncthreads();
     if (warp == 0)
@@ -389,6 +419,7 @@ struct TcWs {
     CUtensorMap mapA[2][2];  // [buffer][part]
     CUtensorMap mapB[3];     // [part]
     void *mem;
+    int num_sms;
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
@@ -423,7 +454,7 @@ bool encode(CUtensorMap *map, void *ptr, bool bf16, int rank, int ldp, int rows,
 template <int MODE>
 constexpr size_t smem_bytes()
 {
-    return (size_t)stages<MODE>() * stage_bytes<MODE>() + 1024 + 256;
+    return (size_t)stages<MODE>() * stage_bytes<MODE>() + 1024 + 256;  // stages, alignment, barriers
 }
 
 // E = E_h + E_m + E_l, each part TF32-rounded.
@@ -450,6 +481,13 @@ int tc_prepare(sldqmc_ctx *c)
     if (c->N < BM) return SLDQMC_ERR_UNSUPPORTED;  // tensor-core tiles are 128 x 128
     TcWs *w = new TcWs();
     c->tc_ws = w;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        w->num_sms = 0;
+        if (cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || w->num_sms < 1)
+            w->num_sms = 148;
+    }
     const int N = c->N;
     w->ldp = (N + 63) / 64 * 64;
     const bool bf = c->p.prec == SLDQMC_BF16;
@@ -537,13 +575,15 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
         k_tc_prep<0><<<gp, 256, 0, c->st>>>(Ut, c->nn, N, w->ldp, d_s + (long long)slices[0] * N, sS, cu, cd,
                                             w->opf[0][0], w->opf[0][1], nullptr, s_out);
     c->launches++;
-    dim3 grid((N + BN - 1) / BN, (N + BM - 1) / BM, B);
+    const int tiles = ((N + BN - 1) / BN) * ((N + BM - 1) / BM) * B;
+    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
     for (int j = 0; j < nb; ++j) {
         const int src = j & 1, dst = src ^ 1;
         TcArgs a{};
         a.N = N;
         a.ldp = w->ldp;
         a.nk = w->ldp / (bf ? 64 : 32);
+        a.batch = B;
         a.s_out = s_out;
         a.s_f64 = c->nn;
         a.flag = c->d_flag;
@@ -561,10 +601,10 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
         }
         prof_begin(c, SLDQMC_KC_GEMM_TC, 2.0 * (double)N * N * N * B);
         if (bf)
-            k_tc_gemm<1><<<grid, 128, smem_bytes<1>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
+            k_tc_gemm<1><<<grid, NTHREADS, smem_bytes<1>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
                                                                 w->mapB[1], w->mapB[2], a);
         else
-            k_tc_gemm<0><<<grid, 128, smem_bytes<0>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
+            k_tc_gemm<0><<<grid, NTHREADS, smem_bytes<0>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
                                                                 w->mapB[1], w->mapB[2], a);
         prof_end(c);
         c->launches++;
