@@ -136,24 +136,27 @@ __global__ void __launch_bounds__(128) k_chol_panel(const double *W, long long s
         Rk[r][c] = v;
     }
     __syncthreads();
-    for (int j = 0; j < KB; ++j) {
-        if (threadIdx.x == 0) {
+    // Factor the KB x KB block with one warp (lane c owns column c): no
+    // block-wide barrier inside the elimination.
+    if (threadIdx.x < 32) {
+        const int c = threadIdx.x;
+        for (int j = 0; j < KB; ++j) {
             double d = Rk[j][j];
             if (!(d > 0.0) || !isfinite(d)) {
-                if (j < kb) atomicOr(flag, FLAG_NUMERICAL);
+                if (c == 0 && j < kb) atomicOr(flag, FLAG_NUMERICAL);
                 d = 1.0;
             }
-            Rk[j][j] = sqrt(d);
+            d = sqrt(d);
+            __syncwarp();
+            if (c == j) Rk[j][j] = d;
+            else if (c > j) Rk[j][c] /= d;
+            __syncwarp();
+            const double rjc = Rk[j][c];
+            for (int r = j + 1; r <= c; ++r) Rk[r][c] -= Rk[j][r] * rjc;
+            __syncwarp();
         }
-        __syncthreads();
-        for (int c = j + 1 + threadIdx.x; c < KB; c += blockDim.x) Rk[j][c] /= Rk[j][j];
-        __syncthreads();
-        for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
-            int r = e / KB, c = e % KB;
-            if (r > j && c >= r) Rk[r][c] -= Rk[j][r] * Rk[j][c];
-        }
-        __syncthreads();
     }
+    __syncthreads();
     if (blockIdx.x == 0) {
         double *Rb = R + (long long)b * sR;
         for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
