@@ -254,6 +254,13 @@ long long sldqmc_kernel_launches(const sldqmc_ctx *ctx);
 int sldqmc_weight_noalloc(const sldqmc_params *p, void *stream, const int8_t *d_s, int B, int eta,
                           double *d_logabsdet, int *d_sign);
 
+/* Failure-path self-test of the bounded device waits used by the
+ * tensor-core kernels: launches a kernel that waits on an mbarrier nothing
+ * arrives at, for at most max_polls polls (1 .. 2^24), so the wait runs out
+ * and raises the timeout flag; sldqmc_sync then returns SLDQMC_ERR_TIMEOUT
+ * and the context stays usable. */
+int sldqmc_wait_selftest(sldqmc_ctx *ctx, int max_polls);
+
 /* Kernel classes for the timing hooks below. */
 #define SLDQMC_KC_GEMM_F64 0   /* FP64 GEMM (slice products in FP64 mode, Gram, trailing updates) */
 #define SLDQMC_KC_GEMM_TC 1    /* tensor-core slice products (3xTF32 / BF16) */

@@ -38,6 +38,7 @@ void launch_step_advance(sldqmc_ctx *c, uint32_t *d_step);
 void stab_set_limits(int Npad);
 // tc_gemm.cu
 void tc_convert_E(sldqmc_ctx *c);
+void launch_wait_selftest(sldqmc_ctx *c, int limit);
 int tc_prepare(sldqmc_ctx *c);
 void tc_release(sldqmc_ctx *c);
 void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, double cu, double cd,
@@ -1132,6 +1133,13 @@ int sldqmc_graph_sync(sldqmc_graph *g)
         if (r && !rc) rc = r;
     }
     return rc;
+}
+
+int sldqmc_wait_selftest(sldqmc_ctx *c, int max_polls)
+{
+    if (!c || max_polls < 1 || max_polls > (1 << 24)) return SLDQMC_ERR_ARG;
+    launch_wait_selftest(c, max_polls);
+    return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
 }
 
 int sldqmc_profile_enable(sldqmc_ctx *c, int on)

@@ -136,25 +136,33 @@ __global__ void __launch_bounds__(128) k_chol_panel(const double *W, long long s
         Rk[r][c] = v;
     }
     __syncthreads();
-    // Factor the KB x KB block with one warp (lane c owns column c): no
-    // block-wide barrier inside the elimination.
+    // Factor the KB x KB block with one warp, in registers: lane c holds
+    // column c; row j of the factor is broadcast by shuffles, so the
+    // elimination needs neither block barriers nor shared-memory round trips.
     if (threadIdx.x < 32) {
         const int c = threadIdx.x;
+        double col[KB];
+#pragma unroll
+        for (int r = 0; r < KB; ++r) col[r] = Rk[r][c];
+#pragma unroll
         for (int j = 0; j < KB; ++j) {
-            double d = Rk[j][j];
+            double d = __shfl_sync(0xffffffffu, col[j], j);
             if (!(d > 0.0) || !isfinite(d)) {
                 if (c == 0 && j < kb) atomicOr(flag, FLAG_NUMERICAL);
                 d = 1.0;
             }
             d = sqrt(d);
-            __syncwarp();
-            if (c == j) Rk[j][j] = d;
-            else if (c > j) Rk[j][c] /= d;
-            __syncwarp();
-            const double rjc = Rk[j][c];
-            for (int r = j + 1; r <= c; ++r) Rk[r][c] -= Rk[j][r] * rjc;
-            __syncwarp();
+            if (c == j) col[j] = d;
+            else if (c > j) col[j] /= d;
+            const double rjc = col[j];
+#pragma unroll
+            for (int r = j + 1; r < KB; ++r) {
+                const double rjr = __shfl_sync(0xffffffffu, col[j], r);
+                if (c >= r) col[r] -= rjr * rjc;
+            }
         }
+#pragma unroll
+        for (int r = 0; r < KB; ++r) Rk[r][c] = col[r];
     }
     __syncthreads();
     if (blockIdx.x == 0) {

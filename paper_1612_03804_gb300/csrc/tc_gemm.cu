@@ -81,14 +81,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: gives up after 2^22 polls (well over a second), raising the
-// timeout flag instead of spinning forever.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *flag)
+// Bounded wait: gives up after `limit` polls (2^22 by default, well over a
+// second), raising the timeout flag instead of spinning forever.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *flag, int limit = 1 << 22)
 {
-    for (int it = 0; it < (1 << 22); ++it)
+    for (int it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     atomicOr(flag, FLAG_TIMEOUT);
     return false;
+}
+
+// Exercises the bounded-wait path: waits on an mbarrier that nothing
+// arrives at, so the wait must run out, raise the flag and return.
+__global__ void k_wait_selftest(int *flag, int limit)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0, flag, limit);
 }
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar)
@@ -475,6 +488,12 @@ __global__ void k_split_E3(const double *E, int N, int ldp, float *h, float *mid
 }
 
 }  // namespace
+
+void launch_wait_selftest(sldqmc_ctx *c, int limit)
+{
+    k_wait_selftest<<<1, 32, 0, c->st>>>(c->d_flag, limit);
+    c->launches++;
+}
 
 int tc_prepare(sldqmc_ctx *c)
 {

@@ -93,6 +93,7 @@ def load(path=None):
         "sldqmc_graph_launch": ([vp, i], i),
         "sldqmc_graph_sync": ([vp], i),
         "sldqmc_graph_destroy": ([vp], None),
+        "sldqmc_wait_selftest": ([vp, i], i),
         "sldqmc_profile_read": ([vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
@@ -302,6 +303,9 @@ class Context:
         _chk(load().sldqmc_profile_read(self.h, _p(la), _p(ms), _p(fl)), "profile_read")
         return {k: dict(launches=int(la[i]), ms=float(ms[i]), flops=float(fl[i]))
                 for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def wait_selftest(self, max_polls):
+        _chk(load().sldqmc_wait_selftest(self.h, int(max_polls)), "wait_selftest")
 
     def sync(self):
         _chk(load().sldqmc_sync(self.h), "sync")
