@@ -513,7 +513,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=128)
-    ap.add_argument("--prec", default="3xtf32", choices=["3xtf32", "bf16", "fp64"])
+    ap.add_argument("--prec", default="3xtf32", choices=["3xtf32", "bf16x3", "bf16", "fp64"])
     ap.add_argument("--train-configs", type=int, default=2000)
     ap.add_argument("--train-chains", type=int, default=64)
     ap.add_argument("--thermalize", type=int, default=20)

@@ -62,7 +62,10 @@ typedef enum {
     SLDQMC_3XTF32 = 1, /* split-TF32 tensor-core products: the running product in two TF32
                           parts, exp(-dtau K) in three (five MMAs per K-step), FP32
                           accumulation spread over eight tensor-memory accumulators */
-    SLDQMC_BF16 = 2    /* BF16 tensor-core products, FP32 accumulate */
+    SLDQMC_BF16 = 2,   /* BF16 tensor-core products, FP32 accumulate */
+    SLDQMC_BF16X3 = 3  /* split-BF16 tensor-core products: both operands in three BF16 parts,
+                          six MMAs per 16-wide K-step, FP32 accumulation spread over eight
+                          tensor-memory accumulators */
 } sldqmc_prec;
 
 typedef struct {

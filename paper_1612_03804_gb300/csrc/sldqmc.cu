@@ -432,7 +432,7 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     if (!p || !out) return SLDQMC_ERR_ARG;
     *out = nullptr;
     if (p->Lx < 1 || p->Ly < 1 || p->n_wrap < 1 || p->max_batch < 1 || !(p->dtau > 0.0) ||
-        !(p->beta > 0.0) || p->prec < 0 || p->prec > 2 || !isfinite(p->t) || !isfinite(p->mu) ||
+        !(p->beta > 0.0) || p->prec < 0 || p->prec > 3 || !isfinite(p->t) || !isfinite(p->mu) ||
         !isfinite(p->xi) || !isfinite(p->J_ising) || !(p->h > 0.0))
         return SLDQMC_ERR_ARG;
     const long long N = (long long)p->Lx * p->Ly;

@@ -136,35 +136,31 @@ __global__ void __launch_bounds__(128) k_chol_panel(const double *W, long long s
         Rk[r][c] = v;
     }
     __syncthreads();
-    // Factor the KB x KB block with one warp, in registers: lane c holds
-    // column c; row j of the factor is broadcast by shuffles, so the
-    // elimination needs neither block barriers nor shared-memory round trips.
-    if (threadIdx.x < 32) {
-        const int c = threadIdx.x;
-        double col[KB];
-#pragma unroll
-        for (int r = 0; r < KB; ++r) col[r] = Rk[r][c];
-#pragma unroll
-        for (int j = 0; j < KB; ++j) {
-            double d = __shfl_sync(0xffffffffu, col[j], j);
+    // Factor the KB x KB block (right-looking, all threads of the CTA); the
+    // reciprocals of the pivots are kept so that every later division is a
+    // multiplication (FP64 division is many times slower than an FMA here).
+    __shared__ double rinv[KB];
+    for (int j = 0; j < KB; ++j) {
+        if (threadIdx.x == 0) {
+            double d = Rk[j][j];
             if (!(d > 0.0) || !isfinite(d)) {
-                if (c == 0 && j < kb) atomicOr(flag, FLAG_NUMERICAL);
+                if (j < kb) atomicOr(flag, FLAG_NUMERICAL);
                 d = 1.0;
             }
             d = sqrt(d);
-            if (c == j) col[j] = d;
-            else if (c > j) col[j] /= d;
-            const double rjc = col[j];
-#pragma unroll
-            for (int r = j + 1; r < KB; ++r) {
-                const double rjr = __shfl_sync(0xffffffffu, col[j], r);
-                if (c >= r) col[r] -= rjr * rjc;
-            }
+            Rk[j][j] = d;
+            rinv[j] = 1.0 / d;
         }
-#pragma unroll
-        for (int r = 0; r < KB; ++r) Rk[r][c] = col[r];
+        __syncthreads();
+        const double ri = rinv[j];
+        for (int c = j + 1 + threadIdx.x; c < KB; c += blockDim.x) Rk[j][c] *= ri;
+        __syncthreads();
+        for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
+            int r = e / KB, c = e % KB;
+            if (r > j && c >= r) Rk[r][c] -= Rk[j][r] * Rk[j][c];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (blockIdx.x == 0) {
         double *Rb = R + (long long)b * sR;
         for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
@@ -197,7 +193,7 @@ __global__ void __launch_bounds__(128) k_chol_panel(const double *W, long long s
         double acc = w[r];
 #pragma unroll
         for (int l = 0; l < r; ++l) acc -= Rk[l][r] * w[l];
-        w[r] = acc / Rk[r][r];
+        w[r] = acc * rinv[r];
     }
 #pragma unroll
     for (int r = 0; r < KB; ++r)
@@ -304,8 +300,8 @@ __global__ void __launch_bounds__(1024) k_lu_panel(double *A, long long sA, int 
             lusgn[b] *= sg;
         }
         __syncthreads();
-        const double v = Ab[(long long)j * lda + j];
-        for (int i = j + 1 + threadIdx.x; i < N; i += blockDim.x) Ab[(long long)i * lda + j] /= v;
+        const double vinv = 1.0 / Ab[(long long)j * lda + j];
+        for (int i = j + 1 + threadIdx.x; i < N; i += blockDim.x) Ab[(long long)i * lda + j] *= vinv;
         __syncthreads();
         const int w = k0 + kb - j - 1;
         if (w > 0) {
@@ -354,6 +350,7 @@ template <int KB>
 __global__ void __launch_bounds__(128) k_trsm_upper_rhs(double *A, long long sA, int lda, int N, int k0, int kb)
 {
     __shared__ double Uk[KB][KB + 1];
+    __shared__ double uinv[KB];
     const int b = blockIdx.y;
     double *Ab = A + (long long)b * sA;
     for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
@@ -363,6 +360,8 @@ __global__ void __launch_bounds__(128) k_trsm_upper_rhs(double *A, long long sA,
         else if (r == c) v = 1.0;
         Uk[r][c] = v;
     }
+    __syncthreads();
+    if (threadIdx.x < KB) uinv[threadIdx.x] = 1.0 / Uk[threadIdx.x][threadIdx.x];
     __syncthreads();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
@@ -374,7 +373,7 @@ __global__ void __launch_bounds__(128) k_trsm_upper_rhs(double *A, long long sA,
         double acc = w[r];
 #pragma unroll
         for (int l = r + 1; l < KB; ++l) acc -= Uk[r][l] * w[l];
-        w[r] = acc / Uk[r][r];
+        w[r] = acc * uinv[r];
     }
 #pragma unroll
     for (int r = 0; r < KB; ++r)

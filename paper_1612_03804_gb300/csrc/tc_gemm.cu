@@ -47,8 +47,7 @@ constexpr int TMEM_COLS = BN * NACC;
 
 struct TcArgs {
     int N, ldp, nk, batch;
-    float *out_hi, *out_lo;
-    __nv_bfloat16 *out_bf;
+    void *out[3];  // next operand, split in parts (FP32 for split TF32, BF16 otherwise)
     double *out_f64;
     long long s_out, s_f64;
     const int8_t *s_n;
@@ -183,10 +182,18 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
+// Modes: 0 = split TF32 (A in 2 parts, E in 3, five kind::tf32 MMAs per
+// 8-wide K-step); 1 = BF16 (one kind::f16 MMA per 16-wide K-step); 2 = split
+// BF16 (A and E in 3 BF16 parts each, six kind::f16 MMAs per 16-wide K-step).
+template <int MODE> struct ModeCfg;
+template <> struct ModeCfg<0> { static constexpr int NPA = 2, NPB = 3, STAGES = 3, KELEM = 32; static constexpr uint32_t FMT = 2; };
+template <> struct ModeCfg<1> { static constexpr int NPA = 1, NPB = 1, STAGES = 5, KELEM = 64; static constexpr uint32_t FMT = 1; };
+template <> struct ModeCfg<2> { static constexpr int NPA = 3, NPB = 3, STAGES = 3, KELEM = 64; static constexpr uint32_t FMT = 1; };
+
 template <int MODE>
-__host__ __device__ constexpr int stages() { return MODE == 0 ? 3 : 5; }
+__host__ __device__ constexpr int stages() { return ModeCfg<MODE>::STAGES; }
 template <int MODE>
-__host__ __device__ constexpr int stage_bytes() { return MODE == 0 ? 2 * TILE_A + 3 * TILE_B : TILE_A + TILE_B; }
+__host__ __device__ constexpr int stage_bytes() { return ModeCfg<MODE>::NPA * TILE_A + ModeCfg<MODE>::NPB * TILE_B; }
 
 // Persistent kernel: one CTA per SM loops over the 128 x 64 output tiles of
 // the whole batch (tile t = blockIdx.x, blockIdx.x + gridDim.x, ...).
@@ -197,16 +204,20 @@ __host__ __device__ constexpr int stage_bytes() { return MODE == 0 ? 2 * TILE_A 
 // stores while the next tile's operands are already loading.
 constexpr int NTHREADS = 192;
 
+__device__ __forceinline__ __nv_bfloat16 bf16_rn(float x) { return __float2bfloat16_rn(x); }
+
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
-              const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
-              const __grid_constant__ CUtensorMap tB2, TcArgs a)
+              const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
+              const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, TcArgs a)
 {
+    using C = ModeCfg<MODE>;
     constexpr int STAGE_BYTES = stage_bytes<MODE>();
-    constexpr int STAGES = stages<MODE>();
+    constexpr int STAGES = C::STAGES;
     constexpr int KSTEPS = 4;  // 128-byte row / 32 bytes per MMA K-step (8 TF32 or 16 BF16)
-    constexpr uint32_t IDESC = instr_desc(MODE == 0 ? 2u : 1u);
+    constexpr uint32_t IDESC = instr_desc(C::FMT);
+    constexpr bool SPLIT = MODE != 1;  // leading products on accumulators 0..6, corrections on 7
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -245,6 +256,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             int it = 0;  // global k-block counter of this CTA
             bool ok = true;
+            const CUtensorMap *mA[3] = {&tA0, &tA1, &tA2};
+            const CUtensorMap *mB[3] = {&tB0, &tB1, &tB2};
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
                 const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
                 const int n0 = tn * BN, m0 = tm * BM;
@@ -253,16 +266,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, a.flag)) { ok = false; break; }
                     mbar_expect_tx(&full[s], STAGE_BYTES);
                     uint8_t *st = base + s * STAGE_BYTES;
-                    const int k0 = kb * (128 / (MODE == 0 ? 4 : 2));
-                    tma_load_3d(st, &tA0, k0, m0, b, &full[s]);
-                    if (MODE == 0) {
-                        tma_load_3d(st + TILE_A, &tA1, k0, m0, b, &full[s]);
-                        tma_load_2d(st + 2 * TILE_A, &tB0, k0, n0, &full[s]);
-                        tma_load_2d(st + 2 * TILE_A + TILE_B, &tB1, k0, n0, &full[s]);
-                        tma_load_2d(st + 2 * TILE_A + 2 * TILE_B, &tB2, k0, n0, &full[s]);
-                    } else {
-                        tma_load_2d(st + TILE_A, &tB0, k0, n0, &full[s]);
-                    }
+                    const int k0 = kb * C::KELEM;
+#pragma unroll
+                    for (int p = 0; p < C::NPA; ++p) tma_load_3d(st + p * TILE_A, mA[p], k0, m0, b, &full[s]);
+#pragma unroll
+                    for (int q = 0; q < C::NPB; ++q)
+                        tma_load_2d(st + C::NPA * TILE_A + q * TILE_B, mB[q], k0, n0, &full[s]);
                 }
             }
         }
@@ -279,29 +288,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if (!mbar_wait(&full[s], (it / STAGES) & 1, a.flag)) { ok = false; break; }
                     fence_after();
                     const uint32_t sa = smem_u32(base + s * STAGE_BYTES);
+                    const uint32_t sb = sa + C::NPA * TILE_A;
 #pragma unroll
                     for (int k = 0; k < KSTEPS; ++k) {
                         const uint32_t off = k * 32;
                         const int g = kb * KSTEPS + k;
-                        if (MODE == 0) {
-                            // A_h E_h round-robin over accumulators 0..6; the four small
-                            // correction products all go to accumulator 7, where their
-                            // rounding is relative to a sum 2^-11 smaller.
+                        if (SPLIT) {
+                            // The leading product round-robin over accumulators 0..6; the
+                            // small correction products all go to accumulator 7, where their
+                            // rounding is relative to a much smaller sum.
                             const uint32_t acc_main = tmem + (uint32_t)((g % (NACC - 1)) * BN);
                             const uint32_t acc_small = tmem + (uint32_t)((NACC - 1) * BN);
-                            const uint64_t ah = smem_desc(sa + off), al = smem_desc(sa + TILE_A + off);
-                            const uint32_t sb = sa + 2 * TILE_A + off;
-                            const uint64_t eh = smem_desc(sb), em = smem_desc(sb + TILE_B),
-                                           el = smem_desc(sb + 2 * TILE_B);
-                            mma<0>(acc_main, ah, eh, IDESC, g < NACC - 1 ? 0u : 1u);
-                            mma<0>(acc_small, ah, em, IDESC, g == 0 ? 0u : 1u);
-                            mma<0>(acc_small, al, eh, IDESC, 1u);
-                            mma<0>(acc_small, ah, el, IDESC, 1u);
-                            mma<0>(acc_small, al, em, IDESC, 1u);
+                            const uint64_t a0 = smem_desc(sa + off), a1 = smem_desc(sa + TILE_A + off);
+                            const uint64_t e0 = smem_desc(sb + off), e1 = smem_desc(sb + TILE_B + off),
+                                           e2 = smem_desc(sb + 2 * TILE_B + off);
+                            mma<MODE == 0 ? 0 : 1>(acc_main, a0, e0, IDESC, g < NACC - 1 ? 0u : 1u);
+                            mma<MODE == 0 ? 0 : 1>(acc_small, a0, e1, IDESC, g == 0 ? 0u : 1u);
+                            mma<MODE == 0 ? 0 : 1>(acc_small, a1, e0, IDESC, 1u);
+                            mma<MODE == 0 ? 0 : 1>(acc_small, a0, e2, IDESC, 1u);
+                            mma<MODE == 0 ? 0 : 1>(acc_small, a1, e1, IDESC, 1u);
+                            if (MODE == 2) {
+                                const uint64_t a2 = smem_desc(sa + 2 * TILE_A + off);
+                                mma<1>(acc_small, a2, e0, IDESC, 1u);
+                            }
                         } else {
                             const uint32_t acc_t = tmem + (uint32_t)((g % NACC) * BN);
-                            mma<1>(acc_t, smem_desc(sa + off), smem_desc(sa + TILE_A + off), IDESC,
-                                   g < NACC ? 0u : 1u);
+                            mma<1>(acc_t, smem_desc(sa + off), smem_desc(sb + off), IDESC, g < NACC ? 0u : 1u);
                         }
                     }
                     mma_commit(&empty[s]);
@@ -313,7 +325,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // epilogue warps 2..5
         const int q4 = warp & 3;
         const int row = q4 * 32 + lane;
-        const uint32_t used_mask = MODE == 0
+        const uint32_t used_mask = SPLIT
                                        ? (((1u << (ksteps < NACC - 1 ? ksteps : NACC - 1)) - 1u) | (1u << (NACC - 1)))
                                        : ((1u << (ksteps < NACC ? ksteps : NACC)) - 1u);
         int ti = 0;
@@ -351,41 +363,57 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     continue;
                 }
-                float hi[16], lo[16];
+                const long long o = (long long)b * a.s_out + (long long)m * a.ldp + nb;
+                float p0[16], p1[16], p2[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     // y = v * d with d = dh + dl: yh = fl(v dh), ye = the rounding error of
                     // that product (exact by FMA) plus v dl.
                     float yh = v[j], ye = 0.0f;
-                    if (sn) {
-                        const bool up = (nb + j < a.N) && sn[nb + j] > 0;
+                    if (sn && nb + j < a.N) {
+                        const bool up = sn[nb + j] > 0;
                         const float dh = up ? a.cu_h : a.cd_h, dl = up ? a.cu_l : a.cd_l;
                         yh = v[j] * dh;
                         ye = fmaf(v[j], dh, -yh) + v[j] * dl;
                     }
                     if (MODE == 0) {
-                        hi[j] = to_tf32(yh);
-                        lo[j] = to_tf32((yh - hi[j]) + ye);
+                        p0[j] = to_tf32(yh);
+                        p1[j] = to_tf32((yh - p0[j]) + ye);
+                    } else if (MODE == 1) {
+                        p0[j] = __bfloat162float(bf16_rn(yh + ye));
                     } else {
-                        hi[j] = yh + ye;
+                        p0[j] = __bfloat162float(bf16_rn(yh));
+                        const float r1 = (yh - p0[j]) + ye;
+                        p1[j] = __bfloat162float(bf16_rn(r1));
+                        p2[j] = __bfloat162float(bf16_rn(r1 - p1[j]));
                     }
                 }
-                const long long o = (long long)b * a.s_out + (long long)m * a.ldp + nb;
-                if (MODE == 0) {
-                    if (full16) {
+                const int nparts = MODE == 0 ? 2 : (MODE == 1 ? 1 : 3);
 #pragma unroll
-                        for (int j = 0; j < 16; j += 4) {
-                            *reinterpret_cast<float4 *>(a.out_hi + o + j) = make_float4(hi[j], hi[j + 1], hi[j + 2], hi[j + 3]);
-                            *reinterpret_cast<float4 *>(a.out_lo + o + j) = make_float4(lo[j], lo[j + 1], lo[j + 2], lo[j + 3]);
+                for (int part = 0; part < 3; ++part) {
+                    if (part >= nparts) break;
+                    const float *src = part == 0 ? p0 : (part == 1 ? p1 : p2);
+                    if (MODE == 0) {
+                        float *dst = static_cast<float *>(a.out[part]) + o;
+                        if (full16) {
+#pragma unroll
+                            for (int j = 0; j < 16; j += 4)
+                                *reinterpret_cast<float4 *>(dst + j) = make_float4(src[j], src[j + 1], src[j + 2], src[j + 3]);
+                        } else {
+                            for (int j = 0; j < 16 && nb + j < a.N; ++j) dst[j] = src[j];
                         }
                     } else {
-                        for (int j = 0; j < 16 && nb + j < a.N; ++j) {
-                            a.out_hi[o + j] = hi[j];
-                            a.out_lo[o + j] = lo[j];
+                        __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(a.out[part]) + o;
+                        if (full16) {
+                            __nv_bfloat162 h2[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(src[2 * j], src[2 * j + 1]);
+                            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(&h2[0]);
+                            *reinterpret_cast<uint4 *>(dst + 8) = *reinterpret_cast<const uint4 *>(&h2[4]);
+                        } else {
+                            for (int j = 0; j < 16 && nb + j < a.N; ++j) dst[j] = bf16_rn(src[j]);
                         }
                     }
-                } else {
-                    for (int j = 0; j < 16 && nb + j < a.N; ++j) a.out_bf[o + j] = __float2bfloat16_rn(hi[j]);
                 }
             }
             // hand the accumulators back to the MMA thread
@@ -401,35 +429,46 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-// Operand of the first product of a block: Ut diag(d_first), split.
+// Split of an FP64 matrix (times an optional K-index field scale) into the
+// operand parts of a mode: the first product of a block (Ut diag(d_first))
+// and, once per context, E itself.
 template <int MODE>
-__global__ void k_tc_prep(const double *Ut, long long nn, int N, int ldp, const int8_t *s_k, long long sSk, double cu,
-                          double cd, float *hi, float *lo, __nv_bfloat16 *bf, long long s_out)
+__global__ void k_tc_split(const double *X, long long sX, int N, int ldp, const int8_t *s_k, long long sSk, double cu,
+                           double cd, void *o0, void *o1, void *o2, long long s_out, int e_parts)
 {
     const int b = blockIdx.z, m = blockIdx.y;
     const int8_t *sk = s_k ? s_k + (long long)b * sSk : nullptr;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
-        double v = Ut[(long long)b * nn + (long long)m * N + k];
+        double v = X[(long long)b * sX + (long long)m * N + k];
         if (sk) v *= (sk[k] > 0 ? cu : cd);
         const long long o = (long long)b * s_out + (long long)m * ldp + k;
         if (MODE == 0) {
             const float h = to_tf32((float)v);
-            hi[o] = h;
-            lo[o] = to_tf32((float)(v - (double)h));
+            const double r1 = v - (double)h;
+            const float mid = to_tf32((float)r1);
+            static_cast<float *>(o0)[o] = h;
+            static_cast<float *>(o1)[o] = mid;
+            if (e_parts == 3) static_cast<float *>(o2)[o] = to_tf32((float)(r1 - (double)mid));
+        } else if (MODE == 1) {
+            static_cast<__nv_bfloat16 *>(o0)[o] = bf16_rn((float)v);
         } else {
-            bf[o] = __float2bfloat16_rn((float)v);
+            const __nv_bfloat16 p0 = bf16_rn((float)v);
+            const double r1 = v - (double)__bfloat162float(p0);
+            const __nv_bfloat16 p1 = bf16_rn((float)r1);
+            const __nv_bfloat16 p2 = bf16_rn((float)(r1 - (double)__bfloat162float(p1)));
+            static_cast<__nv_bfloat16 *>(o0)[o] = p0;
+            static_cast<__nv_bfloat16 *>(o1)[o] = p1;
+            static_cast<__nv_bfloat16 *>(o2)[o] = p2;
         }
     }
 }
 
 struct TcWs {
-    int ldp;
-    size_t part_elems;  // per operand part: cap * N * ldp
-    float *opf[2][2];   // [buffer][hi/lo]
-    __nv_bfloat16 *opb[2];
-    float *Ep[3];            // E split in three TF32 parts
-    __nv_bfloat16 *Ebf;
-    CUtensorMap mapA[2][2];  // [buffer][part]
+    int mode, ldp, npa, npb, esz;
+    size_t part_elems;       // per operand part: cap * N * ldp
+    void *op[2][3];          // [ping-pong buffer][part]
+    void *Ep[3];             // E in parts
+    CUtensorMap mapA[2][3];  // [buffer][part]
     CUtensorMap mapB[3];     // [part]
     void *mem;
     int num_sms;
@@ -470,21 +509,23 @@ constexpr size_t smem_bytes()
     return (size_t)stages<MODE>() * stage_bytes<MODE>() + 1024 + 256;  // stages, alignment, barriers
 }
 
-// E = E_h + E_m + E_l, each part TF32-rounded.
-__global__ void k_split_E3(const double *E, int N, int ldp, float *h, float *mid, float *l)
+int mode_of(const sldqmc_ctx *c) { return c->p.prec == SLDQMC_3XTF32 ? 0 : (c->p.prec == SLDQMC_BF16 ? 1 : 2); }
+
+template <int MODE>
+void launch_split(sldqmc_ctx *c, const TcWs *w, const double *X, long long sX, int B, const int8_t *s_k, long long sSk,
+                  double cu, double cd, void *const *o, long long s_out, int e_parts)
 {
-    const int m = blockIdx.y;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
-        const double v = E[(long long)m * N + k];
-        const float a = to_tf32((float)v);
-        const double r1 = v - (double)a;
-        const float b2 = to_tf32((float)r1);
-        const float c3 = to_tf32((float)(r1 - (double)b2));
-        const long long o = (long long)m * ldp + k;
-        h[o] = a;
-        mid[o] = b2;
-        l[o] = c3;
-    }
+    dim3 g((c->N + 255) / 256, c->N, B);
+    k_tc_split<MODE><<<g, 256, 0, c->st>>>(X, sX, c->N, w->ldp, s_k, sSk, cu, cd, o[0], o[1], o[2], s_out, e_parts);
+    c->launches++;
+}
+
+template <int MODE>
+void launch_gemm(sldqmc_ctx *c, const TcWs *w, int src, int grid, const TcArgs &a)
+{
+    const CUtensorMap *A = w->mapA[src];
+    k_tc_gemm<MODE><<<grid, NTHREADS, smem_bytes<MODE>(), c->st>>>(A[0], A[1], A[2], w->mapB[0], w->mapB[1], w->mapB[2],
+                                                                   a);
 }
 
 }  // namespace
@@ -497,7 +538,7 @@ void launch_wait_selftest(sldqmc_ctx *c, int limit)
 
 int tc_prepare(sldqmc_ctx *c)
 {
-    if (c->N < BM) return SLDQMC_ERR_UNSUPPORTED;  // tensor-core tiles are 128 x 128
+    if (c->N < BM) return SLDQMC_ERR_UNSUPPORTED;  // tensor-core tiles are 128 x 64
     TcWs *w = new TcWs();
     c->tc_ws = w;
     {
@@ -508,13 +549,14 @@ int tc_prepare(sldqmc_ctx *c)
             w->num_sms = 148;
     }
     const int N = c->N;
+    w->mode = mode_of(c);
     w->ldp = (N + 63) / 64 * 64;
-    const bool bf = c->p.prec == SLDQMC_BF16;
+    w->npa = w->mode == 0 ? 2 : (w->mode == 1 ? 1 : 3);
+    w->npb = w->mode == 0 ? 3 : (w->mode == 1 ? 1 : 3);
+    w->esz = w->mode == 0 ? 4 : 2;
+    const bool bf = w->mode != 0;
     w->part_elems = (size_t)c->cap * N * w->ldp;
-    const size_t esz = bf ? 2 : 4;
-    const size_t parts = bf ? 2 : 4;              // operand buffers
-    const size_t eparts = bf ? 1 : 3;             // E copies
-    const size_t bytes = esz * (parts * w->part_elems + eparts * (size_t)N * w->ldp);
+    const size_t bytes = (size_t)w->esz * (2 * w->npa * w->part_elems + (size_t)w->npb * N * w->ldp);
     if (cudaMalloc(&w->mem, bytes) != cudaSuccess) {
         cudaGetLastError();
         w->mem = nullptr;
@@ -522,36 +564,30 @@ int tc_prepare(sldqmc_ctx *c)
     }
     cudaMemset(w->mem, 0, bytes);  // zero pads: columns N..ldp-1 are never written
     uint8_t *q = (uint8_t *)w->mem;
-    if (!bf) {
-        for (int i = 0; i < 2; ++i)
-            for (int p = 0; p < 2; ++p) {
-                w->opf[i][p] = (float *)q;
-                q += esz * w->part_elems;
-            }
+    for (int i = 0; i < 2; ++i)
         for (int p = 0; p < 3; ++p) {
-            w->Ep[p] = (float *)q;
-            q += esz * (size_t)N * w->ldp;
+            if (p < w->npa) {
+                w->op[i][p] = q;
+                q += w->esz * w->part_elems;
+                if (!encode(&w->mapA[i][p], w->op[i][p], bf, 3, w->ldp, N, c->cap, BM)) return SLDQMC_ERR_CUDA;
+            } else {
+                w->op[i][p] = nullptr;
+                w->mapA[i][p] = w->mapA[i][0];
+            }
         }
-        for (int i = 0; i < 2; ++i)
-            for (int p = 0; p < 2; ++p)
-                if (!encode(&w->mapA[i][p], w->opf[i][p], false, 3, w->ldp, N, c->cap, BM)) return SLDQMC_ERR_CUDA;
-        for (int p = 0; p < 3; ++p)
-            if (!encode(&w->mapB[p], w->Ep[p], false, 2, w->ldp, N, 1, BN)) return SLDQMC_ERR_CUDA;
-    } else {
-        for (int i = 0; i < 2; ++i) {
-            w->opb[i] = (__nv_bfloat16 *)q;
-            q += esz * w->part_elems;
+    for (int p = 0; p < 3; ++p) {
+        if (p < w->npb) {
+            w->Ep[p] = q;
+            q += (size_t)w->esz * N * w->ldp;
+            if (!encode(&w->mapB[p], w->Ep[p], bf, 2, w->ldp, N, 1, BN)) return SLDQMC_ERR_CUDA;
+        } else {
+            w->Ep[p] = nullptr;
+            w->mapB[p] = w->mapB[0];
         }
-        w->Ebf = (__nv_bfloat16 *)q;
-        for (int i = 0; i < 2; ++i) {
-            if (!encode(&w->mapA[i][0], w->opb[i], true, 3, w->ldp, N, c->cap, BM)) return SLDQMC_ERR_CUDA;
-            w->mapA[i][1] = w->mapA[i][0];
-        }
-        if (!encode(&w->mapB[0], w->Ebf, true, 2, w->ldp, N, 1, BN)) return SLDQMC_ERR_CUDA;
-        w->mapB[1] = w->mapB[2] = w->mapB[0];
     }
     cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<0>());
     cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1>());
+    cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2>());
     return SLDQMC_OK;
 }
 
@@ -567,13 +603,10 @@ void tc_release(sldqmc_ctx *c)
 void tc_convert_E(sldqmc_ctx *c)
 {
     TcWs *w = (TcWs *)c->tc_ws;
-    const int N = c->N;
-    dim3 g((N + 255) / 256, N, 1);
-    if (c->p.prec == SLDQMC_BF16)
-        k_tc_prep<1><<<g, 256, 0, c->st>>>(c->d_E, c->nn, N, w->ldp, nullptr, 0, 1.0, 1.0, nullptr, nullptr, w->Ebf, 0);
-    else
-        k_split_E3<<<g, 256, 0, c->st>>>(c->d_E, N, w->ldp, w->Ep[0], w->Ep[1], w->Ep[2]);
-    c->launches++;
+    void *o[3] = {w->Ep[0], w->Ep[1], w->Ep[2]};
+    if (w->mode == 0) launch_split<0>(c, w, c->d_E, 0, 1, nullptr, 0, 1.0, 1.0, o, 0, 3);
+    else if (w->mode == 1) launch_split<1>(c, w, c->d_E, 0, 1, nullptr, 0, 1.0, 1.0, o, 0, 1);
+    else launch_split<2>(c, w, c->d_E, 0, 1, nullptr, 0, 1.0, 1.0, o, 0, 3);
 }
 
 // X^T = Ut D_{s0} E D_{s1} E ... D_{s_{nb-1}} E for one block; result (FP64)
@@ -583,17 +616,15 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
 {
     TcWs *w = (TcWs *)c->tc_ws;
     const int N = c->N, M = c->M;
-    const bool bf = c->p.prec == SLDQMC_BF16;
     const long long sS = (long long)M * N;
     const long long s_out = (long long)N * w->ldp;
-    dim3 gp((N + 255) / 256, N, B);
-    if (bf)
-        k_tc_prep<1><<<gp, 256, 0, c->st>>>(Ut, c->nn, N, w->ldp, d_s + (long long)slices[0] * N, sS, cu, cd, nullptr,
-                                            nullptr, w->opb[0], s_out);
-    else
-        k_tc_prep<0><<<gp, 256, 0, c->st>>>(Ut, c->nn, N, w->ldp, d_s + (long long)slices[0] * N, sS, cu, cd,
-                                            w->opf[0][0], w->opf[0][1], nullptr, s_out);
-    c->launches++;
+    {
+        void *o[3] = {w->op[0][0], w->op[0][1], w->op[0][2]};
+        const int8_t *sk = d_s + (long long)slices[0] * N;
+        if (w->mode == 0) launch_split<0>(c, w, Ut, c->nn, B, sk, sS, cu, cd, o, s_out, 2);
+        else if (w->mode == 1) launch_split<1>(c, w, Ut, c->nn, B, sk, sS, cu, cd, o, s_out, 1);
+        else launch_split<2>(c, w, Ut, c->nn, B, sk, sS, cu, cd, o, s_out, 3);
+    }
     const int tiles = ((N + BN - 1) / BN) * ((N + BM - 1) / BM) * B;
     const int grid = tiles < w->num_sms ? tiles : w->num_sms;
     for (int j = 0; j < nb; ++j) {
@@ -601,7 +632,7 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
         TcArgs a{};
         a.N = N;
         a.ldp = w->ldp;
-        a.nk = w->ldp / (bf ? 64 : 32);
+        a.nk = w->ldp / (w->mode == 0 ? 32 : 64);
         a.batch = B;
         a.s_out = s_out;
         a.s_f64 = c->nn;
@@ -615,16 +646,12 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
             a.cu_l = (float)(cu - (double)a.cu_h);
             a.cd_h = (float)cd;
             a.cd_l = (float)(cd - (double)a.cd_h);
-            if (bf) a.out_bf = w->opb[dst];
-            else { a.out_hi = w->opf[dst][0]; a.out_lo = w->opf[dst][1]; }
+            for (int p = 0; p < 3; ++p) a.out[p] = w->op[dst][p];
         }
         prof_begin(c, SLDQMC_KC_GEMM_TC, 2.0 * (double)N * N * N * B);
-        if (bf)
-            k_tc_gemm<1><<<grid, NTHREADS, smem_bytes<1>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
-                                                                w->mapB[1], w->mapB[2], a);
-        else
-            k_tc_gemm<0><<<grid, NTHREADS, smem_bytes<0>(), c->st>>>(w->mapA[src][0], w->mapA[src][1], w->mapB[0],
-                                                                w->mapB[1], w->mapB[2], a);
+        if (w->mode == 0) launch_gemm<0>(c, w, src, grid, a);
+        else if (w->mode == 1) launch_gemm<1>(c, w, src, grid, a);
+        else launch_gemm<2>(c, w, src, grid, a);
         prof_end(c);
         c->launches++;
     }

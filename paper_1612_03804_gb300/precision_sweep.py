@@ -40,7 +40,7 @@ def sweep(args):
     out = []
     for nw in (5, 10, 20):
         res = {}
-        for prec in ("fp64", "3xtf32", "bf16"):
+        for prec in ("fp64", "3xtf32", "bf16x3", "bf16"):
             with sldqmc.Context(L, L, mu=mu, xi=1.0, beta=beta, dtau=dtau, n_wrap=nw, prec=prec,
                                 max_batch=args.fields) as ctx:
                 ld = torch.zeros(args.fields, dtype=torch.float64, device="cuda")
@@ -57,7 +57,7 @@ def sweep(args):
                 res[prec] = (ld.cpu().numpy(), G.cpu().numpy()[0], float(lu.item()), dt)
         ref_ld, ref_G = res["fp64"][0], res["fp64"][1]
         cf = closed_form(L, beta, 1.0, mu - 1.0)  # eta = -1, s = +1: mu -> mu - xi
-        for prec in ("fp64", "3xtf32", "bf16"):
+        for prec in ("fp64", "3xtf32", "bf16x3", "bf16"):
             ld, G, lu, dt = res[prec]
             out.append({"n_wrap": nw, "prec": prec,
                         "logdet_rel_err_max": float(np.max(np.abs(ld - ref_ld) / np.abs(ref_ld))),

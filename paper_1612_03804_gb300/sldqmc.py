@@ -18,8 +18,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "sldqmc.h")
 OK = 0
 ERRORS = {-1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_NUMERICAL", -5: "ERR_TIMEOUT",
           -6: "ERR_UNSUPPORTED"}
-FP64, TF32X3, BF16 = 0, 1, 2
-PREC = {"fp64": FP64, "3xtf32": TF32X3, "bf16": BF16}
+FP64, TF32X3, BF16, BF16X3 = 0, 1, 2, 3
+PREC = {"fp64": FP64, "3xtf32": TF32X3, "bf16": BF16, "bf16x3": BF16X3}
 
 _lib = None
 

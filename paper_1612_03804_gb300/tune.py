@@ -20,7 +20,7 @@ import math
 
 LADDER = (2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 25, 32, 40, 50, 64)
 LIMIT = 16.0
-TOL = {"fp64": 1e-9, "3xtf32": 1e-6, "bf16": 1e-2}
+TOL = {"fp64": 1e-9, "3xtf32": 1e-6, "bf16": 1e-2, "bf16x3": 1e-6}
 
 
 def candidates(M, dtau, t=1.0, xi=1.0, limit=LIMIT):

@@ -11,8 +11,8 @@ from paper_1612_03804_gb300.inputs import batch_uniform, uniform_field
 
 pytestmark = pytest.mark.gpu
 
-BOUND = {"3xtf32": 1e-6, "bf16": 1e-2}
-G_BOUND = {"3xtf32": 1e-5, "bf16": 5e-2}
+BOUND = {"3xtf32": 1e-6, "bf16": 1e-2, "bf16x3": 1e-6}
+G_BOUND = {"3xtf32": 1e-5, "bf16": 5e-2, "bf16x3": 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,7 +28,7 @@ def _ctx(L, beta, dtau, mu, nw, prec, max_batch=2):
     return sldqmc.Context(L, L, mu=mu, xi=1.0, beta=beta, dtau=dtau, n_wrap=nw, prec=prec, max_batch=max_batch)
 
 
-@pytest.mark.parametrize("prec", ["3xtf32", "bf16"])
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16", "bf16x3"])
 def test_single_product_block_against_oracle(prec):
     """n_wrap = 1: every block is one tensor-core product; 12x12 has a ragged 128-tile."""
     m = O.Model(12, 12, mu=-0.5, xi=1.0, beta=1.0, dtau=0.1, n_wrap=1)
@@ -41,7 +41,7 @@ def test_single_product_block_against_oracle(prec):
             assert abs(ld - ref) <= BOUND[prec] * abs(ref), (prec, eta, ld, ref)
 
 
-@pytest.mark.parametrize("prec", ["3xtf32", "bf16"])
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16", "bf16x3"])
 @pytest.mark.parametrize("L,beta,dtau,nw", [(16, 8.0, 0.05, 10), (12, 4.0, 0.05, 20)])
 def test_against_fp64_path(prec, L, beta, dtau, nw):
     fields = batch_uniform(11, 3, int(round(beta / dtau)), L * L)
@@ -60,7 +60,7 @@ def test_against_fp64_path(prec, L, beta, dtau, nw):
         assert err <= G_BOUND[prec]
 
 
-@pytest.mark.parametrize("prec", ["3xtf32", "bf16"])
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16", "bf16x3"])
 def test_uniform_field_closed_form(prec):
     L, beta, dtau, mu = 16, 8.0, 0.05, -0.5
     M = int(round(beta / dtau))
