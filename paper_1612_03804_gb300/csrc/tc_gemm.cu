@@ -175,6 +175,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The same load without the wait: several loads share one tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// Waits for outstanding tcgen05.ld and makes the 32 loaded registers outputs
+// of the wait, so that no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t a[16], uint32_t b[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                   "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]),
+                   "+r"(a[15]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]),
+                   "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]),
+                   "+r"(b[14]), "+r"(b[15])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ float to_tf32(float x)
 {
     uint32_t r;
@@ -338,16 +362,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 float v[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = 0.0f;
                 const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c0;
-                for (int q = 0; q < NACC; ++q) {
-                    if (!((used_mask >> q) & 1u)) continue;
-                    uint32_t r[16];
-                    tmem_ld16(lane_base + (uint32_t)(q * BN), r);
+                {
+                    // accumulators loaded in pairs, one wait per pair (every
+                    // accumulator received MMAs: K >= 128)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
+                    for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < NACC; q += 2) {
+                        uint32_t r0[16], r1[16];
+                        tmem_ld16_nowait(lane_base + (uint32_t)(q * BN), r0);
+                        tmem_ld16_nowait(lane_base + (uint32_t)((q + 1) * BN), r1);
+                        tmem_wait_ld32(r0, r1);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    }
                 }
+                (void)used_mask;
                 if (!ok || m >= a.N) continue;
                 const int nb = n0 + c0;
                 if (nb >= a.N) continue;
