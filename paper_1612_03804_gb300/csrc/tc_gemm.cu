@@ -165,17 +165,8 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// The same load without the wait: several loads share one tcgen05.wait::ld.
+// Load of 16 consecutive 32-bit accumulator columns of this warp's 32 lanes;
+// several loads share one tcgen05.wait::ld.
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16])
 {
     asm volatile(
@@ -227,6 +218,7 @@ __host__ __device__ constexpr int stage_bytes() { return ModeCfg<MODE>::NPA * TI
 // (TMEM lane quarter = warp % 4), scale, re-split and store with vector
 // stores while the next tile's operands are already loading.
 constexpr int NTHREADS = 192;
+constexpr int STG_FLOATS = 32 * 9 * 2;  // per-warp staging block: 32 rows x 17 floats, or 32 x 9 doubles
 
 __device__ __forceinline__ __nv_bfloat16 bf16_rn(float x) { return __float2bfloat16_rn(x); }
 
@@ -349,6 +341,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // epilogue warps 2..5
         const int q4 = warp & 3;
         const int row = q4 * 32 + lane;
+        float *stg = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(tmem_slot) + 16) + (warp - 2) * STG_FLOATS;
         const uint32_t used_mask = SPLIT
                                        ? (((1u << (ksteps < NACC - 1 ? ksteps : NACC - 1)) - 1u) | (1u << (NACC - 1)))
                                        : ((1u << (ksteps < NACC ? ksteps : NACC)) - 1u);
@@ -356,7 +349,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
             const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
             const int n0 = tn * BN, m0 = tm * BM;
-            const int m = m0 + row;
             const bool ok = mbar_wait(tmem_full, ti & 1, a.flag);
             fence_after();
             const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
@@ -379,22 +371,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 (void)used_mask;
-                if (!ok || m >= a.N) continue;
                 const int nb = n0 + c0;
-                if (nb >= a.N) continue;
-                const bool full16 = nb + 16 <= a.N;
+                if (!ok || nb >= a.N) continue;  // uniform over the warp
+                // Stores go through a per-warp 32-row staging block so that each
+                // warp store instruction writes whole 64-byte row segments.
+                const int r0 = m0 + q4 * 32;
                 if (a.out_f64) {
-                    double *o = a.out_f64 + (long long)b * a.s_f64 + (long long)m * a.N + nb;
-                    if (full16 && (a.N & 1) == 0) {
+                    double *sd = reinterpret_cast<double *>(stg);
 #pragma unroll
-                        for (int j = 0; j < 16; j += 2)
-                            *reinterpret_cast<double2 *>(o + j) = make_double2((double)v[j], (double)v[j + 1]);
-                    } else {
-                        for (int j = 0; j < 16 && nb + j < a.N; ++j) o[j] = (double)v[j];
+                    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) sd[lane * 9 + j] = (double)v[half * 8 + j];
+                        __syncwarp();
+#pragma unroll
+                        for (int it = 0; it < 2; ++it) {
+                            const int rr = it * 16 + (lane >> 1), cc = (lane & 1) * 4;
+                            const int mm = r0 + rr, n = nb + half * 8 + cc;
+                            if (mm < a.N && n < a.N) {
+                                double *o = a.out_f64 + (long long)b * a.s_f64 + (long long)mm * a.N + n;
+                                const double *src = sd + rr * 9 + cc;
+                                if (n + 4 <= a.N && (((long long)mm * a.N + n) & 1) == 0) {
+                                    *reinterpret_cast<double2 *>(o) = make_double2(src[0], src[1]);
+                                    *reinterpret_cast<double2 *>(o + 2) = make_double2(src[2], src[3]);
+                                } else {
+                                    for (int k = 0; k < 4 && n + k < a.N; ++k) o[k] = src[k];
+                                }
+                            }
+                        }
+                        __syncwarp();
                     }
                     continue;
                 }
-                const long long o = (long long)b * a.s_out + (long long)m * a.ldp + nb;
                 float p0[16], p1[16], p2[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -419,32 +426,36 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         p2[j] = __bfloat162float(bf16_rn(r1 - p1[j]));
                     }
                 }
-                const int nparts = MODE == 0 ? 2 : (MODE == 1 ? 1 : 3);
+                constexpr int NPARTS = MODE == 0 ? 2 : (MODE == 1 ? 1 : 3);
 #pragma unroll
-                for (int part = 0; part < 3; ++part) {
-                    if (part >= nparts) break;
-                    const float *src = part == 0 ? p0 : (part == 1 ? p1 : p2);
-                    if (MODE == 0) {
-                        float *dst = static_cast<float *>(a.out[part]) + o;
-                        if (full16) {
+                for (int part = 0; part < NPARTS; ++part) {
 #pragma unroll
-                            for (int j = 0; j < 16; j += 4)
-                                *reinterpret_cast<float4 *>(dst + j) = make_float4(src[j], src[j + 1], src[j + 2], src[j + 3]);
-                        } else {
-                            for (int j = 0; j < 16 && nb + j < a.N; ++j) dst[j] = src[j];
-                        }
-                    } else {
-                        __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(a.out[part]) + o;
-                        if (full16) {
-                            __nv_bfloat162 h2[8];
+                    for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = part == 0 ? p0[j] : (part == 1 ? p1[j] : p2[j]);
+                    __syncwarp();
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(src[2 * j], src[2 * j + 1]);
-                            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(&h2[0]);
-                            *reinterpret_cast<uint4 *>(dst + 8) = *reinterpret_cast<const uint4 *>(&h2[4]);
-                        } else {
-                            for (int j = 0; j < 16 && nb + j < a.N; ++j) dst[j] = bf16_rn(src[j]);
+                    for (int it = 0; it < 4; ++it) {
+                        const int rr = it * 8 + (lane >> 2), cc = (lane & 3) * 4;
+                        const int mm = r0 + rr, n = nb + cc;
+                        if (mm < a.N && n < a.N) {
+                            const float *src = stg + rr * 17 + cc;
+                            const long long o = (long long)b * a.s_out + (long long)mm * a.ldp + n;
+                            if (MODE == 0) {
+                                float *dst = static_cast<float *>(a.out[part]) + o;
+                                if (n + 4 <= a.N) *reinterpret_cast<float4 *>(dst) = make_float4(src[0], src[1], src[2], src[3]);
+                                else for (int k = 0; k < 4 && n + k < a.N; ++k) dst[k] = src[k];
+                            } else {
+                                __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(a.out[part]) + o;
+                                if (n + 4 <= a.N) {
+                                    __nv_bfloat162 h2[2] = {__floats2bfloat162_rn(src[0], src[1]),
+                                                            __floats2bfloat162_rn(src[2], src[3])};
+                                    *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(&h2[0]);
+                                } else {
+                                    for (int k = 0; k < 4 && n + k < a.N; ++k) dst[k] = bf16_rn(src[k]);
+                                }
+                            }
                         }
                     }
+                    __syncwarp();
                 }
             }
             // hand the accumulators back to the MMA thread
@@ -537,7 +548,8 @@ bool encode(CUtensorMap *map, void *ptr, bool bf16, int rank, int ldp, int rows,
 template <int MODE>
 constexpr size_t smem_bytes()
 {
-    return (size_t)stages<MODE>() * stage_bytes<MODE>() + 1024 + 256;  // stages, alignment, barriers
+    // stages, alignment, barriers, four per-warp staging blocks
+    return (size_t)stages<MODE>() * stage_bytes<MODE>() + 1024 + 256 + 4 * STG_FLOATS * sizeof(float);
 }
 
 int mode_of(const sldqmc_ctx *c) { return c->p.prec == SLDQMC_3XTF32 ? 0 : (c->p.prec == SLDQMC_BF16 ? 1 : 2); }
