@@ -340,7 +340,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else {
         // epilogue warps 2..5
         const int q4 = warp & 3;
-        const int row = q4 * 32 + lane;
         float *stg = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(tmem_slot) + 16) + (warp - 2) * STG_FLOATS;
         const uint32_t used_mask = SPLIT
                                        ? (((1u << (ksteps < NACC - 1 ? ksteps : NACC - 1)) - 1u) | (1u << (NACC - 1)))
