@@ -126,4 +126,7 @@ struct sldqmc_ctx {
     sldqmc::Prof *prof;
     const uint32_t *step_dev;  // when set (graph capture), kernels read the MC step from here
     uint32_t *d_step;          // this context's device step counter
+    sldqmc_ctx *twin;          // second workspace + stream: the other flavour's weight runs concurrently
+    cudaEvent_t ev_fork, ev_join;
+    int no_twin;               // set on a twin itself, or when the twin could not be created
 };

@@ -5,6 +5,7 @@
 // rounded operations so that it matches a plain IEEE evaluation.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <string.h>
 
 #include "internal.h"
 
@@ -203,10 +204,25 @@ __global__ void k_drift(const double *Gw, const double *Gf, long long nn, long l
 }
 
 // ------------------------------------------------------ effective model
-// Offsets of the classes live in constant memory: n_off[c] triples each.
-__constant__ int c_noff[32];
-__constant__ int c_off[64 * 3];
-__constant__ double c_J[32];
+// The model of one context travels with each launch as a kernel parameter
+// (constant bank): class c has noff[c] offset triples (dx, dy, dtau), listed
+// class after class in off, and coupling J[c].
+struct EffModel {
+    int n_class;
+    int noff[32];
+    int off[64 * 3];
+    double J[32];
+};
+
+static EffModel eff_model_of(const sldqmc_ctx *c)
+{
+    EffModel m;
+    m.n_class = c->n_class;
+    memcpy(m.noff, c->h_n_off, sizeof(m.noff));
+    memcpy(m.off, c->h_offsets, sizeof(m.off));
+    memcpy(m.J, c->h_J, sizeof(m.J));
+    return m;
+}
 
 __device__ __forceinline__ int shift_site(int v, int N, int Lx, int Ly, int M, const int *o, int sg)
 {
@@ -219,7 +235,7 @@ __device__ __forceinline__ int shift_site(int v, int N, int Lx, int Ly, int M, c
 // neighbour sums (self-pairs excluded), accumulated in class order.
 template <bool SMEM>
 __global__ void __launch_bounds__(1024) k_eff_sweeps(int8_t *s_all, int Lx, int Ly, int M, double beta,
-                                                     int n_class, const int *col_start,
+                                                     const __grid_constant__ EffModel em, const int *col_start,
                                                      const int *col_sites, int n_colors, int n_sweeps,
                                                      uint64_t seed, uint32_t step, int dir_fixed,
                                                      long long *n_accept, long long *n_margin,
@@ -248,15 +264,15 @@ __global__ void __launch_bounds__(1024) k_eff_sweeps(int8_t *s_all, int Lx, int 
                 const int v = col_sites[q];
                 double sum = 0.0;
                 int oi = 0;
-                for (int c = 0; c < n_class; ++c) {
+                for (int c = 0; c < em.n_class; ++c) {
                     int n = 0;
-                    for (int t = 0; t < c_noff[c]; ++t, ++oi) {
-                        const int b1 = shift_site(v, N, Lx, Ly, M, c_off + 3 * oi, 1);
-                        const int b2 = shift_site(v, N, Lx, Ly, M, c_off + 3 * oi, -1);
+                    for (int t = 0; t < em.noff[c]; ++t, ++oi) {
+                        const int b1 = shift_site(v, N, Lx, Ly, M, em.off + 3 * oi, 1);
+                        const int b2 = shift_site(v, N, Lx, Ly, M, em.off + 3 * oi, -1);
                         if (b1 != v) n += s[b1];
                         if (b2 != v) n += s[b2];
                     }
-                    sum = __dadd_rn(sum, __dmul_rn(c_J[c], (double)n));
+                    sum = __dadd_rn(sum, __dmul_rn(em.J[c], (double)n));
                 }
                 const int sv = s[v];
                 const double av = __dmul_rn(__dmul_rn(twob, sum), (double)sv);
@@ -292,18 +308,20 @@ __global__ void __launch_bounds__(1024) k_eff_sweeps(int8_t *s_all, int Lx, int 
 
 // f_c(C) = sum_x sum_{o in c} s_x s_{x+o} (self-pairs give 1), one CTA per
 // configuration; out[b*n_class + c].
-__global__ void k_features(const int8_t *s_all, int Lx, int Ly, int M, int n_class, long long *out)
+__global__ void k_features(const int8_t *s_all, int Lx, int Ly, int M, const __grid_constant__ EffModel em,
+                           long long *out)
 {
     const int b = blockIdx.x;
     const int N = Lx * Ly, V = N * M;
     const int8_t *s = s_all + (long long)b * V;
     __shared__ long long red[32];
+    const int n_class = em.n_class;
     int oi = 0;
     for (int c = 0; c < n_class; ++c) {
         long long acc = 0;
-        for (int t = 0; t < c_noff[c]; ++t, ++oi)
+        for (int t = 0; t < em.noff[c]; ++t, ++oi)
             for (int v = threadIdx.x; v < V; v += blockDim.x)
-                acc += s[v] * s[shift_site(v, N, Lx, Ly, M, c_off + 3 * oi, 1)];
+                acc += s[v] * s[shift_site(v, N, Lx, Ly, M, em.off + 3 * oi, 1)];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
         __syncthreads();
@@ -319,16 +337,17 @@ __global__ void k_features(const int8_t *s_all, int Lx, int Ly, int M, int n_cla
 // Eq. 4 in log form, per chain:
 //   log r = [lw1 - lw0] - [-beta sum_c J_c (f1_c - f0_c)],  accept iff log u < log r.
 __global__ void k_cumulative_accept(const double *lw1, double *lw0, const long long *f0, const long long *f1,
-                                    int n_class, double beta, uint64_t seed, uint32_t step, int B,
+                                    const __grid_constant__ EffModel em, double beta, uint64_t seed, uint32_t step, int B,
                                     int *accepted, int *accept_count, double *log_r, long long *margin,
                                     const uint32_t *d_step)
 {
     if (d_step) step = *d_step;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
+    const int n_class = em.n_class;
     double acc = 0.0;
     for (int c = 0; c < n_class; ++c)
-        acc = __dadd_rn(acc, __dmul_rn(c_J[c], (double)(f1[(long long)b * n_class + c] - f0[(long long)b * n_class + c])));
+        acc = __dadd_rn(acc, __dmul_rn(em.J[c], (double)(f1[(long long)b * n_class + c] - f0[(long long)b * n_class + c])));
     const double dlweff = __dmul_rn(-beta, acc);
     const double lr = __dadd_rn(__dadd_rn(lw1[b], -lw0[b]), -dlweff);
     const uint64_t key = seed + ((uint64_t)b << 32);
@@ -392,31 +411,20 @@ void launch_drift(sldqmc_ctx *c, const double *Gw, const double *Gf, int B2x, in
     c->launches++;
 }
 
-int upload_effective_model(sldqmc_ctx *c)
-{
-    if (cudaMemcpyToSymbolAsync(c_noff, c->h_n_off, sizeof(int) * 32, 0, cudaMemcpyHostToDevice, c->st) !=
-            cudaSuccess ||
-        cudaMemcpyToSymbolAsync(c_off, c->h_offsets, sizeof(int) * 64 * 3, 0, cudaMemcpyHostToDevice, c->st) !=
-            cudaSuccess ||
-        cudaMemcpyToSymbolAsync(c_J, c->h_J, sizeof(double) * 32, 0, cudaMemcpyHostToDevice, c->st) !=
-            cudaSuccess)
-        return SLDQMC_ERR_CUDA;
-    return SLDQMC_OK;
-}
-
 void launch_eff_sweeps(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t seed, uint32_t step,
                        int dir, long long *n_accept, long long *n_margin)
 {
     const long long V = (long long)c->N * c->M;
     const int nt = 1024;
+    const EffModel em = eff_model_of(c);
     prof_begin(c, SLDQMC_KC_EFF, 0.0);
     if (V <= 200 * 1024) {
         k_eff_sweeps<true><<<B, nt, (size_t)V, c->st>>>(d_s, c->p.Lx, c->p.Ly, c->M, c->p.beta,
-                                                        c->n_class, c->d_col_start, c->d_col_sites,
+                                                        em, c->d_col_start, c->d_col_sites,
                                                         c->n_colors, n_sweeps, seed, step, dir,
                                                         n_accept, n_margin, c->step_dev);
     } else {
-        k_eff_sweeps<false><<<B, nt, 0, c->st>>>(d_s, c->p.Lx, c->p.Ly, c->M, c->p.beta, c->n_class,
+        k_eff_sweeps<false><<<B, nt, 0, c->st>>>(d_s, c->p.Lx, c->p.Ly, c->M, c->p.beta, em,
                                                  c->d_col_start, c->d_col_sites, c->n_colors, n_sweeps,
                                                  seed, step, dir, n_accept, n_margin, c->step_dev);
     }
@@ -426,7 +434,7 @@ void launch_eff_sweeps(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t
 
 void launch_features(sldqmc_ctx *c, const int8_t *d_s, int B, long long *out)
 {
-    k_features<<<B, 512, 0, c->st>>>(d_s, c->p.Lx, c->p.Ly, c->M, c->n_class, out);
+    k_features<<<B, 512, 0, c->st>>>(d_s, c->p.Lx, c->p.Ly, c->M, eff_model_of(c), out);
     c->launches++;
 }
 
@@ -434,7 +442,7 @@ void launch_cumulative_accept(sldqmc_ctx *c, const double *lw1, double *lw0, con
                               const long long *f1, uint64_t seed, uint32_t step, int B, int *accepted,
                               int *accept_count, double *log_r, long long *margin)
 {
-    k_cumulative_accept<<<cdiv(B, 128), 128, 0, c->st>>>(lw1, lw0, f0, f1, c->n_class, c->p.beta, seed,
+    k_cumulative_accept<<<cdiv(B, 128), 128, 0, c->st>>>(lw1, lw0, f0, f1, eff_model_of(c), c->p.beta, seed,
                                                         step, B, accepted, accept_count, log_r, margin,
                                                         c->step_dev);
     c->launches++;

@@ -25,7 +25,6 @@ void launch_log_bare(sldqmc_ctx *c, const int8_t *d_s, int B, double *out, int a
 void launch_local_flips(sldqmc_ctx *c, double *Gp, double *Gm, int8_t *d_s, int B, int tau,
                         uint32_t sweep, uint64_t seed, long long *stats);
 void launch_drift(sldqmc_ctx *c, const double *Gw, const double *Gf, int B2x, int B, long long *stats);
-int upload_effective_model(sldqmc_ctx *c);
 void launch_eff_sweeps(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t seed, uint32_t step,
                        int dir, long long *n_accept, long long *n_margin);
 void launch_features(sldqmc_ctx *c, const int8_t *d_s, int B, long long *out);
@@ -150,11 +149,16 @@ int flag_to_status(int f)
 int sync_and_flag(sldqmc_ctx *c)
 {
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    if (c->twin && cudaStreamSynchronize(c->twin->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
     if (cudaGetLastError() != cudaSuccess) return SLDQMC_ERR_CUDA;
-    int f = 0;
+    int f = 0, g = 0;
     if (cudaMemcpy(&f, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SLDQMC_ERR_CUDA;
-    if (f) cudaMemset(c->d_flag, 0, sizeof(int));
-    return flag_to_status(f);
+    if (f) cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st);
+    if (c->twin) {
+        if (cudaMemcpy(&g, c->twin->d_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SLDQMC_ERR_CUDA;
+        if (g) cudaMemsetAsync(c->twin->d_flag, 0, sizeof(int), c->twin->st);
+    }
+    return flag_to_status(f | g);
 }
 
 template <typename T>
@@ -220,13 +224,74 @@ int weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, int tau0, doubl
     return SLDQMC_OK;
 }
 
+__global__ void k_add_vec(double *a, const double *b, int B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B) a[i] += b[i];
+}
+
+// A second context with the same parameters and its own stream, used to run
+// the eta = -1 weight concurrently with the eta = +1 weight (independent
+// chains of kernels; each fills the other's launch tails).  Created on first
+// use when its workspace takes under a third of the free device memory;
+// otherwise the flavours run in sequence.
+sldqmc_ctx *get_twin(sldqmc_ctx *c)
+{
+    if (c->no_twin) return nullptr;
+    if (c->twin) return c->twin;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        c->no_twin = 1;
+        return nullptr;
+    }
+    const double ws_bytes = 12.0 * (double)c->nn * 8.0 * c->cap + 2.0 * c->M * (double)c->N * c->cap;
+    if (ws_bytes * 3.0 > (double)free_b) { c->no_twin = 1; return nullptr; }
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->no_twin = 1;
+        return nullptr;
+    }
+    sldqmc_ctx *t = nullptr;
+    sldqmc_params p = c->p;
+    if (sldqmc_create(&p, (void *)st, &t) != SLDQMC_OK ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (t) sldqmc_destroy(t);
+        cudaStreamDestroy(st);
+        cudaGetLastError();
+        c->no_twin = 1;
+        return nullptr;
+    }
+    t->no_twin = 1;
+    c->twin = t;
+    return t;
+}
+
 // log omega = log phi + 2 ld(+1) + 2 ld(-1) into d_lw.
 int log_weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, double *d_lw)
 {
-    int rc = weight_run(c, d_s, B, 1, 0, d_lw, nullptr, nullptr, 2.0, 0);
+    sldqmc_ctx *t = (c->prof && c->prof->on) ? nullptr : get_twin(c);
+    if (!t) {
+        int rc = weight_run(c, d_s, B, 1, 0, d_lw, nullptr, nullptr, 2.0, 0);
+        if (rc) return rc;
+        rc = weight_run(c, d_s, B, -1, 0, d_lw, nullptr, nullptr, 2.0, 1);
+        if (rc) return rc;
+        launch_log_bare(c, d_s, B, d_lw, 1);
+        return SLDQMC_OK;
+    }
+    cudaStream_t tst = t->st;
+    cudaEventRecord(c->ev_fork, c->st);
+    cudaStreamWaitEvent(tst, c->ev_fork, 0);
+    int rc = weight_run(t, d_s, B, -1, 0, t->d_ld_tmp, nullptr, nullptr, 2.0, 0);
     if (rc) return rc;
-    rc = weight_run(c, d_s, B, -1, 0, d_lw, nullptr, nullptr, 2.0, 1);
+    rc = weight_run(c, d_s, B, 1, 0, d_lw, nullptr, nullptr, 2.0, 0);
     if (rc) return rc;
+    cudaEventRecord(c->ev_join, tst);
+    cudaStreamWaitEvent(c->st, c->ev_join, 0);
+    k_add_vec<<<cdiv(B, 128), 128, 0, c->st>>>(d_lw, t->d_ld_tmp, B);
+    c->launches++;
     launch_log_bare(c, d_s, B, d_lw, 1);
     return SLDQMC_OK;
 }
@@ -386,7 +451,10 @@ const char *sldqmc_strerror(int status)
     }
 }
 
-long long sldqmc_kernel_launches(const sldqmc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+long long sldqmc_kernel_launches(const sldqmc_ctx *ctx)
+{
+    return ctx ? ctx->launches + (ctx->twin ? ctx->twin->launches : 0) : 0;
+}
 
 int sldqmc_dims(const sldqmc_ctx *ctx, int *N, int *M)
 {
@@ -406,6 +474,13 @@ void sldqmc_destroy(sldqmc_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->st);
+    if (c->twin) {
+        cudaStream_t tst = c->twin->st;
+        sldqmc_destroy(c->twin);
+        cudaStreamDestroy(tst);
+        cudaEventDestroy(c->ev_fork);
+        cudaEventDestroy(c->ev_join);
+    }
     tc_release(c);
     if (c->prof) {
         for (cudaEvent_t e : c->prof->pool) cudaEventDestroy(e);
@@ -464,7 +539,7 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     int rc = SLDQMC_OK;
     const size_t nn = (size_t)c->nn, cap = (size_t)c->cap;
     if ((rc = dalloc(&c->d_flag, 1))) goto fail;
-    cudaMemset(c->d_flag, 0, sizeof(int));
+    cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st);
     if ((rc = dalloc(&c->d_K, 3 * nn + 4 * (size_t)(p->Lx + p->Ly)))) goto fail;
     c->d_E = c->d_K + nn;
     c->d_Einv = c->d_E + nn;
@@ -800,16 +875,21 @@ int sldqmc_set_effective_model(sldqmc_ctx *c, int n_class, const int *n_off, con
     int rc = dalloc(&c->d_col_start, start.size());
     if (!rc) rc = dalloc(&c->d_col_sites, sites.size());
     if (rc) return rc;
-    if (cudaMemcpy(c->d_col_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c->d_col_sites, sites.data(), sizeof(int) * sites.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    // stream-ordered copies: the context's stream need not synchronise with
+    // the legacy default stream
+    if (cudaMemcpyAsync(c->d_col_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, c->st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->d_col_sites, sites.data(), sizeof(int) * sites.size(), cudaMemcpyHostToDevice, c->st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess) {
+        cudaStreamSynchronize(c->st);
         return SLDQMC_ERR_CUDA;
+    }
     if (!c->d_feat0) {
         rc = dalloc(&c->d_feat0, 2 * 32 * (size_t)c->cap);
         if (rc) return rc;
         c->d_feat1 = c->d_feat0 + 32 * (size_t)c->cap;
     }
-    rc = upload_effective_model(c);
-    if (rc) return rc;
     c->have_model = 1;
     return sync_and_flag(c);
 }
@@ -1062,7 +1142,8 @@ int sldqmc_graph_create(sldqmc_ctx *const *ctxs, int n, int8_t *const *d_s, doub
             rc = dalloc(&c->d_step, 1);
             if (rc) { sldqmc_graph_destroy(g); return rc; }
         }
-        if (cudaMemcpy(c->d_step, &step0, sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (cudaMemcpyAsync(c->d_step, &step0, sizeof(uint32_t), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+            cudaStreamSynchronize(c->st) != cudaSuccess) {
             sldqmc_graph_destroy(g);
             return SLDQMC_ERR_CUDA;
         }
@@ -1075,7 +1156,10 @@ int sldqmc_graph_create(sldqmc_ctx *const *ctxs, int n, int8_t *const *d_s, doub
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { sldqmc_graph_destroy(g); return SLDQMC_ERR_CUDA; }
         g->events.push_back(e);
     }
-    for (int i = 0; i < n; ++i) cudaStreamSynchronize(ctxs[i]->st);
+    for (int i = 0; i < n; ++i) {
+        get_twin(ctxs[i]);  // allocates, so it must exist before the capture starts
+        cudaStreamSynchronize(ctxs[i]->st);
+    }
     if (cudaStreamBeginCapture(g->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         sldqmc_graph_destroy(g);
         return SLDQMC_ERR_CUDA;
