@@ -22,13 +22,13 @@
 // A persistent CTA per SM walks the 128 x 64 output tiles of the batch:
 // warp 0 drives TMA (128-byte swizzled boxes, mbarrier completion) without
 // stopping at tile boundaries, warp 1 issues the MMAs from one thread, and
-// warps 2-5 drain the accumulators with tcgen05.ld and apply the next
-// slice's column scaling (as a float pair, so that the scale constant adds
-// no systematic error) while re-splitting the result into the operand format
-// of the next product (or FP64 for the stabilisation at the end of the
-// block).  Every mbarrier wait is bounded; a wait that runs out
-// raises the context's timeout flag and the CTA frees its tensor memory and
-// exits.
+// eight epilogue warps drain the accumulators with tcgen05.ld, hand tensor
+// memory back, and then apply the next slice's column scaling (as a float
+// pair, so that the scale constant adds no systematic error) while
+// re-splitting the result into the operand format of the next product (or
+// FP64 for the stabilisation at the end of the block).  Every mbarrier wait
+// is bounded; a wait that runs out raises the context's timeout flag and the
+// CTA frees its tensor memory and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -214,13 +214,50 @@ __host__ __device__ constexpr int stage_bytes() { return ModeCfg<MODE>::NPA * TI
 // the whole batch (tile t = blockIdx.x, blockIdx.x + gridDim.x, ...).
 // Warp 0 (one thread) streams TMA stages continuously across tile
 // boundaries; warp 1 (one thread) issues the MMAs of a tile once the
-// epilogue has handed tensor memory back; warps 2-5 drain the accumulators
-// (TMEM lane quarter = warp % 4), scale, re-split and store with vector
-// stores while the next tile's operands are already loading.
-constexpr int NTHREADS = 192;
-constexpr int STG_FLOATS = 32 * 9 * 2;  // per-warp staging block: 32 rows x 17 floats, or 32 x 9 doubles
+// epilogue has handed tensor memory back; the epilogue warps (two per TMEM
+// lane quarter, each owning half of the tile's columns) drain the
+// accumulators into registers, hand tensor memory back at once, and then
+// scale, re-split and store while the MMAs of the next tile run.
+constexpr int EPI_WARPS = 8;                     // epilogue warps: EPI_WARPS / 4 per TMEM lane quarter
+constexpr int EPI_COLS = BN * 4 / EPI_WARPS;      // accumulator columns drained by one epilogue warp
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
+static_assert(EPI_COLS % 16 == 0, "epilogue warps drain 16-column chunks");
 
 __device__ __forceinline__ __nv_bfloat16 bf16_rn(float x) { return __float2bfloat16_rn(x); }
+
+// Stores one 16-column row segment of an operand part: FP32 (split TF32) or
+// BF16 (rounded here; the leading parts are BF16 values already).  `full`
+// segments are 16-element aligned; a ragged one writes its first `rem`.
+template <int MODE>
+__device__ __forceinline__ void store_part(void *base, long long o, const float (&pp)[16], bool full, int rem)
+{
+    if (MODE == 0) {
+        float *dst = static_cast<float *>(base) + o;
+        if (full) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                reinterpret_cast<float4 *>(dst)[k] = make_float4(pp[4 * k], pp[4 * k + 1], pp[4 * k + 2], pp[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < rem) dst[j] = pp[j];
+        }
+    } else {
+        __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(base) + o;
+        if (full) {
+            uint4 w[2];
+            __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(w);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) h2[k] = __floats2bfloat162_rn(pp[2 * k], pp[2 * k + 1]);
+            reinterpret_cast<uint4 *>(dst)[0] = w[0];
+            reinterpret_cast<uint4 *>(dst)[1] = w[1];
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < rem) dst[j] = bf16_rn(pp[j]);
+        }
+    }
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -253,7 +290,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(tmem_full, 1);
-        mbar_init(tmem_free, 128);
+        mbar_init(tmem_free, 32 * EPI_WARPS);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -266,7 +303,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int ksteps = a.nk * KSTEPS;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -338,66 +374,66 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         }
     } else {
-        // epilogue warps 2..5
+        // epilogue warps: warp w drains TMEM lane quarter w % 4 (rows), columns
+        // [cb, cb + EPI_COLS) of the tile; each thread owns one row.
         const int q4 = warp & 3;
-        float *stg = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(tmem_slot) + 16) + (warp - 2) * STG_FLOATS;
-        const uint32_t used_mask = SPLIT
-                                       ? (((1u << (ksteps < NACC - 1 ? ksteps : NACC - 1)) - 1u) | (1u << (NACC - 1)))
-                                       : ((1u << (ksteps < NACC ? ksteps : NACC)) - 1u);
+        const int cb = ((warp - 2) >> 2) * EPI_COLS;
         int ti = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
             const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
             const int n0 = tn * BN, m0 = tm * BM;
+            // Column scale signs of this tile as a 64-bit mask, fetched before
+            // the accumulators are ready.
+            uint64_t up_mask = 0;
+            const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
+            if (sn) {
+                const bool u0 = n0 + lane < a.N && sn[n0 + lane] > 0;
+                const bool u1 = n0 + 32 + lane < a.N && sn[n0 + 32 + lane] > 0;
+                up_mask = (uint64_t)__ballot_sync(0xffffffffu, u0) | ((uint64_t)__ballot_sync(0xffffffffu, u1) << 32);
+            }
             const bool ok = mbar_wait(tmem_full, ti & 1, a.flag);
             fence_after();
-            const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float v[16];
-                const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c0;
-                {
-                    // accumulators loaded in pairs, one wait per pair (every
-                    // accumulator received MMAs: K >= 128)
+            // Drain this warp's accumulator columns into registers (summed over
+            // the accumulators; every accumulator received MMAs since K >= 128),
+            // then hand tensor memory back so that the next tile's MMAs run
+            // while this tile is scaled, split and stored.
+            float v[EPI_COLS / 16][16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+            for (int c = 0; c < EPI_COLS / 16; ++c) {
+                const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cb + c * 16);
 #pragma unroll
-                    for (int q = 0; q < NACC; q += 2) {
-                        uint32_t r0[16], r1[16];
-                        tmem_ld16_nowait(lane_base + (uint32_t)(q * BN), r0);
-                        tmem_ld16_nowait(lane_base + (uint32_t)((q + 1) * BN), r1);
-                        tmem_wait_ld32(r0, r1);
+                for (int j = 0; j < 16; ++j) v[c][j] = 0.0f;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
-                    }
+                for (int q = 0; q < NACC; q += 2) {
+                    uint32_t r0[16], r1[16];
+                    tmem_ld16_nowait(lane_base + (uint32_t)(q * BN), r0);
+                    tmem_ld16_nowait(lane_base + (uint32_t)((q + 1) * BN), r1);
+                    tmem_wait_ld32(r0, r1);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[c][j] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
                 }
-                (void)used_mask;
+            }
+            fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_free)) : "memory");
+            if (!ok) break;  // a wait ran out: the flag is raised, stop instead of waiting per tile
+            const int mm = m0 + q4 * 32 + lane;
+#pragma unroll
+            for (int c = 0; c < EPI_COLS / 16; ++c) {
+                const int c0 = cb + c * 16;
                 const int nb = n0 + c0;
-                if (!ok || nb >= a.N) continue;  // uniform over the warp
-                // Stores go through a per-warp 32-row staging block so that each
-                // warp store instruction writes whole 64-byte row segments.
-                const int r0 = m0 + q4 * 32;
+                if (nb >= a.N || mm >= a.N) continue;
+                const bool full = nb + 16 <= a.N;
                 if (a.out_f64) {
-                    double *sd = reinterpret_cast<double *>(stg);
+                    const long long off = (long long)b * a.s_f64 + (long long)mm * a.N + nb;
+                    double *o = a.out_f64 + off;
+                    if (full && (off & 1) == 0) {  // 16-byte aligned (the buffer itself is)
 #pragma unroll
-                    for (int half = 0; half < 2; ++half) {
+                        for (int k = 0; k < 8; ++k)
+                            reinterpret_cast<double2 *>(o)[k] = make_double2((double)v[c][2 * k], (double)v[c][2 * k + 1]);
+                    } else {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) sd[lane * 9 + j] = (double)v[half * 8 + j];
-                        __syncwarp();
-#pragma unroll
-                        for (int it = 0; it < 2; ++it) {
-                            const int rr = it * 16 + (lane >> 1), cc = (lane & 1) * 4;
-                            const int mm = r0 + rr, n = nb + half * 8 + cc;
-                            if (mm < a.N && n < a.N) {
-                                double *o = a.out_f64 + (long long)b * a.s_f64 + (long long)mm * a.N + n;
-                                const double *src = sd + rr * 9 + cc;
-                                if (n + 4 <= a.N && (((long long)mm * a.N + n) & 1) == 0) {
-                                    *reinterpret_cast<double2 *>(o) = make_double2(src[0], src[1]);
-                                    *reinterpret_cast<double2 *>(o + 2) = make_double2(src[2], src[3]);
-                                } else {
-                                    for (int k = 0; k < 4 && n + k < a.N; ++k) o[k] = src[k];
-                                }
-                            }
-                        }
-                        __syncwarp();
+                        for (int j = 0; j < 16; ++j)
+                            if (nb + j < a.N) o[j] = (double)v[c][j];
                     }
                     continue;
                 }
@@ -406,61 +442,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int j = 0; j < 16; ++j) {
                     // y = v * d with d = dh + dl: yh = fl(v dh), ye = the rounding error of
                     // that product (exact by FMA) plus v dl.
-                    float yh = v[j], ye = 0.0f;
-                    if (sn && nb + j < a.N) {
-                        const bool up = sn[nb + j] > 0;
+                    const float x = v[c][j];
+                    float yh = x, ye = 0.0f;
+                    if (sn) {
+                        const bool up = (up_mask >> (c0 + j)) & 1u;
                         const float dh = up ? a.cu_h : a.cd_h, dl = up ? a.cu_l : a.cd_l;
-                        yh = v[j] * dh;
-                        ye = fmaf(v[j], dh, -yh) + v[j] * dl;
+                        yh = x * dh;
+                        ye = fmaf(x, dh, -yh) + x * dl;
                     }
                     if (MODE == 0) {
                         p0[j] = to_tf32(yh);
                         p1[j] = to_tf32((yh - p0[j]) + ye);
                     } else if (MODE == 1) {
-                        p0[j] = __bfloat162float(bf16_rn(yh + ye));
+                        p0[j] = yh + ye;
                     } else {
                         p0[j] = __bfloat162float(bf16_rn(yh));
                         const float r1 = (yh - p0[j]) + ye;
                         p1[j] = __bfloat162float(bf16_rn(r1));
-                        p2[j] = __bfloat162float(bf16_rn(r1 - p1[j]));
+                        p2[j] = r1 - p1[j];
                     }
                 }
-                constexpr int NPARTS = MODE == 0 ? 2 : (MODE == 1 ? 1 : 3);
-#pragma unroll
-                for (int part = 0; part < NPARTS; ++part) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = part == 0 ? p0[j] : (part == 1 ? p1[j] : p2[j]);
-                    __syncwarp();
-#pragma unroll
-                    for (int it = 0; it < 4; ++it) {
-                        const int rr = it * 8 + (lane >> 2), cc = (lane & 3) * 4;
-                        const int mm = r0 + rr, n = nb + cc;
-                        if (mm < a.N && n < a.N) {
-                            const float *src = stg + rr * 17 + cc;
-                            const long long o = (long long)b * a.s_out + (long long)mm * a.ldp + n;
-                            if (MODE == 0) {
-                                float *dst = static_cast<float *>(a.out[part]) + o;
-                                if (n + 4 <= a.N) *reinterpret_cast<float4 *>(dst) = make_float4(src[0], src[1], src[2], src[3]);
-                                else for (int k = 0; k < 4 && n + k < a.N; ++k) dst[k] = src[k];
-                            } else {
-                                __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(a.out[part]) + o;
-                                if (n + 4 <= a.N) {
-                                    __nv_bfloat162 h2[2] = {__floats2bfloat162_rn(src[0], src[1]),
-                                                            __floats2bfloat162_rn(src[2], src[3])};
-                                    *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(&h2[0]);
-                                } else {
-                                    for (int k = 0; k < 4 && n + k < a.N; ++k) dst[k] = bf16_rn(src[k]);
-                                }
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
+                const long long o = (long long)b * a.s_out + (long long)mm * a.ldp + nb;
+                store_part<MODE>(a.out[0], o, p0, full, a.N - nb);
+                if (MODE != 1) store_part<MODE>(a.out[1], o, p1, full, a.N - nb);
+                if (MODE == 2) store_part<MODE>(a.out[2], o, p2, full, a.N - nb);
             }
-            // hand the accumulators back to the MMA thread
-            fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_free)) : "memory");
-            if (!ok) break;  // a wait ran out: the flag is raised, stop instead of waiting per tile
         }
     }
     __syncwarp();
@@ -547,8 +553,8 @@ bool encode(CUtensorMap *map, void *ptr, bool bf16, int rank, int ldp, int rows,
 template <int MODE>
 constexpr size_t smem_bytes()
 {
-    // stages, alignment, barriers, four per-warp staging blocks
-    return (size_t)stages<MODE>() * stage_bytes<MODE>() + 1024 + 256 + 4 * STG_FLOATS * sizeof(float);
+    // stages, alignment, barriers
+    return (size_t)stages<MODE>() * stage_bytes<MODE>() + 1024 + 256;
 }
 
 int mode_of(const sldqmc_ctx *c) { return c->p.prec == SLDQMC_3XTF32 ? 0 : (c->p.prec == SLDQMC_BF16 ? 1 : 2); }
@@ -604,7 +610,9 @@ int tc_prepare(sldqmc_ctx *c)
         w->mem = nullptr;
         return SLDQMC_ERR_OOM;
     }
-    cudaMemset(w->mem, 0, bytes);  // zero pads: columns N..ldp-1 are never written
+    // zero pads (columns N..ldp-1 are never written), ordered before the
+    // context's first kernels on its own stream
+    cudaMemsetAsync(w->mem, 0, bytes, c->st);
     uint8_t *q = (uint8_t *)w->mem;
     for (int i = 0; i < 2; ++i)
         for (int p = 0; p < 3; ++p) {
