@@ -140,7 +140,8 @@ class ClockSampler:
 
 def traffic_record(kernel_class):
     """Per-launch DRAM traffic of a kernel class from a committed ncu summary,
-    valid only while the kernel's source is unchanged."""
+    valid only while the sources it depends on (the kernel, and the code that
+    decides which launches it gets) are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -148,8 +149,10 @@ def traffic_record(kernel_class):
         d = json.load(open(path)).get(kernel_class)
         if not d:
             return None
-        src = open(os.path.join(ROOT, "paper_1612_03804_gb300", "csrc", d["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != d["sha"]:
+        h = hashlib.sha256()
+        for f in d["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_1612_03804_gb300", "csrc", f), "rb").read())
+        if h.hexdigest()[:16] != d["sha"]:
             return None
         return d
     except Exception:

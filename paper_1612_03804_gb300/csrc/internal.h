@@ -59,9 +59,10 @@ GemmF64 gemm_desc(int M, int N, int K, const double *A, long long lda, long long
                   const double *B, long long ldb, long long sB, double *C, long long ldc,
                   long long sC, int batch);
 
-// Mixed-precision slice GEMM (tensor cores, tcgen05): C = A * E with the
-// same scale options as the FP64 GEMM's chain use.  Defined in tc_gemm.cu.
-struct ChainTC;
+// Mixed-precision modes: V <- D^{-1} R D_p P^T V on the tensor cores (R upper
+// triangular, D = c->d_D, D_p = c->d_Dp, P = c->d_perm; row stride N, batch
+// stride nn; result in FP64).  Defined in tc_gemm.cu.
+void tc_update_V(sldqmc_ctx *c, const double *R, double *V, int B);
 
 // Event-bracketed timing of launches (sldqmc_profile_*).
 struct ProfRec {

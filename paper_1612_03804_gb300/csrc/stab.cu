@@ -501,13 +501,19 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B, int pass
     }
     dim3 gd(cdiv(N, 256), B);
     k_new_D<<<gd, 256, 0, c->st>>>(R, nn, N, c->d_Dp, c->d_D, c->d_flag);
+    c->launches++;
+    if (c->tc_ws) {
+        // mixed-precision modes: V = (D^{-1} R D_p) P^T V on the tensor cores
+        tc_update_V(c, R, V, B);
+        return;
+    }
     k_gather_V<<<gg, 256, 0, c->st>>>(V, Vg, nn, N, c->d_perm, c->d_Dp);
     // V = D^{-1} R Vg
     GemmF64 g4 = gemm_desc(N, N, N, R, N, nn, Vg, N, nn, V, N, nn, B);
     g4.a_upper = 1;
     g4.ms = c->d_D; g4.sMs = N; g4.ms_recip = 1;
     gemm_ctx(c, g4, false, false);
-    c->launches += 2;
+    c->launches++;
 }
 
 // Final determinant (and optionally G) from the running U^T, D, V.
