@@ -257,6 +257,18 @@ long long sldqmc_kernel_launches(const sldqmc_ctx *ctx);
 int sldqmc_weight_noalloc(const sldqmc_params *p, void *stream, const int8_t *d_s, int B, int eta,
                           double *d_logabsdet, int *d_sign);
 
+/* Gram matrices W_b = X_b X_b^T of the Cholesky-QR stabilisation (the first
+ * step of each re-orthogonalisation, whose accuracy bounds the condition
+ * number Cholesky-QR can take: kappa(X)^2 eps_W < 1).  d_X holds B row-major
+ * N x N FP64 matrices (item stride N*N), d_W receives B row-major N x N FP64
+ * matrices of which every element on or above the diagonal is written (the
+ * rest is unspecified).  Computed exactly as the context's stabilisation does:
+ * in the mixed-precision modes with 128 <= N <= 384 on the BF16 tensor cores
+ * by error-free digit splitting (FP64 accuracy: error below ~2^-52 of
+ * sqrt(W_ii W_jj)), otherwise by the FP64 GEMM.  1 <= B <= max_batch.
+ * Stream-ordered on the context's stream; caller-owned device buffers. */
+int sldqmc_gram_batch_dev(sldqmc_ctx *ctx, const double *d_X, int B, double *d_W);
+
 /* Failure-path self-test of the bounded device waits used by the
  * tensor-core kernels: launches a kernel that waits on an mbarrier nothing
  * arrives at, for at most max_polls polls (1 .. 2^24), so the wait runs out
@@ -271,7 +283,8 @@ int sldqmc_wait_selftest(sldqmc_ctx *ctx, int max_polls);
 #define SLDQMC_KC_EFF 3        /* effective-model sweeps */
 #define SLDQMC_KC_LOCAL 4      /* local-update flips */
 #define SLDQMC_KC_OTHER 5      /* everything else */
-#define SLDQMC_KC_COUNT 6
+#define SLDQMC_KC_GEMM_OZ 6    /* FP64-accurate Gram matrices on the BF16 tensor cores (mixed modes) */
+#define SLDQMC_KC_COUNT 7
 
 /* Timing hooks (off by default): when on, every launch on the context's
  * stream is bracketed by CUDA events and tagged with its class and its

@@ -1,0 +1,419 @@
+// oz_gram.cu -- FP64-accurate Gram matrices on the BF16 tensor cores
+// (Ozaki's error-free splitting), for the Cholesky-QR of the mixed-precision
+// modes.
+//
+// W = X X^T for the rows x_i of X (N x N per batch item).  Each row is
+// scaled by a power of two, 2^-E_i with |x_ik| < 2^E_i, and written as eight
+// balanced base-2^7 digits,
+//   x_ik 2^-E_i = sum_{p=1..8} a_p,ik 2^-7p   (|a_1| <= 128, |a_p| <= 64, p > 1),
+// exact up to the rounding of x_ik 2^-E_i to a multiple of 2^-56.  Then
+//   W_ij 2^-(E_i+E_j) = sum_{p,q} 2^-7(p+q) sum_k a_p,ik a_q,jk,
+// of which the 36 products with p + q <= 9 are kept: each dropped term is
+// below 2^-56 of the row maxima, the same order as FP64's own rounding of the
+// sum.  The digit planes are BF16 integers; the products of one group
+// g = p + q share one FP32 tensor-memory accumulator, and every partial sum
+// of a group is an integer of magnitude < K (2 * 8192 + 6 * 4096) < 2^24 for
+// K <= 384, so the tensor-core accumulation is exact.  The epilogue converts
+// the eight group sums to integers, combines them in two 64-bit integers and
+// forms the FP64 result with one rounding.
+//
+// One persistent CTA per SM walks the 128 x 32 tiles on or above the
+// diagonal of every item: warp 0 streams the 8 + 8 digit-plane tiles of a
+// 32-wide K-block by TMA (64-byte swizzle), warp 1 issues the 36 MMAs per
+// 16-wide K-step, and eight epilogue warps drain one of two tensor-memory
+// buffers (8 groups x 32 columns each) while the next tile accumulates into
+// the other.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace sldqmc {
+
+namespace {
+
+using namespace tcx;
+
+constexpr int OZ_S = 8;           // digit planes
+constexpr int OZ_BETA = 7;        // bits per digit
+constexpr int OZ_G = 8;           // groups p + q = 2..9
+constexpr int OZ_KMAX = 384;      // largest K with exact group sums
+constexpr int OBM = 128, OBN = 32;
+constexpr int OKE = 32;           // BF16 elements per K-block (64-byte rows)
+constexpr int OSTAGES = 2;
+constexpr int OTILE_A = OBM * 64;  // one digit plane of A per stage
+constexpr int OTILE_B = OBN * 64;
+constexpr int OSTAGE = OZ_S * (OTILE_A + OTILE_B);
+constexpr int OEPI = 8;            // epilogue warps, two per TMEM lane quarter
+constexpr int OTHREADS = 64 + 32 * OEPI;
+constexpr int OTMEM = 2 * OZ_G * OBN;  // two buffers of eight 32-column accumulators
+
+constexpr size_t oz_smem_bytes() { return (size_t)OSTAGES * OSTAGE + 1024 + 256; }
+
+// Shared-memory descriptor of a K-major BF16 operand with 64-byte rows and the
+// 64-byte swizzle (8-row atoms of 512 bytes).
+__device__ __forceinline__ uint64_t smem_desc64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)4u << 61;
+    return d;
+}
+
+// kind::f16 with BF16 operands, FP32 accumulator, K-major A and B, M = 128, N = 32.
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OBN >> 3) << 17) |
+                              ((uint32_t)(OBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc));
+}
+
+// Digits of every row: E[b][i] and the planes (plane p at p * plane_stride,
+// row-major with leading dimension ldp; columns N..ldp-1 stay zero).
+__global__ void __launch_bounds__(128) k_oz_slice(const double *X, long long sX, int N, int ldp,
+                                                  long long plane_stride, __nv_bfloat16 *planes, int *E)
+{
+    const int b = blockIdx.y, i = blockIdx.x;
+    const double *x = X + (long long)b * sX + (long long)i * N;
+    // the largest |x_ik| (non-negative doubles order like their bit patterns)
+    unsigned long long mx = 0;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(x[k]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = u > mx ? u : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+    }
+    __shared__ unsigned long long red[4];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = red[w] > mx ? red[w] : mx;
+    // |x| < 2^Ei for every element of the row (Ei = frexp exponent of the max);
+    // a row of zeros or subnormals gets digits 0
+    const int ef_max = (int)(mx >> 52);
+    const int Ei = ef_max > 0 ? ef_max - 1022 : 0;
+    if (threadIdx.x == 0) E[(long long)b * N + i] = Ei;
+    const long long row = (long long)b * N * ldp + (long long)i * ldp;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(x[k]);
+        const int ef = (int)((u >> 52) & 0x7FF);
+        long long v = 0;
+        if (ef > 0 && ef_max > 0) {
+            // x = m 2^(ef - 1075); v = round(|x| 2^(56 - Ei)) < 2^56
+            const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+            const int sh = ef - 1075 + 56 - Ei;
+            if (sh >= 0) v = (long long)(m << sh);  // sh <= 3 since |x| < 2^Ei
+            else if (sh > -60) v = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+        }
+        int dg[OZ_S];
+#pragma unroll
+        for (int p = OZ_S - 1; p >= 1; --p) {
+            int d = (int)(v & ((1 << OZ_BETA) - 1));
+            v >>= OZ_BETA;
+            if (d >= (1 << (OZ_BETA - 1))) {
+                d -= 1 << OZ_BETA;
+                v += 1;
+            }
+            dg[p] = d;
+        }
+        dg[0] = (int)v;  // 0..128
+        const bool neg = (u >> 63) != 0;
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p)
+            planes[(long long)p * plane_stride + row + k] = __float2bfloat16_rn((float)(neg ? -dg[p] : dg[p]));
+    }
+}
+
+struct OzArgs {
+    int N, batch, nk;
+    const int *E;
+    double *W;
+    long long sW;
+    int ldw;
+    int *flag;
+};
+
+// tile t of the persistent walk -> (item, first row, first column)
+__device__ __forceinline__ void oz_tile(int t, int tiles_m, int tiles_n, int per_item, int &b, int &m0, int &n0)
+{
+    b = t / per_item;
+    int r = t - b * per_item;
+    int tm = 0;
+    for (; tm < tiles_m; ++tm) {
+        const int cnt = tiles_n - 4 * tm;
+        if (r < cnt) break;
+        r -= cnt;
+    }
+    m0 = tm * OBM;
+    n0 = (4 * tm + r) * OBN;
+}
+
+__global__ void __launch_bounds__(OTHREADS, 1)
+    k_oz_gram(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(base + OSTAGES * OSTAGE);
+    uint64_t *empty = full + OSTAGES;
+    uint64_t *tmem_full = empty + OSTAGES;  // [2]
+    uint64_t *tmem_free = tmem_full + 2;    // [2]
+    uint32_t *tmem_slot = (uint32_t *)(tmem_free + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_m = (a.N + OBM - 1) / OBM, tiles_n = (a.N + OBN - 1) / OBN;
+    int per_item = 0;
+    for (int tm = 0; tm < tiles_m; ++tm) per_item += tiles_n - 4 * tm;
+    const int tiles = per_item * a.batch;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OSTAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int u = 0; u < 2; ++u) {
+            mbar_init(&tmem_full[u], 1);
+            mbar_init(&tmem_free[u], 32 * OEPI);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(OTMEM)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                int b, m0, n0;
+                oz_tile(t, tiles_m, tiles_n, per_item, b, m0, n0);
+                for (int kb = 0; kb < a.nk; ++kb, ++it) {
+                    const int s = it % OSTAGES;
+                    if (it >= OSTAGES && !mbar_wait(&empty[s], ((it / OSTAGES) - 1) & 1, a.flag)) { ok = false; break; }
+                    mbar_expect_tx(&full[s], OSTAGE);
+                    uint8_t *st = base + s * OSTAGE;
+                    const int k0 = kb * OKE;
+#pragma unroll
+                    for (int p = 0; p < OZ_S; ++p) {
+                        tma_load_4d(st + p * OTILE_A, &tA, k0, m0, b, p, &full[s]);
+                        tma_load_4d(st + OZ_S * OTILE_A + p * OTILE_B, &tB, k0, n0, b, p, &full[s]);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, ti = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++ti) {
+                const int u = ti & 1;
+                // the epilogue must have drained this buffer (used two tiles ago)
+                if (ti >= 2 && !mbar_wait(&tmem_free[u], ((ti >> 1) - 1) & 1, a.flag)) { ok = false; break; }
+                fence_after();
+                const uint32_t acc0 = tmem + (uint32_t)(u * OZ_G * OBN);
+                uint32_t started = 0;
+                for (int kb = 0; kb < a.nk; ++kb, ++it) {
+                    const int s = it % OSTAGES;
+                    if (!mbar_wait(&full[s], (it / OSTAGES) & 1, a.flag)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t sa = smem_u32(base + s * OSTAGE);
+                    const uint32_t sb = sa + OZ_S * OTILE_A;
+#pragma unroll
+                    for (int k = 0; k < OKE / 16; ++k) {
+#pragma unroll
+                        for (int p = 0; p < OZ_S; ++p) {
+                            const uint64_t da = smem_desc64(sa + p * OTILE_A + k * 32);
+#pragma unroll
+                            for (int q = 0; q < OZ_S - p; ++q) {
+                                const int g = p + q;
+                                mma_bf16(acc0 + (uint32_t)(g * OBN), da, smem_desc64(sb + q * OTILE_B + k * 32),
+                                         (started >> g) & 1u);
+                                started |= 1u << g;
+                            }
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&tmem_full[u]);
+            }
+        }
+    } else {
+        // epilogue: warp w drains lane quarter w % 4, columns [hc, hc + 16)
+        const int q4 = warp & 3;
+        const int hc = ((warp - 2) >> 2) * 16;
+        int ti = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
+            int b, m0, n0;
+            oz_tile(t, tiles_m, tiles_n, per_item, b, m0, n0);
+            const int u = ti & 1;
+            const int mm = m0 + q4 * 32 + lane;
+            const int Ei = mm < a.N ? a.E[(long long)b * a.N + mm] : 0;
+            const bool ok = mbar_wait(&tmem_full[u], (ti >> 1) & 1, a.flag);
+            fence_after();
+            float g[OZ_G][16];
+            const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(u * OZ_G * OBN + hc);
+#pragma unroll
+            for (int gg = 0; gg < OZ_G; gg += 2) {
+                uint32_t r0[16], r1[16];
+                tmem_ld16_nowait(lane_base + (uint32_t)(gg * OBN), r0);
+                tmem_ld16_nowait(lane_base + (uint32_t)((gg + 1) * OBN), r1);
+                tmem_wait_ld32(r0, r1);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    g[gg][j] = __uint_as_float(r0[j]);
+                    g[gg + 1][j] = __uint_as_float(r1[j]);
+                }
+            }
+            fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tmem_free[u])) : "memory");
+            if (!ok) break;
+            if (mm >= a.N) continue;
+            double w[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                // groups 0..3 (p + q = 2..5) and 4..7 (6..9) as integers:
+                // sum_g acc_g 2^-7(g+2) = h 2^-35 + l 2^-63
+                long long h = 0, l = 0;
+#pragma unroll
+                for (int gg = 0; gg < 4; ++gg) h += (long long)__float2int_rn(g[gg][j]) << (OZ_BETA * (3 - gg));
+#pragma unroll
+                for (int gg = 4; gg < 8; ++gg) l += (long long)__float2int_rn(g[gg][j]) << (OZ_BETA * (7 - gg));
+                w[j] = fma((double)l, 0x1p-28, (double)h);
+            }
+            double *o = a.W + (long long)b * a.sW + (long long)mm * a.ldw;
+            const int nb = n0 + hc;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = nb + j;
+                if (n < a.N) {
+                    const int e = Ei + a.E[(long long)b * a.N + n] - 35;
+                    o[n] = (e > -1000 && e < 1000) ? w[j] * __longlong_as_double((long long)(e + 1023) << 52)
+                                                   : scalbn(w[j], e);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OTMEM) : "memory");
+}
+
+struct OzWs {
+    int ldp;
+    long long plane_stride;
+    __nv_bfloat16 *planes;
+    int *E;
+    CUtensorMap mapA, mapB;
+    int num_sms;
+};
+
+bool encode4(CUtensorMap *map, void *ptr, int ldp, int rows, int batch, int box_rows)
+{
+    auto fn = get_encode();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)ldp, (cuuint64_t)rows, (cuuint64_t)batch, (cuuint64_t)OZ_S};
+    cuuint64_t strides[3] = {(cuuint64_t)ldp * 2, (cuuint64_t)ldp * rows * 2, (cuuint64_t)ldp * rows * batch * 2};
+    cuuint32_t box[4] = {(cuuint32_t)OKE, (cuuint32_t)box_rows, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int oz_prepare(sldqmc_ctx *c)
+{
+    c->oz_ws = nullptr;
+    if (c->N < OBM || c->N > OZ_KMAX) return SLDQMC_OK;  // FP64 Gram outside the exact range
+    OzWs *w = new OzWs();
+    const int N = c->N;
+    w->ldp = (N + 63) / 64 * 64;
+    w->plane_stride = (long long)c->cap * N * w->ldp;
+    const size_t pbytes = (size_t)OZ_S * w->plane_stride * sizeof(__nv_bfloat16);
+    if (cudaMalloc(&w->planes, pbytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete w;
+        return SLDQMC_ERR_OOM;
+    }
+    if (cudaMalloc(&w->E, sizeof(int) * (size_t)c->cap * N) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(w->planes);
+        delete w;
+        return SLDQMC_ERR_OOM;
+    }
+    cudaMemsetAsync(w->planes, 0, pbytes, c->st);  // zero pads: columns N..ldp-1 are never written
+    if (!encode4(&w->mapA, w->planes, w->ldp, N, c->cap, OBM) || !encode4(&w->mapB, w->planes, w->ldp, N, c->cap, OBN)) {
+        cudaFree(w->planes);
+        cudaFree(w->E);
+        delete w;
+        return SLDQMC_ERR_CUDA;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || w->num_sms < 1)
+        w->num_sms = 148;
+    cudaFuncSetAttribute(k_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    c->oz_ws = w;
+    return SLDQMC_OK;
+}
+
+void oz_release(sldqmc_ctx *c)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    if (!w) return;
+    cudaFree(w->planes);
+    cudaFree(w->E);
+    delete w;
+    c->oz_ws = nullptr;
+}
+
+// W = X X^T (rows of X: row stride N, batch stride sX); W row stride ldw,
+// batch stride sW.  Tiles on or above the diagonal are written in full.
+void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long sW, int ldw, int B)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    const int N = c->N;
+    k_oz_slice<<<dim3(N, B), 128, 0, c->st>>>(X, sX, N, w->ldp, w->plane_stride, w->planes, w->E);
+    OzArgs a{};
+    a.N = N;
+    a.batch = B;
+    a.nk = w->ldp / OKE;
+    a.E = w->E;
+    a.W = W;
+    a.sW = sW;
+    a.ldw = ldw;
+    a.flag = c->d_flag;
+    const int tiles_m = (N + OBM - 1) / OBM, tiles_n = (N + OBN - 1) / OBN;
+    int per_item = 0;
+    for (int tm = 0; tm < tiles_m; ++tm) per_item += tiles_n - 4 * tm;
+    const int tiles = per_item * B;
+    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B);
+    k_oz_gram<<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapB, a);
+    prof_end(c);
+    c->launches += 2;
+}
+
+}  // namespace sldqmc

@@ -482,6 +482,7 @@ void sldqmc_destroy(sldqmc_ctx *c)
         cudaEventDestroy(c->ev_join);
     }
     tc_release(c);
+    oz_release(c);
     if (c->prof) {
         for (cudaEvent_t e : c->prof->pool) cudaEventDestroy(e);
         delete c->prof;
@@ -567,6 +568,7 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     c->d_ld_tmp2 = c->d_ld_tmp + cap;
     if ((rc = dalloc(&c->d_stats, 4 * cap + 8 * cap))) goto fail;
     if (p->prec != SLDQMC_FP64 && (rc = tc_prepare(c))) goto fail;
+    if (p->prec != SLDQMC_FP64 && (rc = oz_prepare(c))) goto fail;
     {
         // build K, E, E^{-1}
         double *ex_p = c->d_Einv + nn, *ey_p = ex_p + p->Lx, *ex_m = ey_p + p->Ly, *ey_m = ex_m + p->Lx;
@@ -1217,6 +1219,20 @@ int sldqmc_graph_sync(sldqmc_graph *g)
         if (r && !rc) rc = r;
     }
     return rc;
+}
+
+int sldqmc_gram_batch_dev(sldqmc_ctx *c, const double *d_X, int B, double *d_W)
+{
+    if (!c || !d_X || !d_W || B < 1 || B > c->cap) return SLDQMC_ERR_ARG;
+    const int N = c->N;
+    if (c->oz_ws) {
+        oz_gram(c, d_X, c->nn, d_W, c->nn, N, B);
+    } else {
+        GemmF64 g = gemm_desc(N, N, N, d_X, N, c->nn, d_X, N, c->nn, d_W, N, c->nn, B);
+        g.c_upper = 1;
+        gemm_ctx(c, g, false, true);
+    }
+    return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
 }
 
 int sldqmc_wait_selftest(sldqmc_ctx *c, int max_polls)

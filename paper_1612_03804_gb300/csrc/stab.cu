@@ -472,10 +472,14 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B, int pass
     const long long nn = c->nn;
     double *W = c->buf[4];
     double *R1 = c->buf[6], *R2 = c->buf[7], *Vg = c->buf[8], *V = c->buf[1];
-    // W = Xt Xt^T (upper triangle)
-    GemmF64 g = gemm_desc(N, N, N, Xt, N, nn, Xt, N, nn, W, N, 2 * nn, B);
-    g.c_upper = 1;
-    gemm_ctx(c, g, false, true);
+    // W = Xt Xt^T (upper triangle): FP64, or FP64-accurate on the tensor cores
+    if (c->oz_ws) {
+        oz_gram(c, Xt, nn, W, 2 * nn, N, B);
+    } else {
+        GemmF64 g = gemm_desc(N, N, N, Xt, N, nn, Xt, N, nn, W, N, 2 * nn, B);
+        g.c_upper = 1;
+        gemm_ctx(c, g, false, true);
+    }
     int Npad = 1;
     while (Npad < N) Npad <<= 1;
     size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
@@ -489,9 +493,13 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B, int pass
     const double *R = R1;
     if (passes == 2) {
         // second pass: W = Q1^T Q1 (as Y Y^T), upper triangle; Q = Q1 R2^{-1}, R = R2 R1
-        GemmF64 g2 = gemm_desc(N, N, N, Y, N, nn, Y, N, nn, W, N, 2 * nn, B);
-        g2.c_upper = 1;
-        gemm_ctx(c, g2, false, true);
+        if (c->oz_ws) {
+            oz_gram(c, Y, nn, W, 2 * nn, N, B);
+        } else {
+            GemmF64 g2 = gemm_desc(N, N, N, Y, N, nn, Y, N, nn, W, N, 2 * nn, B);
+            g2.c_upper = 1;
+            gemm_ctx(c, g2, false, true);
+        }
         chol_pass(c, W, 2 * nn, Y, R2, B);
         GemmF64 g3 = gemm_desc(N, N, N, R2, N, nn, R1, N, nn, Xt, N, nn, B);
         g3.a_upper = 1;

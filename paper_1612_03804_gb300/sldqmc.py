@@ -94,6 +94,7 @@ def load(path=None):
         "sldqmc_graph_sync": ([vp], i),
         "sldqmc_graph_destroy": ([vp], None),
         "sldqmc_wait_selftest": ([vp, i], i),
+        "sldqmc_gram_batch_dev": ([vp, vp, i, vp], i),
         "sldqmc_profile_read": ([vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
@@ -290,7 +291,7 @@ class Context:
                                             ctypes.c_uint64(seed), ctypes.c_uint32(step0), int(n_steps),
                                             _p(accepts)), "cumulative_batch")
 
-    KERNEL_CLASSES = ("gemm_f64", "gemm_tc", "panel_f64", "eff_sweep", "local_flips", "other")
+    KERNEL_CLASSES = ("gemm_f64", "gemm_tc", "panel_f64", "eff_sweep", "local_flips", "other", "gemm_oz")
 
     def profile(self, on):
         _chk(load().sldqmc_profile_enable(self.h, int(bool(on))), "profile_enable")
@@ -303,6 +304,10 @@ class Context:
         _chk(load().sldqmc_profile_read(self.h, _p(la), _p(ms), _p(fl)), "profile_read")
         return {k: dict(launches=int(la[i]), ms=float(ms[i]), flops=float(fl[i]))
                 for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def gram_batch_dev(self, d_X, d_W):
+        """W_b = X_b X_b^T (upper triangle) for (B, N, N) float64 device tensors."""
+        _chk(load().sldqmc_gram_batch_dev(self.h, _tp(d_X), int(d_X.shape[0]), _tp(d_W)), "gram_batch_dev")
 
     def wait_selftest(self, max_polls):
         _chk(load().sldqmc_wait_selftest(self.h, int(max_polls)), "wait_selftest")
