@@ -78,8 +78,41 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc));
 }
 
-// Digits of every row: E[b][i] and the planes (plane p at p * plane_stride,
-// row-major with leading dimension ldp; columns N..ldp-1 stay zero).
+// Balanced base-2^7 digits of v = round(|x| 2^(56 - E)) < 2^56 for a double x
+// with |x| < 2^E (E the frexp exponent of its row's maximum, ef_max its
+// biased exponent, 0 for a row of zeros or subnormals): x 2^-E = sum_p
+// dg[p] 2^-7(p+1), p = 0..7.
+__device__ __forceinline__ void oz_digits(double x, int E, int ef_max, int dg[OZ_S])
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((u >> 52) & 0x7FF);
+    long long v = 0;
+    if (ef > 0 && ef_max > 0) {
+        // x = m 2^(ef - 1075)
+        const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = ef - 1075 + 56 - E;
+        if (sh >= 0) v = (long long)(m << sh);  // sh <= 3 since |x| < 2^E
+        else if (sh > -60) v = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+    }
+#pragma unroll
+    for (int p = OZ_S - 1; p >= 1; --p) {
+        int d = (int)(v & ((1 << OZ_BETA) - 1));
+        v >>= OZ_BETA;
+        if (d >= (1 << (OZ_BETA - 1))) {
+            d -= 1 << OZ_BETA;
+            v += 1;
+        }
+        dg[p] = d;
+    }
+    dg[0] = (int)v;  // 0..128
+    if (u >> 63)
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) dg[p] = -dg[p];
+}
+
+// Digits of every row of X (row-major N x N per item): E[b][i] and the planes
+// (plane p at p * plane_stride, leading dimension ldp; columns N..ldp-1 stay
+// zero).
 __global__ void __launch_bounds__(128) k_oz_slice(const double *X, long long sX, int N, int ldp,
                                                   long long plane_stride, __nv_bfloat16 *planes, int *E)
 {
@@ -100,56 +133,87 @@ __global__ void __launch_bounds__(128) k_oz_slice(const double *X, long long sX,
     __syncthreads();
     mx = red[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = red[w] > mx ? red[w] : mx;
-    // |x| < 2^Ei for every element of the row (Ei = frexp exponent of the max);
-    // a row of zeros or subnormals gets digits 0
     const int ef_max = (int)(mx >> 52);
     const int Ei = ef_max > 0 ? ef_max - 1022 : 0;
     if (threadIdx.x == 0) E[(long long)b * N + i] = Ei;
     const long long row = (long long)b * N * ldp + (long long)i * ldp;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const unsigned long long u = (unsigned long long)__double_as_longlong(x[k]);
-        const int ef = (int)((u >> 52) & 0x7FF);
-        long long v = 0;
-        if (ef > 0 && ef_max > 0) {
-            // x = m 2^(ef - 1075); v = round(|x| 2^(56 - Ei)) < 2^56
-            const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-            const int sh = ef - 1075 + 56 - Ei;
-            if (sh >= 0) v = (long long)(m << sh);  // sh <= 3 since |x| < 2^Ei
-            else if (sh > -60) v = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
-        }
         int dg[OZ_S];
-#pragma unroll
-        for (int p = OZ_S - 1; p >= 1; --p) {
-            int d = (int)(v & ((1 << OZ_BETA) - 1));
-            v >>= OZ_BETA;
-            if (d >= (1 << (OZ_BETA - 1))) {
-                d -= 1 << OZ_BETA;
-                v += 1;
-            }
-            dg[p] = d;
-        }
-        dg[0] = (int)v;  // 0..128
-        const bool neg = (u >> 63) != 0;
+        oz_digits(x[k], Ei, ef_max, dg);
 #pragma unroll
         for (int p = 0; p < OZ_S; ++p)
-            planes[(long long)p * plane_stride + row + k] = __float2bfloat16_rn((float)(neg ? -dg[p] : dg[p]));
+            planes[(long long)p * plane_stride + row + k] = __float2bfloat16_rn((float)dg[p]);
+    }
+}
+
+// Digits of a 32-wide K-block read column-wise: output row r (0 <= r < R) has
+// the kb values src[k * ld + r], k < kb (zero for kb <= k < 32).  Planes are
+// [plane][item][row][32]; E[b * sE + r].  One CTA converts 32 rows: the
+// 32 x 32 block is read coalesced along r, and eight threads share a row.
+__global__ void __launch_bounds__(256) k_oz_slice_cols(const double *src, long long sS, long long ld, int R, int kb,
+                                                       long long plane_stride, int rows_cap, __nv_bfloat16 *planes,
+                                                       int *E, long long sE)
+{
+    __shared__ double tile[32][33];
+    const int b = blockIdx.y, r0 = blockIdx.x * 32;
+    const double *s = src + (long long)b * sS;
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+        const int k = idx >> 5, r = idx & 31;
+        tile[k][r] = (k < kb && r0 + r < R) ? s[(long long)k * ld + r0 + r] : 0.0;
+    }
+    __syncthreads();
+    const int r = threadIdx.x >> 3, q = threadIdx.x & 7;  // row, quarter of its 32 values
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(tile[4 * q + j][r]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = u > mx ? u : mx;
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o, 8);
+        mx = v > mx ? v : mx;
+    }
+    if (r0 + r >= R) return;
+    const int ef_max = (int)(mx >> 52);
+    const int Er = ef_max > 0 ? ef_max - 1022 : 0;
+    if (q == 0) E[(long long)b * sE + r0 + r] = Er;
+    int dg[4][OZ_S];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) oz_digits(tile[4 * q + j][r], Er, ef_max, dg[j]);
+    const long long row = ((long long)b * rows_cap + r0 + r) * 32 + 4 * q;
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) {
+        __nv_bfloat162 h2[2] = {__floats2bfloat162_rn((float)dg[0][p], (float)dg[1][p]),
+                                __floats2bfloat162_rn((float)dg[2][p], (float)dg[3][p])};
+        *reinterpret_cast<uint2 *>(planes + (long long)p * plane_stride + row) = *reinterpret_cast<const uint2 *>(h2);
     }
 }
 
 struct OzArgs {
-    int N, batch, nk;
-    const int *E;
-    double *W;
-    long long sW;
-    int ldw;
+    int M, Nn;              // rows of A (rows of C) and rows of B (columns of C)
+    int batch, nk;          // items, 32-wide K-blocks
+    const int *EA, *EB;     // row exponents of A and B
+    long long sEA, sEB;     // their item strides
+    double *C;              // result: row stride ldc, item stride sC
+    long long sC;
+    int ldc;
     int *flag;
 };
 
-// tile t of the persistent walk -> (item, first row, first column)
+// Tile t of the persistent walk -> (item, first row, first column).  GRAM:
+// the 128 x 32 tiles on or above the diagonal; otherwise every tile, columns
+// fastest.
+template <bool GRAM>
 __device__ __forceinline__ void oz_tile(int t, int tiles_m, int tiles_n, int per_item, int &b, int &m0, int &n0)
 {
     b = t / per_item;
     int r = t - b * per_item;
+    if (!GRAM) {
+        m0 = (r / tiles_n) * OBM;
+        n0 = (r % tiles_n) * OBN;
+        return;
+    }
     int tm = 0;
     for (; tm < tiles_m; ++tm) {
         const int cnt = tiles_n - 4 * tm;
@@ -160,8 +224,20 @@ __device__ __forceinline__ void oz_tile(int t, int tiles_m, int tiles_n, int per
     n0 = (4 * tm + r) * OBN;
 }
 
+template <bool GRAM>
+__host__ __device__ inline int oz_per_item(int tiles_m, int tiles_n)
+{
+    if (!GRAM) return tiles_m * tiles_n;
+    int n = 0;
+    for (int tm = 0; tm < tiles_m; ++tm) n += tiles_n - 4 * tm;
+    return n;
+}
+
+// GRAM: C = A A^T written on and above the diagonal (A and B the same planes);
+// otherwise C -= A B^T on every tile.
+template <bool GRAM>
 __global__ void __launch_bounds__(OTHREADS, 1)
-    k_oz_gram(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzArgs a)
+    k_oz_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -172,9 +248,8 @@ __global__ void __launch_bounds__(OTHREADS, 1)
     uint32_t *tmem_slot = (uint32_t *)(tmem_free + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_m = (a.N + OBM - 1) / OBM, tiles_n = (a.N + OBN - 1) / OBN;
-    int per_item = 0;
-    for (int tm = 0; tm < tiles_m; ++tm) per_item += tiles_n - 4 * tm;
+    const int tiles_m = (a.M + OBM - 1) / OBM, tiles_n = (a.Nn + OBN - 1) / OBN;
+    const int per_item = oz_per_item<GRAM>(tiles_m, tiles_n);
     const int tiles = per_item * a.batch;
 
     if (threadIdx.x == 0) {
@@ -205,7 +280,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
                 int b, m0, n0;
-                oz_tile(t, tiles_m, tiles_n, per_item, b, m0, n0);
+                oz_tile<GRAM>(t, tiles_m, tiles_n, per_item, b, m0, n0);
                 for (int kb = 0; kb < a.nk; ++kb, ++it) {
                     const int s = it % OSTAGES;
                     if (it >= OSTAGES && !mbar_wait(&empty[s], ((it / OSTAGES) - 1) & 1, a.flag)) { ok = false; break; }
@@ -263,10 +338,10 @@ __global__ void __launch_bounds__(OTHREADS, 1)
         int ti = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
             int b, m0, n0;
-            oz_tile(t, tiles_m, tiles_n, per_item, b, m0, n0);
+            oz_tile<GRAM>(t, tiles_m, tiles_n, per_item, b, m0, n0);
             const int u = ti & 1;
             const int mm = m0 + q4 * 32 + lane;
-            const int Ei = mm < a.N ? a.E[(long long)b * a.N + mm] : 0;
+            const int Ei = mm < a.M ? a.EA[(long long)b * a.sEA + mm] : 0;
             const bool ok = mbar_wait(&tmem_full[u], (ti >> 1) & 1, a.flag);
             fence_after();
             float g[OZ_G][16];
@@ -286,7 +361,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tmem_free[u])) : "memory");
             if (!ok) break;
-            if (mm >= a.N) continue;
+            if (mm >= a.M) continue;
             double w[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -299,15 +374,18 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                 for (int gg = 4; gg < 8; ++gg) l += (long long)__float2int_rn(g[gg][j]) << (OZ_BETA * (7 - gg));
                 w[j] = fma((double)l, 0x1p-28, (double)h);
             }
-            double *o = a.W + (long long)b * a.sW + (long long)mm * a.ldw;
+            double *o = a.C + (long long)b * a.sC + (long long)mm * a.ldc;
             const int nb = n0 + hc;
+            const int *eb = a.EB + (long long)b * a.sEB;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int n = nb + j;
-                if (n < a.N) {
-                    const int e = Ei + a.E[(long long)b * a.N + n] - 35;
-                    o[n] = (e > -1000 && e < 1000) ? w[j] * __longlong_as_double((long long)(e + 1023) << 52)
-                                                   : scalbn(w[j], e);
+                if (n < a.Nn) {
+                    const int e = Ei + eb[n] - 35;
+                    const double v = (e > -1000 && e < 1000) ? w[j] * __longlong_as_double((long long)(e + 1023) << 52)
+                                                             : scalbn(w[j], e);
+                    if (GRAM) o[n] = v;
+                    else o[n] -= v;
                 }
             }
         }
@@ -322,9 +400,15 @@ __global__ void __launch_bounds__(OTHREADS, 1)
 struct OzWs {
     int ldp;
     long long plane_stride;
-    __nv_bfloat16 *planes;
+    __nv_bfloat16 *planes;  // digit planes of the Gram operand
     int *E;
     CUtensorMap mapA, mapB;
+    // 32-wide K-blocks of the Cholesky-QR trailing updates: A = R_blk^T
+    // (rows of the trailing part), B = Q^T_blk^T (N rows)
+    long long kplane_stride;
+    __nv_bfloat16 *kA, *kB;
+    int *EA, *EB;
+    CUtensorMap mapKA, mapKB;
     int num_sms;
 };
 
@@ -351,22 +435,26 @@ int oz_prepare(sldqmc_ctx *c)
     const int N = c->N;
     w->ldp = (N + 63) / 64 * 64;
     w->plane_stride = (long long)c->cap * N * w->ldp;
+    w->kplane_stride = (long long)c->cap * N * OKE;
     const size_t pbytes = (size_t)OZ_S * w->plane_stride * sizeof(__nv_bfloat16);
-    if (cudaMalloc(&w->planes, pbytes) != cudaSuccess) {
+    const size_t kbytes = (size_t)OZ_S * w->kplane_stride * sizeof(__nv_bfloat16);
+    const size_t ebytes = sizeof(int) * (size_t)c->cap * N;
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, pbytes + 2 * kbytes + 3 * ebytes) != cudaSuccess) {
         cudaGetLastError();
         delete w;
         return SLDQMC_ERR_OOM;
     }
-    if (cudaMalloc(&w->E, sizeof(int) * (size_t)c->cap * N) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(w->planes);
-        delete w;
-        return SLDQMC_ERR_OOM;
-    }
-    cudaMemsetAsync(w->planes, 0, pbytes, c->st);  // zero pads: columns N..ldp-1 are never written
-    if (!encode4(&w->mapA, w->planes, w->ldp, N, c->cap, OBM) || !encode4(&w->mapB, w->planes, w->ldp, N, c->cap, OBN)) {
-        cudaFree(w->planes);
-        cudaFree(w->E);
+    w->planes = (__nv_bfloat16 *)mem;
+    w->kA = (__nv_bfloat16 *)((uint8_t *)mem + pbytes);
+    w->kB = (__nv_bfloat16 *)((uint8_t *)mem + pbytes + kbytes);
+    w->E = (int *)((uint8_t *)mem + pbytes + 2 * kbytes);
+    w->EA = w->E + (size_t)c->cap * N;
+    w->EB = w->EA + (size_t)c->cap * N;
+    cudaMemsetAsync(mem, 0, pbytes + 2 * kbytes + 3 * ebytes, c->st);  // zero pads: never written
+    if (!encode4(&w->mapA, w->planes, w->ldp, N, c->cap, OBM) || !encode4(&w->mapB, w->planes, w->ldp, N, c->cap, OBN) ||
+        !encode4(&w->mapKA, w->kA, OKE, N, c->cap, OBM) || !encode4(&w->mapKB, w->kB, OKE, N, c->cap, OBN)) {
+        cudaFree(mem);
         delete w;
         return SLDQMC_ERR_CUDA;
     }
@@ -374,7 +462,8 @@ int oz_prepare(sldqmc_ctx *c)
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || w->num_sms < 1)
         w->num_sms = 148;
-    cudaFuncSetAttribute(k_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    cudaFuncSetAttribute(k_oz_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    cudaFuncSetAttribute(k_oz_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
     c->oz_ws = w;
     return SLDQMC_OK;
 }
@@ -384,7 +473,6 @@ void oz_release(sldqmc_ctx *c)
     OzWs *w = (OzWs *)c->oz_ws;
     if (!w) return;
     cudaFree(w->planes);
-    cudaFree(w->E);
     delete w;
     c->oz_ws = nullptr;
 }
@@ -397,23 +485,57 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
     const int N = c->N;
     k_oz_slice<<<dim3(N, B), 128, 0, c->st>>>(X, sX, N, w->ldp, w->plane_stride, w->planes, w->E);
     OzArgs a{};
-    a.N = N;
+    a.M = N;
+    a.Nn = N;
     a.batch = B;
     a.nk = w->ldp / OKE;
-    a.E = w->E;
-    a.W = W;
-    a.sW = sW;
-    a.ldw = ldw;
+    a.EA = w->E;
+    a.EB = w->E;
+    a.sEA = N;
+    a.sEB = N;
+    a.C = W;
+    a.sC = sW;
+    a.ldc = ldw;
     a.flag = c->d_flag;
-    const int tiles_m = (N + OBM - 1) / OBM, tiles_n = (N + OBN - 1) / OBN;
-    int per_item = 0;
-    for (int tm = 0; tm < tiles_m; ++tm) per_item += tiles_n - 4 * tm;
-    const int tiles = per_item * B;
+    const int tiles = oz_per_item<true>((N + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
     const int grid = tiles < w->num_sms ? tiles : w->num_sms;
     prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B);
-    k_oz_gram<<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapB, a);
+    k_oz_gemm<true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapB, a);
     prof_end(c);
     c->launches += 2;
+}
+
+// Trailing update of the stacked Cholesky-QR: C -= A B^T with
+// A[r][l] = Asrc[l * ldA + r] (r < M), B[n][l] = Bsrc[l * ldB + n] (n < N),
+// l < kb <= 32; C row stride ldc; all item strides nn.
+void oz_update(sldqmc_ctx *c, const double *Asrc, long long ldA, int M, const double *Bsrc, long long ldB, int kb,
+               double *C, int ldc, int B)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    const int N = c->N;
+    k_oz_slice_cols<<<dim3((M + 31) / 32, B), 256, 0, c->st>>>(Asrc, c->nn, ldA, M, kb, w->kplane_stride, N, w->kA,
+                                                              w->EA, N);
+    k_oz_slice_cols<<<dim3((N + 31) / 32, B), 256, 0, c->st>>>(Bsrc, c->nn, ldB, N, kb, w->kplane_stride, N, w->kB,
+                                                              w->EB, N);
+    OzArgs a{};
+    a.M = M;
+    a.Nn = N;
+    a.batch = B;
+    a.nk = 1;
+    a.EA = w->EA;
+    a.EB = w->EB;
+    a.sEA = N;
+    a.sEB = N;
+    a.C = C;
+    a.sC = c->nn;
+    a.ldc = ldc;
+    a.flag = c->d_flag;
+    const int tiles = oz_per_item<false>((M + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
+    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * M * N * kb * B);
+    k_oz_gemm<false><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapKA, w->mapKB, a);
+    prof_end(c);
+    c->launches += 3;
 }
 
 }  // namespace sldqmc

@@ -451,11 +451,16 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
                                   W + (long long)(k0 + kb) * N + k0 + kb, N, sW, B);
             g.alpha = -1.0; g.beta = 1.0; g.c_upper = 1;
             gemm_ctx(c, g, true, false);
-            // Y[k0+kb:, :] -= R_blk^T Qt_blk
-            GemmF64 h = gemm_desc(nW, N, kb, R + (long long)k0 * N + k0 + kb, N, nn,
-                                  Y + (long long)k0 * N, N, nn, Y + (long long)(k0 + kb) * N, N, nn, B);
-            h.alpha = -1.0; h.beta = 1.0;
-            gemm_ctx(c, h, true, false);
+            // Y[k0+kb:, :] -= R_blk^T Qt_blk: FP64, or FP64-accurate on the tensor cores
+            if (c->oz_ws) {
+                oz_update(c, R + (long long)k0 * N + k0 + kb, N, nW, Y + (long long)k0 * N, N, kb,
+                          Y + (long long)(k0 + kb) * N, N, B);
+            } else {
+                GemmF64 h = gemm_desc(nW, N, kb, R + (long long)k0 * N + k0 + kb, N, nn,
+                                      Y + (long long)k0 * N, N, nn, Y + (long long)(k0 + kb) * N, N, nn, B);
+                h.alpha = -1.0; h.beta = 1.0;
+                gemm_ctx(c, h, true, false);
+            }
         }
     }
 }
