@@ -440,7 +440,8 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
         int kb = N - k0 < 32 ? N - k0 : 32;
         int nW = N - (k0 + kb);
         dim3 grid(cdiv(nW + N, 128), B);
-        prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
+        // algorithmic flops: factor of the kb x kb block, triangular solves of nW + N columns
+        prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * ((double)kb * kb * kb / 3.0 + (double)(nW + N) * kb * kb));
         k_chol_panel<32><<<grid, 128, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
         prof_end(c);
         c->launches++;
@@ -547,7 +548,7 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
     const long long sItem = (long long)N * lda;
     for (int k0 = 0; k0 < N; k0 += 32) {
         int kb = N - k0 < 32 ? N - k0 : 32;
-        prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
+        prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * (N - k0) * kb * kb);
         k_lu_panel<<<B, 1024, 0, c->st>>>(A, sItem, lda, N, ncols, k0, kb, c->d_piv, c->d_logacc,
                                           c->d_sgn + c->cap, c->d_flag);
         prof_end(c);
@@ -555,7 +556,7 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
         int rest = ncols - (k0 + kb);
         if (rest > 0) {
             dim3 gt(cdiv(rest, 128), B);
-            prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
+            prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * rest * kb * kb);
             k_lu_trsm_row<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, ncols, k0, kb);
             prof_end(c);
             c->launches++;
@@ -575,7 +576,7 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
             int k0 = kbi * 32;
             int kb = N - k0 < 32 ? N - k0 : 32;
             dim3 gt(cdiv(N, 128), B);
-            prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
+            prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * N * kb * kb);
             k_trsm_upper_rhs<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, N, k0, kb);
             prof_end(c);
             c->launches++;
