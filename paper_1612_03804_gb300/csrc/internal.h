@@ -70,11 +70,12 @@ void tc_update_V(sldqmc_ctx *c, const double *R, double *V, int B);
 int oz_prepare(sldqmc_ctx *c);
 void oz_release(sldqmc_ctx *c);
 void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long sW, int ldw, int B);
-// Trailing update C -= A B^T of the stacked Cholesky-QR, FP64-accurate on the
-// tensor cores: A[r][l] = Asrc[l*ldA + r] (r < M), B[n][l] = Bsrc[l*ldB + n]
-// (n < N), l < kb <= 32; C row stride ldc; item strides N*N.
-void oz_update(sldqmc_ctx *c, const double *Asrc, long long ldA, int M, const double *Bsrc, long long ldB, int kb,
-               double *C, int ldc, int B);
+// Trailing updates of the stacked Cholesky-QR after a panel of kb <= 32
+// columns, FP64-accurate on the tensor cores: with A[r][l] = Asrc[l*N + r]
+// (r < M) and B[n][l] = Bsrc[l*N + n] (n < N), Yt -= A B^T and Wt -= A A^T
+// (tiles on or above the diagonal); row strides N, item strides N*N (sW for Wt).
+void oz_trailing(sldqmc_ctx *c, const double *Asrc, int M, const double *Bsrc, int kb, double *Yt, double *Wt,
+                 long long sW, int B);
 
 // Event-bracketed timing of launches (sldqmc_profile_*).
 struct ProfRec {

@@ -201,15 +201,15 @@ struct OzArgs {
     int *flag;
 };
 
-// Tile t of the persistent walk -> (item, first row, first column).  GRAM:
+// Tile t of the persistent walk -> (item, first row, first column).  UPPER:
 // the 128 x 32 tiles on or above the diagonal; otherwise every tile, columns
 // fastest.
-template <bool GRAM>
+template <bool UPPER>
 __device__ __forceinline__ void oz_tile(int t, int tiles_m, int tiles_n, int per_item, int &b, int &m0, int &n0)
 {
     b = t / per_item;
     int r = t - b * per_item;
-    if (!GRAM) {
+    if (!UPPER) {
         m0 = (r / tiles_n) * OBM;
         n0 = (r % tiles_n) * OBN;
         return;
@@ -224,18 +224,18 @@ __device__ __forceinline__ void oz_tile(int t, int tiles_m, int tiles_n, int per
     n0 = (4 * tm + r) * OBN;
 }
 
-template <bool GRAM>
+template <bool UPPER>
 __host__ __device__ inline int oz_per_item(int tiles_m, int tiles_n)
 {
-    if (!GRAM) return tiles_m * tiles_n;
+    if (!UPPER) return tiles_m * tiles_n;
     int n = 0;
     for (int tm = 0; tm < tiles_m; ++tm) n += tiles_n - 4 * tm;
     return n;
 }
 
-// GRAM: C = A A^T written on and above the diagonal (A and B the same planes);
-// otherwise C -= A B^T on every tile.
-template <bool GRAM>
+// UPPER: only the tiles on or above the diagonal (C square, A and B the same
+// rows); SUB: C -= A B^T, otherwise C = A B^T.
+template <bool UPPER, bool SUB>
 __global__ void __launch_bounds__(OTHREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzArgs a)
 {
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_m = (a.M + OBM - 1) / OBM, tiles_n = (a.Nn + OBN - 1) / OBN;
-    const int per_item = oz_per_item<GRAM>(tiles_m, tiles_n);
+    const int per_item = oz_per_item<UPPER>(tiles_m, tiles_n);
     const int tiles = per_item * a.batch;
 
     if (threadIdx.x == 0) {
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
                 int b, m0, n0;
-                oz_tile<GRAM>(t, tiles_m, tiles_n, per_item, b, m0, n0);
+                oz_tile<UPPER>(t, tiles_m, tiles_n, per_item, b, m0, n0);
                 for (int kb = 0; kb < a.nk; ++kb, ++it) {
                     const int s = it % OSTAGES;
                     if (it >= OSTAGES && !mbar_wait(&empty[s], ((it / OSTAGES) - 1) & 1, a.flag)) { ok = false; break; }
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
         int ti = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
             int b, m0, n0;
-            oz_tile<GRAM>(t, tiles_m, tiles_n, per_item, b, m0, n0);
+            oz_tile<UPPER>(t, tiles_m, tiles_n, per_item, b, m0, n0);
             const int u = ti & 1;
             const int mm = m0 + q4 * 32 + lane;
             const int Ei = mm < a.M ? a.EA[(long long)b * a.sEA + mm] : 0;
@@ -384,8 +384,8 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                     const int e = Ei + eb[n] - 35;
                     const double v = (e > -1000 && e < 1000) ? w[j] * __longlong_as_double((long long)(e + 1023) << 52)
                                                              : scalbn(w[j], e);
-                    if (GRAM) o[n] = v;
-                    else o[n] -= v;
+                    if (SUB) o[n] -= v;
+                    else o[n] = v;
                 }
             }
         }
@@ -408,7 +408,7 @@ struct OzWs {
     long long kplane_stride;
     __nv_bfloat16 *kA, *kB;
     int *EA, *EB;
-    CUtensorMap mapKA, mapKB;
+    CUtensorMap mapKA, mapKB, mapKA32;  // mapKA32: A planes in 32-row boxes (symmetric W update)
     int num_sms;
 };
 
@@ -453,7 +453,8 @@ int oz_prepare(sldqmc_ctx *c)
     w->EB = w->EA + (size_t)c->cap * N;
     cudaMemsetAsync(mem, 0, pbytes + 2 * kbytes + 3 * ebytes, c->st);  // zero pads: never written
     if (!encode4(&w->mapA, w->planes, w->ldp, N, c->cap, OBM) || !encode4(&w->mapB, w->planes, w->ldp, N, c->cap, OBN) ||
-        !encode4(&w->mapKA, w->kA, OKE, N, c->cap, OBM) || !encode4(&w->mapKB, w->kB, OKE, N, c->cap, OBN)) {
+        !encode4(&w->mapKA, w->kA, OKE, N, c->cap, OBM) || !encode4(&w->mapKB, w->kB, OKE, N, c->cap, OBN) ||
+        !encode4(&w->mapKA32, w->kA, OKE, N, c->cap, OBN)) {
         cudaFree(mem);
         delete w;
         return SLDQMC_ERR_CUDA;
@@ -462,8 +463,9 @@ int oz_prepare(sldqmc_ctx *c)
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || w->num_sms < 1)
         w->num_sms = 148;
-    cudaFuncSetAttribute(k_oz_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
-    cudaFuncSetAttribute(k_oz_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    cudaFuncSetAttribute(k_oz_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    cudaFuncSetAttribute(k_oz_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    cudaFuncSetAttribute(k_oz_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
     c->oz_ws = w;
     return SLDQMC_OK;
 }
@@ -500,22 +502,25 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
     const int tiles = oz_per_item<true>((N + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
     const int grid = tiles < w->num_sms ? tiles : w->num_sms;
     prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B);
-    k_oz_gemm<true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapB, a);
+    k_oz_gemm<true, false><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapB, a);
     prof_end(c);
     c->launches += 2;
 }
 
-// Trailing update of the stacked Cholesky-QR: C -= A B^T with
-// A[r][l] = Asrc[l * ldA + r] (r < M), B[n][l] = Bsrc[l * ldB + n] (n < N),
-// l < kb <= 32; C row stride ldc; all item strides nn.
-void oz_update(sldqmc_ctx *c, const double *Asrc, long long ldA, int M, const double *Bsrc, long long ldB, int kb,
-               double *C, int ldc, int B)
+// Trailing updates of the stacked Cholesky-QR after a panel of kb <= 32
+// columns: with A[r][l] = Asrc[l * N + r] (the panel's block row of R beyond
+// the panel, r < M) and B[n][l] = Bsrc[l * N + n] (the panel's rows of Q^T,
+// n < N),
+//   Yt -= A B^T   (all M x N),      Wt -= A A^T   (tiles on or above the diagonal),
+// Yt, Wt row stride N; item strides N*N for A, B, Yt and sW for Wt.
+void oz_trailing(sldqmc_ctx *c, const double *Asrc, int M, const double *Bsrc, int kb, double *Yt, double *Wt,
+                 long long sW, int B)
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
-    k_oz_slice_cols<<<dim3((M + 31) / 32, B), 256, 0, c->st>>>(Asrc, c->nn, ldA, M, kb, w->kplane_stride, N, w->kA,
+    k_oz_slice_cols<<<dim3((M + 31) / 32, B), 256, 0, c->st>>>(Asrc, c->nn, N, M, kb, w->kplane_stride, N, w->kA,
                                                               w->EA, N);
-    k_oz_slice_cols<<<dim3((N + 31) / 32, B), 256, 0, c->st>>>(Bsrc, c->nn, ldB, N, kb, w->kplane_stride, N, w->kB,
+    k_oz_slice_cols<<<dim3((N + 31) / 32, B), 256, 0, c->st>>>(Bsrc, c->nn, N, N, kb, w->kplane_stride, N, w->kB,
                                                               w->EB, N);
     OzArgs a{};
     a.M = M;
@@ -526,16 +531,25 @@ void oz_update(sldqmc_ctx *c, const double *Asrc, long long ldA, int M, const do
     a.EB = w->EB;
     a.sEA = N;
     a.sEB = N;
-    a.C = C;
+    a.C = Yt;
     a.sC = c->nn;
-    a.ldc = ldc;
+    a.ldc = N;
     a.flag = c->d_flag;
-    const int tiles = oz_per_item<false>((M + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
-    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
+    int tiles = oz_per_item<false>((M + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
+    int grid = tiles < w->num_sms ? tiles : w->num_sms;
     prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * M * N * kb * B);
-    k_oz_gemm<false><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapKA, w->mapKB, a);
+    k_oz_gemm<false, true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapKA, w->mapKB, a);
     prof_end(c);
-    c->launches += 3;
+    a.Nn = M;
+    a.EB = w->EA;
+    a.C = Wt;
+    a.sC = sW;
+    tiles = oz_per_item<true>((M + OBM - 1) / OBM, (M + OBN - 1) / OBN) * B;
+    grid = tiles < w->num_sms ? tiles : w->num_sms;
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)M * (M + 1) * kb * B);
+    k_oz_gemm<true, true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapKA, w->mapKA32, a);
+    prof_end(c);
+    c->launches += 4;
 }
 
 }  // namespace sldqmc

@@ -445,23 +445,23 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
         k_chol_panel<32><<<grid, 128, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
         prof_end(c);
         c->launches++;
-        if (nW > 0) {
+        if (nW > 0 && c->oz_ws) {
+            // W[k0+kb:, k0+kb:] -= R_blk^T R_blk (upper) and Y[k0+kb:, :] -= R_blk^T Qt_blk,
+            // FP64-accurate on the tensor cores
+            oz_trailing(c, R + (long long)k0 * N + k0 + kb, nW, Y + (long long)k0 * N, kb,
+                        Y + (long long)(k0 + kb) * N, W + (long long)(k0 + kb) * N + k0 + kb, sW, B);
+        } else if (nW > 0) {
             // W[k0+kb:, k0+kb:] -= R_blk^T R_blk   (upper triangle only)
             GemmF64 g = gemm_desc(nW, nW, kb, R + (long long)k0 * N + k0 + kb, N, nn,
                                   R + (long long)k0 * N + k0 + kb, N, nn,
                                   W + (long long)(k0 + kb) * N + k0 + kb, N, sW, B);
             g.alpha = -1.0; g.beta = 1.0; g.c_upper = 1;
             gemm_ctx(c, g, true, false);
-            // Y[k0+kb:, :] -= R_blk^T Qt_blk: FP64, or FP64-accurate on the tensor cores
-            if (c->oz_ws) {
-                oz_update(c, R + (long long)k0 * N + k0 + kb, N, nW, Y + (long long)k0 * N, N, kb,
-                          Y + (long long)(k0 + kb) * N, N, B);
-            } else {
-                GemmF64 h = gemm_desc(nW, N, kb, R + (long long)k0 * N + k0 + kb, N, nn,
-                                      Y + (long long)k0 * N, N, nn, Y + (long long)(k0 + kb) * N, N, nn, B);
-                h.alpha = -1.0; h.beta = 1.0;
-                gemm_ctx(c, h, true, false);
-            }
+            // Y[k0+kb:, :] -= R_blk^T Qt_blk
+            GemmF64 h = gemm_desc(nW, N, kb, R + (long long)k0 * N + k0 + kb, N, nn,
+                                  Y + (long long)k0 * N, N, nn, Y + (long long)(k0 + kb) * N, N, nn, B);
+            h.alpha = -1.0; h.beta = 1.0;
+            gemm_ctx(c, h, true, false);
         }
     }
 }
