@@ -342,9 +342,22 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             const int u = ti & 1;
             const int mm = m0 + q4 * 32 + lane;
             const int Ei = mm < a.M ? a.EA[(long long)b * a.sEA + mm] : 0;
+            // for an update, the old values of this thread's row segment, fetched
+            // while the MMAs run
+            double *o = a.C + (long long)b * a.sC + (long long)mm * a.ldc;
+            const int nb = n0 + hc;
+            const int *eb = a.EB + (long long)b * a.sEB;
+            double cold[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) cold[j] = (SUB && mm < a.M && nb + j < a.Nn) ? o[nb + j] : 0.0;
             const bool ok = mbar_wait(&tmem_full[u], (ti >> 1) & 1, a.flag);
             fence_after();
-            float g[OZ_G][16];
+            // group sums as exact integers, folded as they arrive: groups 0..3
+            // (p + q = 2..5) into h, 4..7 (6..9) into l, so that
+            // sum_g acc_g 2^-7(g+2) = h 2^-35 + l 2^-63
+            long long h[16], l[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) h[j] = l[j] = 0;
             const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(u * OZ_G * OBN + hc);
 #pragma unroll
             for (int gg = 0; gg < OZ_G; gg += 2) {
@@ -354,8 +367,10 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                 tmem_wait_ld32(r0, r1);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    g[gg][j] = __uint_as_float(r0[j]);
-                    g[gg + 1][j] = __uint_as_float(r1[j]);
+                    const long long v0 = (long long)__float2int_rn(__uint_as_float(r0[j]));
+                    const long long v1 = (long long)__float2int_rn(__uint_as_float(r1[j]));
+                    if (gg < 4) h[j] += (v0 << (OZ_BETA * (3 - gg))) + (v1 << (OZ_BETA * (2 - gg)));
+                    else l[j] += (v0 << (OZ_BETA * (7 - gg))) + (v1 << (OZ_BETA * (6 - gg)));
                 }
             }
             fence_before();
@@ -364,19 +379,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             if (mm >= a.M) continue;
             double w[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                // groups 0..3 (p + q = 2..5) and 4..7 (6..9) as integers:
-                // sum_g acc_g 2^-7(g+2) = h 2^-35 + l 2^-63
-                long long h = 0, l = 0;
-#pragma unroll
-                for (int gg = 0; gg < 4; ++gg) h += (long long)__float2int_rn(g[gg][j]) << (OZ_BETA * (3 - gg));
-#pragma unroll
-                for (int gg = 4; gg < 8; ++gg) l += (long long)__float2int_rn(g[gg][j]) << (OZ_BETA * (7 - gg));
-                w[j] = fma((double)l, 0x1p-28, (double)h);
-            }
-            double *o = a.C + (long long)b * a.sC + (long long)mm * a.ldc;
-            const int nb = n0 + hc;
-            const int *eb = a.EB + (long long)b * a.sEB;
+            for (int j = 0; j < 16; ++j) w[j] = fma((double)l[j], 0x1p-28, (double)h[j]);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int n = nb + j;
@@ -384,8 +387,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                     const int e = Ei + eb[n] - 35;
                     const double v = (e > -1000 && e < 1000) ? w[j] * __longlong_as_double((long long)(e + 1023) << 52)
                                                              : scalbn(w[j], e);
-                    if (SUB) o[n] -= v;
-                    else o[n] = v;
+                    o[n] = SUB ? cold[j] - v : v;
                 }
             }
         }
