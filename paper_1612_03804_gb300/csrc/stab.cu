@@ -315,6 +315,109 @@ __global__ void __launch_bounds__(1024) k_lu_panel(double *A, long long sA, int 
     }
 }
 
+// The same panel factorisation with the panel (rows k0..N-1, kb <= 32
+// columns) held in shared memory: pivot search, row swap, scaling and rank-1
+// update run on shared memory, the row interchanges are applied to the
+// columns outside the panel afterwards (in pivot order), and the logarithms
+// of the pivots are taken in parallel and added in pivot order.  Same pivot
+// choice (largest |v|, lowest row on ties) and the same arithmetic as
+// k_lu_panel.  Dynamic shared memory: (N - k0) * 33 doubles + 2 * 32 values.
+constexpr int LU_SMEM_MAX_ROWS = 800;
+__global__ void __launch_bounds__(1024) k_lu_panel_smem(double *A, long long sA, int lda, int N, int ncols, int k0,
+                                                        int kb, int *piv, double *logacc, int *lusgn, int *flag)
+{
+    extern __shared__ double P[];  // [R][33]
+    __shared__ double wv[32], pv[32], lg[32];
+    __shared__ int wi[32], pr[32];
+    __shared__ int s_p;
+    const int b = blockIdx.x;
+    double *Ab = A + (long long)b * sA;
+    const int R = N - k0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = wid; r < R; r += nw) P[r * 33 + lane] = lane < kb ? Ab[(long long)(k0 + r) * lda + k0 + lane] : 0.0;
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        double best = -1.0;
+        int bi = R;
+        for (int r = j + threadIdx.x; r < R; r += blockDim.x) {
+            const double v = fabs(P[r * 33 + j]);
+            if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bv = wv[0];
+            int bidx = wi[0];
+            for (int w = 1; w < nw; ++w)
+                if (wv[w] > bv || (wv[w] == bv && wi[w] < bidx)) { bv = wv[w]; bidx = wi[w]; }
+            const int p = bidx < R ? bidx : j;
+            s_p = p;
+            pr[j] = p;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != j && threadIdx.x < 32) {
+            const double t = P[j * 33 + threadIdx.x];
+            P[j * 33 + threadIdx.x] = P[p * 33 + threadIdx.x];
+            P[p * 33 + threadIdx.x] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v = P[j * 33 + j];
+            if (v == 0.0 || !isfinite(v)) {
+                atomicOr(flag, FLAG_NUMERICAL);
+                v = 1.0;
+                P[j * 33 + j] = 1.0;
+            }
+            pv[j] = v;
+        }
+        __syncthreads();
+        const double vinv = 1.0 / P[j * 33 + j];
+        for (int r = j + 1 + threadIdx.x; r < R; r += blockDim.x) P[r * 33 + j] *= vinv;
+        __syncthreads();
+        if (j + 1 < kb)
+            for (int r = j + 1 + wid; r < R; r += nw)
+                if (lane > j && lane < kb) P[r * 33 + lane] -= P[r * 33 + j] * P[j * 33 + lane];
+        __syncthreads();
+    }
+    // the factored panel back to global memory
+    for (int r = wid; r < R; r += nw)
+        if (lane < kb) Ab[(long long)(k0 + r) * lda + k0 + lane] = P[r * 33 + lane];
+    // row interchanges of the columns outside the panel, in pivot order
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+        if (c >= k0 && c < k0 + kb) continue;
+        for (int j = 0; j < kb; ++j) {
+            const int p = pr[j];
+            if (p != j) {
+                const double t = Ab[(long long)(k0 + j) * lda + c];
+                Ab[(long long)(k0 + j) * lda + c] = Ab[(long long)(k0 + p) * lda + c];
+                Ab[(long long)(k0 + p) * lda + c] = t;
+            }
+        }
+    }
+    if (threadIdx.x < kb) {
+        lg[threadIdx.x] = log(fabs(pv[threadIdx.x]));
+        piv[(long long)b * N + k0 + threadIdx.x] = k0 + pr[threadIdx.x];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = logacc[b];
+        int sg = 1;
+        for (int j = 0; j < kb; ++j) {
+            acc += lg[j];
+            if (pr[j] != j) sg = -sg;
+            if (pv[j] < 0.0) sg = -sg;
+        }
+        logacc[b] = acc;
+        lusgn[b] *= sg;
+    }
+}
+
 // U12 = L11^{-1} A12 for the block row k0..k0+kb (L11 unit lower).
 template <int KB>
 __global__ void __launch_bounds__(128) k_lu_trsm_row(double *A, long long sA, int lda, int ncols, int k0, int kb)
@@ -420,8 +523,19 @@ static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b)
 
 void stab_set_limits(int Npad)
 {
-    size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
-    if (sh > 48 * 1024) cudaFuncSetAttribute(k_sort_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    // attributes only grow, so that a smaller context never lowers a larger one's limit
+    static size_t sort_max = 48 * 1024;
+    const size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
+    if (sh > sort_max) {
+        cudaFuncSetAttribute(k_sort_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        sort_max = sh;
+    }
+    static bool lu_set = false;
+    if (!lu_set) {
+        cudaFuncSetAttribute(k_lu_panel_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * 33 * LU_SMEM_MAX_ROWS));
+        lu_set = true;
+    }
 }
 
 void launch_init_udv(sldqmc_ctx *c, double *Ut, double *V, int B)
@@ -549,8 +663,12 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
     for (int k0 = 0; k0 < N; k0 += 32) {
         int kb = N - k0 < 32 ? N - k0 : 32;
         prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * (N - k0) * kb * kb);
-        k_lu_panel<<<B, 1024, 0, c->st>>>(A, sItem, lda, N, ncols, k0, kb, c->d_piv, c->d_logacc,
-                                          c->d_sgn + c->cap, c->d_flag);
+        if (N - k0 <= LU_SMEM_MAX_ROWS)
+            k_lu_panel_smem<<<B, 1024, sizeof(double) * 33 * (N - k0), c->st>>>(
+                A, sItem, lda, N, ncols, k0, kb, c->d_piv, c->d_logacc, c->d_sgn + c->cap, c->d_flag);
+        else
+            k_lu_panel<<<B, 1024, 0, c->st>>>(A, sItem, lda, N, ncols, k0, kb, c->d_piv, c->d_logacc,
+                                              c->d_sgn + c->cap, c->d_flag);
         prof_end(c);
         c->launches++;
         int rest = ncols - (k0 + kb);
