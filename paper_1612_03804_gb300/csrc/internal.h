@@ -70,12 +70,15 @@ void tc_update_V(sldqmc_ctx *c, const double *R, double *V, int B);
 int oz_prepare(sldqmc_ctx *c);
 void oz_release(sldqmc_ctx *c);
 void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long sW, int ldw, int B);
-// Trailing updates of the stacked Cholesky-QR after a panel of kb <= 32
-// columns, FP64-accurate on the tensor cores: with A[r][l] = Asrc[l*N + r]
-// (r < M) and B[n][l] = Bsrc[l*N + n] (n < N), Yt -= A B^T and Wt -= A A^T
-// (tiles on or above the diagonal); row strides N, item strides N*N (sW for Wt).
-void oz_trailing(sldqmc_ctx *c, const double *Asrc, int M, const double *Bsrc, int kb, double *Yt, double *Wt,
-                 long long sW, int B);
+// Left-looking Cholesky-QR on the tensor cores (mixed modes, same N range):
+// oz_chol_begin fixes the digit exponents of R's columns from diag(W);
+// oz_chol_update subtracts the finished rows' contributions from the panel's
+// rows k0..k0+kb of W and of Y = Q^T (k0 > 0); oz_chol_slice splits the
+// panel's finished rows of R and Q^T for the later panels.  W row stride N,
+// item stride sW; R, Y row stride N, item stride N*N.
+void oz_chol_begin(sldqmc_ctx *c, const double *W, long long sW, int B);
+void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, double *Y, int B);
+void oz_chol_slice(sldqmc_ctx *c, int k0, int kb, const double *R, const double *Y, int B);
 
 // Event-bracketed timing of launches (sldqmc_profile_*).
 struct ProfRec {

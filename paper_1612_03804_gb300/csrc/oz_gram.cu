@@ -146,42 +146,41 @@ __global__ void __launch_bounds__(128) k_oz_slice(const double *X, long long sX,
     }
 }
 
-// Digits of a 32-wide K-block read column-wise: output row r (0 <= r < R) has
-// the kb values src[k * ld + r], k < kb (zero for kb <= k < 32).  Planes are
-// [plane][item][row][32]; E[b * sE + r].  One CTA converts 32 rows: the
-// 32 x 32 block is read coalesced along r, and eight threads share a row.
-__global__ void __launch_bounds__(256) k_oz_slice_cols(const double *src, long long sS, long long ld, int R, int kb,
-                                                       long long plane_stride, int rows_cap, __nv_bfloat16 *planes,
-                                                       int *E, long long sE)
+// Digits of a block of kb <= 32 rows of a row-major matrix (row stride ld),
+// stored as K-block koff/32 of the planes: plane row j (j0 <= j < Nc) gets the
+// values src[l * ld + j], l < kb, at K positions koff + l (0 for l >= kb).
+// The exponents are given (Ej[b * sE + j]; sE = 0 for one shared row of
+// exponents), chosen by the caller as bounds known before the values exist;
+// a value at or above its bound raises the numerical flag.  One CTA converts
+// 32 plane rows; eight threads share a row.
+__global__ void __launch_bounds__(256) k_oz_slice_fixed(const double *src, long long sS, long long ld, int j0, int Nc,
+                                                        int kb, int koff, long long plane_stride, int rows_cap,
+                                                        int ldk, __nv_bfloat16 *planes, const int *Ej, long long sE,
+                                                        int *flag)
 {
     __shared__ double tile[32][33];
-    const int b = blockIdx.y, r0 = blockIdx.x * 32;
+    const int b = blockIdx.y, c0 = j0 + blockIdx.x * 32;
     const double *s = src + (long long)b * sS;
     for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-        const int k = idx >> 5, r = idx & 31;
-        tile[k][r] = (k < kb && r0 + r < R) ? s[(long long)k * ld + r0 + r] : 0.0;
+        const int l = idx >> 5, r = idx & 31;
+        tile[l][r] = (l < kb && c0 + r < Nc) ? s[(long long)l * ld + c0 + r] : 0.0;
     }
     __syncthreads();
-    const int r = threadIdx.x >> 3, q = threadIdx.x & 7;  // row, quarter of its 32 values
-    unsigned long long mx = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const unsigned long long u = (unsigned long long)__double_as_longlong(tile[4 * q + j][r]) & 0x7FFFFFFFFFFFFFFFull;
-        mx = u > mx ? u : mx;
-    }
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o, 8);
-        mx = v > mx ? v : mx;
-    }
-    if (r0 + r >= R) return;
-    const int ef_max = (int)(mx >> 52);
-    const int Er = ef_max > 0 ? ef_max - 1022 : 0;
-    if (q == 0) E[(long long)b * sE + r0 + r] = Er;
+    const int r = threadIdx.x >> 3, q = threadIdx.x & 7;
+    const int j = c0 + r;
+    if (j >= Nc) return;
+    const int E = Ej[(long long)b * sE + j];
+    const unsigned long long bound = (unsigned long long)(E + 1023) << 52;  // bit pattern of 2^E
     int dg[4][OZ_S];
+    bool over = false;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) oz_digits(tile[4 * q + j][r], Er, ef_max, dg[j]);
-    const long long row = ((long long)b * rows_cap + r0 + r) * 32 + 4 * q;
+    for (int jj = 0; jj < 4; ++jj) {
+        const double x = tile[4 * q + jj][r];
+        over |= ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) >= bound;
+        oz_digits(x, E, 1, dg[jj]);
+    }
+    if (over) atomicOr(flag, FLAG_NUMERICAL);
+    const long long row = ((long long)b * rows_cap + j) * ldk + koff + 4 * q;
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p) {
         __nv_bfloat162 h2[2] = {__floats2bfloat162_rn((float)dg[0][p], (float)dg[1][p]),
@@ -190,8 +189,24 @@ __global__ void __launch_bounds__(256) k_oz_slice_cols(const double *src, long l
     }
 }
 
+// Bounds for the entries of R's columns in a Cholesky factorisation of the
+// Gram matrix W: sum_l R_lj^2 = W_jj, so |R_lj| <= sqrt(W_jj) < 2^E_j with
+// E_j = ceil(e/2) + 1, W_jj < 2^e (one bit of margin for rounding).
+__global__ void k_oz_col_exponents(const double *W, long long sW, int ldw, int N, int *E)
+{
+    const int b = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        const unsigned long long u =
+            (unsigned long long)__double_as_longlong(W[(long long)b * sW + (long long)j * ldw + j]) & 0x7FFFFFFFFFFFFFFFull;
+        const int ef = (int)(u >> 52);
+        const int e = ef > 0 ? ef - 1022 : -1022;
+        E[(long long)b * N + j] = ((e + 1) >> 1) + 1;
+    }
+}
+
 struct OzArgs {
     int M, Nn;              // rows of A (rows of C) and rows of B (columns of C)
+    int arow0, brow0;       // first plane rows of A and B (tensor-map row coordinates)
     int batch, nk;          // items, 32-wide K-blocks
     const int *EA, *EB;     // row exponents of A and B
     long long sEA, sEB;     // their item strides
@@ -234,8 +249,9 @@ __host__ __device__ inline int oz_per_item(int tiles_m, int tiles_n)
 }
 
 // UPPER: only the tiles on or above the diagonal (C square, A and B the same
-// rows); SUB: C -= A B^T, otherwise C = A B^T.
-template <bool UPPER, bool SUB>
+// rows); SUB: C -= A B^T, otherwise C = A B^T; TRANS: element (m, n) of the
+// product lives at C[n * ldc + m] (a warp's 32 rows m are then contiguous).
+template <bool UPPER, bool SUB, bool TRANS = false>
 __global__ void __launch_bounds__(OTHREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzArgs a)
 {
@@ -289,8 +305,8 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                     const int k0 = kb * OKE;
 #pragma unroll
                     for (int p = 0; p < OZ_S; ++p) {
-                        tma_load_4d(st + p * OTILE_A, &tA, k0, m0, b, p, &full[s]);
-                        tma_load_4d(st + OZ_S * OTILE_A + p * OTILE_B, &tB, k0, n0, b, p, &full[s]);
+                        tma_load_4d(st + p * OTILE_A, &tA, k0, a.arow0 + m0, b, p, &full[s]);
+                        tma_load_4d(st + OZ_S * OTILE_A + p * OTILE_B, &tB, k0, a.brow0 + n0, b, p, &full[s]);
                     }
                 }
             }
@@ -344,12 +360,14 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             const int Ei = mm < a.M ? a.EA[(long long)b * a.sEA + mm] : 0;
             // for an update, the old values of this thread's row segment, fetched
             // while the MMAs run
-            double *o = a.C + (long long)b * a.sC + (long long)mm * a.ldc;
+            // element (mm, n) at o[n * cs]
+            double *o = a.C + (long long)b * a.sC + (TRANS ? (long long)mm : (long long)mm * a.ldc);
+            const long long cs = TRANS ? a.ldc : 1;
             const int nb = n0 + hc;
             const int *eb = a.EB + (long long)b * a.sEB;
             double cold[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) cold[j] = (SUB && mm < a.M && nb + j < a.Nn) ? o[nb + j] : 0.0;
+            for (int j = 0; j < 16; ++j) cold[j] = (SUB && mm < a.M && nb + j < a.Nn) ? o[(nb + j) * cs] : 0.0;
             const bool ok = mbar_wait(&tmem_full[u], (ti >> 1) & 1, a.flag);
             fence_after();
             // group sums as exact integers, folded as they arrive: groups 0..3
@@ -387,7 +405,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                     const int e = Ei + eb[n] - 35;
                     const double v = (e > -1000 && e < 1000) ? w[j] * __longlong_as_double((long long)(e + 1023) << 52)
                                                              : scalbn(w[j], e);
-                    o[n] = SUB ? cold[j] - v : v;
+                    o[n * cs] = SUB ? cold[j] - v : v;
                 }
             }
         }
@@ -402,15 +420,15 @@ __global__ void __launch_bounds__(OTHREADS, 1)
 struct OzWs {
     int ldp;
     long long plane_stride;
-    __nv_bfloat16 *planes;  // digit planes of the Gram operand
+    __nv_bfloat16 *planes;  // digit planes of the Gram operand; in the Cholesky-QR, of Q's finished rows
     int *E;
     CUtensorMap mapA, mapB;
-    // 32-wide K-blocks of the Cholesky-QR trailing updates: A = R_blk^T
-    // (rows of the trailing part), B = Q^T_blk^T (N rows)
-    long long kplane_stride;
-    __nv_bfloat16 *kA, *kB;
-    int *EA, *EB;
-    CUtensorMap mapKA, mapKB, mapKA32;  // mapKA32: A planes in 32-row boxes (symmetric W update)
+    // Cholesky-QR: digit planes of R's finished rows, stored by column of R
+    // (plane row j holds R[l][j] at K position l), with fixed exponents ER
+    // (bounds from the Gram diagonal) and EQ = 1 for Q's rows (|Q_lj| < 2)
+    __nv_bfloat16 *rplanes;
+    int *ER, *EQ;
+    CUtensorMap mapRA, mapRB;  // 128-row and 32-row boxes
     int num_sms;
 };
 
@@ -432,31 +450,37 @@ bool encode4(CUtensorMap *map, void *ptr, int ldp, int rows, int batch, int box_
 int oz_prepare(sldqmc_ctx *c)
 {
     c->oz_ws = nullptr;
-    if (c->N < OBM || c->N > OZ_KMAX) return SLDQMC_OK;  // FP64 Gram outside the exact range
+    if (c->N < OBM || c->N > OZ_KMAX) return SLDQMC_OK;  // FP64 path outside the exact range
     OzWs *w = new OzWs();
     const int N = c->N;
     w->ldp = (N + 63) / 64 * 64;
     w->plane_stride = (long long)c->cap * N * w->ldp;
-    w->kplane_stride = (long long)c->cap * N * OKE;
     const size_t pbytes = (size_t)OZ_S * w->plane_stride * sizeof(__nv_bfloat16);
-    const size_t kbytes = (size_t)OZ_S * w->kplane_stride * sizeof(__nv_bfloat16);
     const size_t ebytes = sizeof(int) * (size_t)c->cap * N;
     void *mem = nullptr;
-    if (cudaMalloc(&mem, pbytes + 2 * kbytes + 3 * ebytes) != cudaSuccess) {
+    if (cudaMalloc(&mem, 2 * pbytes + 2 * ebytes + sizeof(int) * N) != cudaSuccess) {
         cudaGetLastError();
         delete w;
         return SLDQMC_ERR_OOM;
     }
     w->planes = (__nv_bfloat16 *)mem;
-    w->kA = (__nv_bfloat16 *)((uint8_t *)mem + pbytes);
-    w->kB = (__nv_bfloat16 *)((uint8_t *)mem + pbytes + kbytes);
-    w->E = (int *)((uint8_t *)mem + pbytes + 2 * kbytes);
-    w->EA = w->E + (size_t)c->cap * N;
-    w->EB = w->EA + (size_t)c->cap * N;
-    cudaMemsetAsync(mem, 0, pbytes + 2 * kbytes + 3 * ebytes, c->st);  // zero pads: never written
+    w->rplanes = (__nv_bfloat16 *)((uint8_t *)mem + pbytes);
+    w->E = (int *)((uint8_t *)mem + 2 * pbytes);
+    w->ER = w->E + (size_t)c->cap * N;
+    w->EQ = w->ER + (size_t)c->cap * N;
+    cudaMemsetAsync(mem, 0, 2 * pbytes + 2 * ebytes, c->st);  // zero pads: never written
+    {
+        std::vector<int> ones((size_t)N, 1);
+        if (cudaMemcpyAsync(w->EQ, ones.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+            cudaStreamSynchronize(c->st) != cudaSuccess) {
+            cudaFree(mem);
+            delete w;
+            return SLDQMC_ERR_CUDA;
+        }
+    }
     if (!encode4(&w->mapA, w->planes, w->ldp, N, c->cap, OBM) || !encode4(&w->mapB, w->planes, w->ldp, N, c->cap, OBN) ||
-        !encode4(&w->mapKA, w->kA, OKE, N, c->cap, OBM) || !encode4(&w->mapKB, w->kB, OKE, N, c->cap, OBN) ||
-        !encode4(&w->mapKA32, w->kA, OKE, N, c->cap, OBN)) {
+        !encode4(&w->mapRA, w->rplanes, w->ldp, N, c->cap, OBM) ||
+        !encode4(&w->mapRB, w->rplanes, w->ldp, N, c->cap, OBN)) {
         cudaFree(mem);
         delete w;
         return SLDQMC_ERR_CUDA;
@@ -466,8 +490,8 @@ int oz_prepare(sldqmc_ctx *c)
     if (cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || w->num_sms < 1)
         w->num_sms = 148;
     cudaFuncSetAttribute(k_oz_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
-    cudaFuncSetAttribute(k_oz_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
-    cudaFuncSetAttribute(k_oz_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    cudaFuncSetAttribute(k_oz_gemm<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)oz_smem_bytes());
     c->oz_ws = w;
     return SLDQMC_OK;
 }
@@ -509,49 +533,79 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
     c->launches += 2;
 }
 
-// Trailing updates of the stacked Cholesky-QR after a panel of kb <= 32
-// columns: with A[r][l] = Asrc[l * N + r] (the panel's block row of R beyond
-// the panel, r < M) and B[n][l] = Bsrc[l * N + n] (the panel's rows of Q^T,
-// n < N),
-//   Yt -= A B^T   (all M x N),      Wt -= A A^T   (tiles on or above the diagonal),
-// Yt, Wt row stride N; item strides N*N for A, B, Yt and sW for Wt.
-void oz_trailing(sldqmc_ctx *c, const double *Asrc, int M, const double *Bsrc, int kb, double *Yt, double *Wt,
-                 long long sW, int B)
+// Left-looking Cholesky-QR of W = X X^T (row stride N, item stride sW) that
+// forms Q^T = R^-T X^T in Y (row stride N, item stride N*N): before the panel
+// of rows k0..k0+kb the products of all finished rows are subtracted from the
+// panel's rows,
+//   W[k0+r][k0+n] -= sum_{l<k0} R[l][k0+n] R[l][k0+r],
+//   Y[k0+r][n]    -= sum_{l<k0} Q^T[l][n] R[l][k0+r],
+// both FP64-accurate on the tensor cores (the product computed with rows n and
+// columns r, stored transposed so that a warp's stores are contiguous); after
+// the panel its rows of R and Q^T are split into K-block k0/32 of the digit
+// planes.  oz_chol_begin fixes the exponents of R's columns from W's diagonal.
+void oz_chol_begin(sldqmc_ctx *c, const double *W, long long sW, int B)
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
-    k_oz_slice_cols<<<dim3((M + 31) / 32, B), 256, 0, c->st>>>(Asrc, c->nn, N, M, kb, w->kplane_stride, N, w->kA,
-                                                              w->EA, N);
-    k_oz_slice_cols<<<dim3((N + 31) / 32, B), 256, 0, c->st>>>(Bsrc, c->nn, N, N, kb, w->kplane_stride, N, w->kB,
-                                                              w->EB, N);
+    k_oz_col_exponents<<<dim3((N + 255) / 256, B), 256, 0, c->st>>>(W, sW, N, N, w->ER);
+    c->launches++;
+}
+
+void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, double *Y, int B)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    const int N = c->N;
     OzArgs a{};
-    a.M = M;
-    a.Nn = N;
     a.batch = B;
-    a.nk = 1;
-    a.EA = w->EA;
-    a.EB = w->EB;
-    a.sEA = N;
+    a.nk = k0 / OKE;
+    a.flag = c->d_flag;
+    a.brow0 = k0;
+    a.EB = w->ER + k0;
     a.sEB = N;
-    a.C = Yt;
+    a.Nn = kb;
+    // Y rows k0.. : product rows n = columns of Q^T (all N)
+    a.M = N;
+    a.arow0 = 0;
+    a.EA = w->EQ;
+    a.sEA = 0;
+    a.C = Y + (long long)k0 * N;
     a.sC = c->nn;
     a.ldc = N;
-    a.flag = c->d_flag;
-    int tiles = oz_per_item<false>((M + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
+    int tiles = oz_per_item<false>((N + OBM - 1) / OBM, 1) * B;
     int grid = tiles < w->num_sms ? tiles : w->num_sms;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * M * N * kb * B);
-    k_oz_gemm<false, true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapKA, w->mapKB, a);
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * N * kb * k0 * B);
+    k_oz_gemm<false, true, true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRB, a);
     prof_end(c);
-    a.Nn = M;
-    a.EB = w->EA;
-    a.C = Wt;
+    // W rows k0.. : product rows n = columns k0.. of R
+    const int M = N - k0;
+    a.M = M;
+    a.arow0 = k0;
+    a.EA = w->ER + k0;
+    a.sEA = N;
+    a.C = W + (long long)k0 * N + k0;
     a.sC = sW;
-    tiles = oz_per_item<true>((M + OBM - 1) / OBM, (M + OBN - 1) / OBN) * B;
+    tiles = oz_per_item<false>((M + OBM - 1) / OBM, 1) * B;
     grid = tiles < w->num_sms ? tiles : w->num_sms;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)M * (M + 1) * kb * B);
-    k_oz_gemm<true, true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapKA, w->mapKA32, a);
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * M * kb * k0 * B);
+    k_oz_gemm<false, true, true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapRA, w->mapRB, a);
     prof_end(c);
-    c->launches += 4;
+    c->launches += 2;
+}
+
+void oz_chol_slice(sldqmc_ctx *c, int k0, int kb, const double *R, const double *Y, int B)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    const int N = c->N;
+    // R's rows k0..k0+kb, columns k0+kb.. (the ones later panels read)
+    const int j0 = k0 + kb;
+    k_oz_slice_fixed<<<dim3((N - j0 + 31) / 32, B), 256, 0, c->st>>>(R + (long long)k0 * N, c->nn, N, j0, N, kb, k0,
+                                                                    w->plane_stride, N, w->ldp, w->rplanes, w->ER, N,
+                                                                    c->d_flag);
+    // Q^T's rows k0..k0+kb, all columns
+    k_oz_slice_fixed<<<dim3((N + 31) / 32, B), 256, 0, c->st>>>(Y + (long long)k0 * N, c->nn, N, 0, N, kb, k0,
+                                                               w->plane_stride, N, w->ldp, w->planes, w->EQ, 0,
+                                                               c->d_flag);
+    c->launches += 2;
 }
 
 }  // namespace sldqmc

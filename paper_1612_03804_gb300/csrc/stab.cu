@@ -550,21 +550,26 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
     const int N = c->N;
     const long long nn = c->nn;
     cudaMemsetAsync(R, 0, sizeof(double) * nn * B, c->st);
+    // Tensor-core path (mixed modes): left-looking, the panel's rows of W and
+    // Y are brought up to date just before the panel (FP64-accurate digit
+    // splitting), and the panel's finished rows of R and Q^T are split for the
+    // later panels.  Otherwise right-looking with FP64 trailing updates.
+    const bool oz = c->oz_ws != nullptr;
+    if (oz) oz_chol_begin(c, W, sW, B);
     for (int k0 = 0; k0 < N; k0 += 32) {
         int kb = N - k0 < 32 ? N - k0 : 32;
         int nW = N - (k0 + kb);
+        if (oz && k0 > 0) oz_chol_update(c, k0, kb, W, sW, Y, B);
         dim3 grid(cdiv(nW + N, 128), B);
         // algorithmic flops: factor of the kb x kb block, triangular solves of nW + N columns
         prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * ((double)kb * kb * kb / 3.0 + (double)(nW + N) * kb * kb));
         k_chol_panel<32><<<grid, 128, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
         prof_end(c);
         c->launches++;
-        if (nW > 0 && c->oz_ws) {
-            // W[k0+kb:, k0+kb:] -= R_blk^T R_blk (upper) and Y[k0+kb:, :] -= R_blk^T Qt_blk,
-            // FP64-accurate on the tensor cores
-            oz_trailing(c, R + (long long)k0 * N + k0 + kb, nW, Y + (long long)k0 * N, kb,
-                        Y + (long long)(k0 + kb) * N, W + (long long)(k0 + kb) * N + k0 + kb, sW, B);
-        } else if (nW > 0) {
+        if (nW == 0) continue;
+        if (oz) {
+            oz_chol_slice(c, k0, kb, R, Y, B);
+        } else {
             // W[k0+kb:, k0+kb:] -= R_blk^T R_blk   (upper triangle only)
             GemmF64 g = gemm_desc(nW, nW, kb, R + (long long)k0 * N + k0 + kb, N, nn,
                                   R + (long long)k0 * N + k0 + kb, N, nn,
