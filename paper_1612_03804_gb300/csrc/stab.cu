@@ -117,7 +117,7 @@ __global__ void k_gather_pivot(const double *W, long long sW, const double *Xt, 
 // block W_kk = R_kk^T R_kk (in shared memory, every CTA redundantly), then
 // solve R_kk^T y = w for each column: W-columns right of the block give
 // R's block row, Y-columns give Q^T's block row (in place).
-template <int KB>
+template <int KB, int CPT>
 __global__ void __launch_bounds__(128) k_chol_panel(const double *W, long long sW, int ldw, double *Y,
                                                     long long sY, double *R, long long sR, int N,
                                                     int k0, int kb, int *flag)
@@ -169,35 +169,53 @@ __global__ void __launch_bounds__(128) k_chol_panel(const double *W, long long s
         }
     }
     const int nW = N - (k0 + kb);
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    const double *src;
-    double *dst;
-    long long lds, ldd;
-    int c;
-    if (col < nW) {
-        c = k0 + kb + col;
-        src = Wb; lds = ldw;
-        dst = R + (long long)b * sR; ldd = N;
-    } else if (col < nW + N) {
-        c = col - nW;
-        src = Y + (long long)b * sY; lds = N;
-        dst = Y + (long long)b * sY; ldd = N;
-    } else {
-        return;
-    }
-    double w[KB];
+    // CPT columns per thread (blockDim.x apart, so each load and store
+    // instruction stays coalesced); every shared-memory load of R_kk then feeds
+    // CPT independent FMA chains.
+    double w[CPT][KB];
+    double *dst[CPT];
+    int cc[CPT];
+    long long ldd[CPT];
 #pragma unroll
-    for (int r = 0; r < KB; ++r) w[r] = (r < kb) ? src[(long long)(k0 + r) * lds + c] : 0.0;
+    for (int q = 0; q < CPT; ++q) {
+        const int col = (blockIdx.x * CPT + q) * blockDim.x + threadIdx.x;
+        const double *src = nullptr;
+        long long lds = 0;
+        cc[q] = -1;
+        dst[q] = nullptr;
+        ldd[q] = 0;
+        if (col < nW) {
+            cc[q] = k0 + kb + col;
+            src = Wb; lds = ldw;
+            dst[q] = R + (long long)b * sR; ldd[q] = N;
+        } else if (col < nW + N) {
+            cc[q] = col - nW;
+            src = Y + (long long)b * sY; lds = N;
+            dst[q] = Y + (long long)b * sY; ldd[q] = N;
+        }
+#pragma unroll
+        for (int r = 0; r < KB; ++r) w[q][r] = (cc[q] >= 0 && r < kb) ? src[(long long)(k0 + r) * lds + cc[q]] : 0.0;
+    }
 #pragma unroll
     for (int r = 0; r < KB; ++r) {
-        double acc = w[r];
+        double acc[CPT];
 #pragma unroll
-        for (int l = 0; l < r; ++l) acc -= Rk[l][r] * w[l];
-        w[r] = acc * rinv[r];
+        for (int q = 0; q < CPT; ++q) acc[q] = w[q][r];
+#pragma unroll
+        for (int l = 0; l < r; ++l) {
+            const double rl = Rk[l][r];
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) acc[q] -= rl * w[q][l];
+        }
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) w[q][r] = acc[q] * rinv[r];
     }
 #pragma unroll
-    for (int r = 0; r < KB; ++r)
-        if (r < kb) dst[(long long)(k0 + r) * ldd + c] = w[r];
+    for (int q = 0; q < CPT; ++q)
+        if (cc[q] >= 0)
+#pragma unroll
+            for (int r = 0; r < KB; ++r)
+                if (r < kb) dst[q][(long long)(k0 + r) * ldd[q] + cc[q]] = w[q][r];
 }
 
 // D_new[k] = R_kk * D_p[k]  (R from Cholesky has a positive diagonal).
@@ -545,6 +563,8 @@ void launch_init_udv(sldqmc_ctx *c, double *Ut, double *V, int B)
     c->launches++;
 }
 
+constexpr int CHOL_CPT = 2;  // columns per thread of the panel solves
+
 static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double *R, int B)
 {
     const int N = c->N;
@@ -560,10 +580,10 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
         int kb = N - k0 < 32 ? N - k0 : 32;
         int nW = N - (k0 + kb);
         if (oz && k0 > 0) oz_chol_update(c, k0, kb, W, sW, Y, B);
-        dim3 grid(cdiv(nW + N, 128), B);
+        dim3 grid(cdiv(nW + N, 128 * CHOL_CPT), B);
         // algorithmic flops: factor of the kb x kb block, triangular solves of nW + N columns
         prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * ((double)kb * kb * kb / 3.0 + (double)(nW + N) * kb * kb));
-        k_chol_panel<32><<<grid, 128, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
+        k_chol_panel<32, CHOL_CPT><<<grid, 128, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
         prof_end(c);
         c->launches++;
         if (nW == 0) continue;
