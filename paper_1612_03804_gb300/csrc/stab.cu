@@ -196,19 +196,22 @@ __global__ void __launch_bounds__(128) k_chol_panel(const double *W, long long s
 #pragma unroll
         for (int r = 0; r < KB; ++r) w[q][r] = (cc[q] >= 0 && r < kb) ? src[(long long)(k0 + r) * lds + cc[q]] : 0.0;
     }
+    // Column-oriented order: once w[l] is final, its contribution is
+    // subtracted from every later w[r] -- up to KB - 1 independent FMAs per
+    // step.  Each w[r] receives the same operations in the same order as in
+    // the row-oriented form (r's terms l = 0, 1, ..., r - 1, then the scale).
 #pragma unroll
-    for (int r = 0; r < KB; ++r) {
-        double acc[CPT];
+    for (int l = 0; l < KB; ++l) {
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) acc[q] = w[q][r];
+        for (int q = 0; q < CPT; ++q) w[q][l] *= rinv[l];
 #pragma unroll
-        for (int l = 0; l < r; ++l) {
-            const double rl = Rk[l][r];
+        for (int r = 0; r < KB; ++r) {
+            if (r > l) {
+                const double rl = Rk[l][r];
 #pragma unroll
-            for (int q = 0; q < CPT; ++q) acc[q] -= rl * w[q][l];
+                for (int q = 0; q < CPT; ++q) w[q][r] -= rl * w[q][l];
+            }
         }
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) w[q][r] = acc[q] * rinv[r];
     }
 #pragma unroll
     for (int q = 0; q < CPT; ++q)
@@ -563,7 +566,8 @@ void launch_init_udv(sldqmc_ctx *c, double *Ut, double *V, int B)
     c->launches++;
 }
 
-constexpr int CHOL_CPT = 2;  // columns per thread of the panel solves
+constexpr int CHOL_CPT = 2;      // columns per thread of the panel solves
+constexpr int CHOL_THREADS = 128; // threads per CTA of the panel kernel
 
 static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double *R, int B)
 {
@@ -580,10 +584,10 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
         int kb = N - k0 < 32 ? N - k0 : 32;
         int nW = N - (k0 + kb);
         if (oz && k0 > 0) oz_chol_update(c, k0, kb, W, sW, Y, B);
-        dim3 grid(cdiv(nW + N, 128 * CHOL_CPT), B);
+        dim3 grid(cdiv(nW + N, CHOL_THREADS * CHOL_CPT), B);
         // algorithmic flops: factor of the kb x kb block, triangular solves of nW + N columns
         prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * ((double)kb * kb * kb / 3.0 + (double)(nW + N) * kb * kb));
-        k_chol_panel<32, CHOL_CPT><<<grid, 128, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
+        k_chol_panel<32, CHOL_CPT><<<grid, CHOL_THREADS, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
         prof_end(c);
         c->launches++;
         if (nW == 0) continue;
