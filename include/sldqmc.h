@@ -263,8 +263,8 @@ int sldqmc_weight_noalloc(const sldqmc_params *p, void *stream, const int8_t *d_
  * N x N FP64 matrices (item stride N*N), d_W receives B row-major N x N FP64
  * matrices of which every element on or above the diagonal is written (the
  * rest is unspecified).  Computed exactly as the context's stabilisation does:
- * in the mixed-precision modes with 128 <= N <= 384 on the BF16 tensor cores
- * by error-free digit splitting (FP64 accuracy: error below ~2^-52 of
+ * in the mixed-precision modes with N >= 128 on the BF16 tensor cores by
+ * error-free digit splitting (FP64 accuracy: error below ~2^-52 of
  * sqrt(W_ii W_jj)), otherwise by the FP64 GEMM.  1 <= B <= max_batch.
  * Stream-ordered on the context's stream; caller-owned device buffers. */
 int sldqmc_gram_batch_dev(sldqmc_ctx *ctx, const double *d_X, int B, double *d_W);

@@ -63,7 +63,7 @@ GemmF64 gemm_desc(int M, int N, int K, const double *A, long long lda, long long
 // triangular, D = c->d_D, D_p = c->d_Dp, P = c->d_perm; row stride N, batch
 // stride nn; result in FP64).  Defined in tc_gemm.cu.
 void tc_update_V(sldqmc_ctx *c, const double *R, double *V, int B);
-// Mixed-precision modes, 128 <= N <= 384: W = X X^T to FP64 accuracy on the
+// Mixed-precision modes, N >= 128: W = X X^T to FP64 accuracy on the
 // BF16 tensor cores (Ozaki splitting; X row stride N, batch stride sX; W row
 // stride ldw, batch stride sW; tiles on or above the diagonal written).
 // oz_prepare leaves c->oz_ws null outside that range.  Defined in oz_gram.cu.
@@ -121,7 +121,7 @@ struct sldqmc_ctx {
     double *d_D, *d_Dp, *d_logacc;
     int *d_perm, *d_sgn, *d_piv;
     void *tc_ws;       // tensor-core operand workspace (split copies)
-    void *oz_ws;       // digit planes of the tensor-core Gram (mixed modes, 128 <= N <= 384)
+    void *oz_ws;       // digit planes of the tensor-core Gram and Cholesky-QR (mixed modes, N >= 128)
     // Monte Carlo state
     int8_t *d_s_tmp;   // cap * M * N proposal buffer
     int8_t *d_s_one;   // staging for host calls

@@ -13,9 +13,10 @@
 // sum.  The digit planes are BF16 integers; the products of one group
 // g = p + q share one FP32 tensor-memory accumulator, and every partial sum
 // of a group is an integer of magnitude < K (2 * 8192 + 6 * 4096) < 2^24 for
-// K <= 384, so the tensor-core accumulation is exact.  The epilogue converts
-// the eight group sums to integers, combines them in two 64-bit integers and
-// forms the FP64 result with one rounding.
+// K <= 384, so the tensor-core accumulation is exact.  Longer contractions
+// run in chunks of at most 384: the epilogue converts each chunk's eight
+// group sums to integers, combines them in two 64-bit integers, forms the
+// chunk's FP64 value with one rounding and adds the chunks in FP64.
 //
 // One persistent CTA per SM walks the 128 x 32 tiles on or above the
 // diagonal of every item: warp 0 streams the 8 + 8 digit-plane tiles of a
@@ -40,7 +41,7 @@ using namespace tcx;
 constexpr int OZ_S = 8;           // digit planes
 constexpr int OZ_BETA = 7;        // bits per digit
 constexpr int OZ_G = 8;           // groups p + q = 2..9
-constexpr int OZ_KMAX = 384;      // largest K with exact group sums
+constexpr int OZ_KCHUNK = 12;     // K-blocks (of 32) per exactly accumulated chunk: K <= 384
 constexpr int OBM = 128, OBN = 32;
 constexpr int OKE = 32;           // BF16 elements per K-block (64-byte rows)
 constexpr int OSTAGES = 2;
@@ -313,54 +314,56 @@ __global__ void __launch_bounds__(OTHREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int it = 0, ti = 0;
+            int it = 0, cc = 0;  // K-block and chunk counters of this CTA
             bool ok = true;
-            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++ti) {
-                const int u = ti & 1;
-                // the epilogue must have drained this buffer (used two tiles ago)
-                if (ti >= 2 && !mbar_wait(&tmem_free[u], ((ti >> 1) - 1) & 1, a.flag)) { ok = false; break; }
-                fence_after();
-                const uint32_t acc0 = tmem + (uint32_t)(u * OZ_G * OBN);
-                uint32_t started = 0;
-                for (int kb = 0; kb < a.nk; ++kb, ++it) {
-                    const int s = it % OSTAGES;
-                    if (!mbar_wait(&full[s], (it / OSTAGES) & 1, a.flag)) { ok = false; break; }
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                for (int kc0 = 0; kc0 < a.nk && ok; kc0 += OZ_KCHUNK, ++cc) {
+                    const int u = cc & 1;
+                    // the epilogue must have drained this buffer (used two chunks ago)
+                    if (cc >= 2 && !mbar_wait(&tmem_free[u], ((cc >> 1) - 1) & 1, a.flag)) { ok = false; break; }
                     fence_after();
-                    const uint32_t sa = smem_u32(base + s * OSTAGE);
-                    const uint32_t sb = sa + OZ_S * OTILE_A;
+                    const uint32_t acc0 = tmem + (uint32_t)(u * OZ_G * OBN);
+                    uint32_t started = 0;
+                    const int kc1 = kc0 + OZ_KCHUNK < a.nk ? kc0 + OZ_KCHUNK : a.nk;
+                    for (int kb = kc0; kb < kc1; ++kb, ++it) {
+                        const int s = it % OSTAGES;
+                        if (!mbar_wait(&full[s], (it / OSTAGES) & 1, a.flag)) { ok = false; break; }
+                        fence_after();
+                        const uint32_t sa = smem_u32(base + s * OSTAGE);
+                        const uint32_t sb = sa + OZ_S * OTILE_A;
 #pragma unroll
-                    for (int k = 0; k < OKE / 16; ++k) {
+                        for (int k = 0; k < OKE / 16; ++k) {
 #pragma unroll
-                        for (int p = 0; p < OZ_S; ++p) {
-                            const uint64_t da = smem_desc64(sa + p * OTILE_A + k * 32);
+                            for (int p = 0; p < OZ_S; ++p) {
+                                const uint64_t da = smem_desc64(sa + p * OTILE_A + k * 32);
 #pragma unroll
-                            for (int q = 0; q < OZ_S - p; ++q) {
-                                const int g = p + q;
-                                mma_bf16(acc0 + (uint32_t)(g * OBN), da, smem_desc64(sb + q * OTILE_B + k * 32),
-                                         (started >> g) & 1u);
-                                started |= 1u << g;
+                                for (int q = 0; q < OZ_S - p; ++q) {
+                                    const int g = p + q;
+                                    mma_bf16(acc0 + (uint32_t)(g * OBN), da, smem_desc64(sb + q * OTILE_B + k * 32),
+                                             (started >> g) & 1u);
+                                    started |= 1u << g;
+                                }
                             }
                         }
+                        mma_commit(&empty[s]);
                     }
-                    mma_commit(&empty[s]);
+                    if (ok) mma_commit(&tmem_full[u]);
                 }
-                if (ok) mma_commit(&tmem_full[u]);
             }
         }
     } else {
         // epilogue: warp w drains lane quarter w % 4, columns [hc, hc + 16)
         const int q4 = warp & 3;
         const int hc = ((warp - 2) >> 2) * 16;
-        int ti = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
+        int cc = 0;  // chunk counter, in step with the MMA thread's
+        bool ok = true;
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
             int b, m0, n0;
             oz_tile<UPPER>(t, tiles_m, tiles_n, per_item, b, m0, n0);
-            const int u = ti & 1;
             const int mm = m0 + q4 * 32 + lane;
             const int Ei = mm < a.M ? a.EA[(long long)b * a.sEA + mm] : 0;
-            // for an update, the old values of this thread's row segment, fetched
-            // while the MMAs run
-            // element (mm, n) at o[n * cs]
+            // element (mm, n) at o[n * cs]; for an update, the old values of this
+            // thread's row segment, fetched while the MMAs run
             double *o = a.C + (long long)b * a.sC + (TRANS ? (long long)mm : (long long)mm * a.ldc);
             const long long cs = TRANS ? a.ldc : 1;
             const int nb = n0 + hc;
@@ -368,36 +371,46 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             double cold[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) cold[j] = (SUB && mm < a.M && nb + j < a.Nn) ? o[(nb + j) * cs] : 0.0;
-            const bool ok = mbar_wait(&tmem_full[u], (ti >> 1) & 1, a.flag);
-            fence_after();
-            // group sums as exact integers, folded as they arrive: groups 0..3
-            // (p + q = 2..5) into h, 4..7 (6..9) into l, so that
-            // sum_g acc_g 2^-7(g+2) = h 2^-35 + l 2^-63
-            long long h[16], l[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) h[j] = l[j] = 0;
-            const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(u * OZ_G * OBN + hc);
-#pragma unroll
-            for (int gg = 0; gg < OZ_G; gg += 2) {
-                uint32_t r0[16], r1[16];
-                tmem_ld16_nowait(lane_base + (uint32_t)(gg * OBN), r0);
-                tmem_ld16_nowait(lane_base + (uint32_t)((gg + 1) * OBN), r1);
-                tmem_wait_ld32(r0, r1);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const long long v0 = (long long)__float2int_rn(__uint_as_float(r0[j]));
-                    const long long v1 = (long long)__float2int_rn(__uint_as_float(r1[j]));
-                    if (gg < 4) h[j] += (v0 << (OZ_BETA * (3 - gg))) + (v1 << (OZ_BETA * (2 - gg)));
-                    else l[j] += (v0 << (OZ_BETA * (7 - gg))) + (v1 << (OZ_BETA * (6 - gg)));
-                }
-            }
-            fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tmem_free[u])) : "memory");
-            if (!ok) break;
-            if (mm >= a.M) continue;
+            // sum over K-chunks of the exactly accumulated chunk products
             double w[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) w[j] = fma((double)l[j], 0x1p-28, (double)h[j]);
+            for (int j = 0; j < 16; ++j) w[j] = 0.0;
+            for (int kc0 = 0; kc0 < a.nk; kc0 += OZ_KCHUNK, ++cc) {
+                const int u = cc & 1;
+                ok = mbar_wait(&tmem_full[u], (cc >> 1) & 1, a.flag);
+                fence_after();
+                const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(u * OZ_G * OBN + hc);
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    // group sums as exact integers, folded as they arrive: groups 0..3
+                    // (p + q = 2..5) into h, 4..7 (6..9) into l, so that
+                    // sum_g acc_g 2^-7(g+2) = h 2^-35 + l 2^-63
+                    long long h[8], l[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = l[j] = 0;
+#pragma unroll
+                    for (int gg = 0; gg < OZ_G; gg += 2) {
+                        uint32_t r0[8], r1[8];
+                        tmem_ld8_nowait(lane_base + (uint32_t)(gg * OBN + half * 8), r0);
+                        tmem_ld8_nowait(lane_base + (uint32_t)((gg + 1) * OBN + half * 8), r1);
+                        tmem_wait_ld8x2(r0, r1);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const long long v0 = (long long)__float2int_rn(__uint_as_float(r0[j]));
+                            const long long v1 = (long long)__float2int_rn(__uint_as_float(r1[j]));
+                            if (gg < 4) h[j] += (v0 << (OZ_BETA * (3 - gg))) + (v1 << (OZ_BETA * (2 - gg)));
+                            else l[j] += (v0 << (OZ_BETA * (7 - gg))) + (v1 << (OZ_BETA * (6 - gg)));
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) w[half * 8 + j] += fma((double)l[j], 0x1p-28, (double)h[j]);
+                }
+                fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tmem_free[u])) : "memory");
+                if (!ok) break;
+            }
+            if (!ok) break;
+            if (mm >= a.M) continue;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int n = nb + j;
@@ -450,7 +463,7 @@ bool encode4(CUtensorMap *map, void *ptr, int ldp, int rows, int batch, int box_
 int oz_prepare(sldqmc_ctx *c)
 {
     c->oz_ws = nullptr;
-    if (c->N < OBM || c->N > OZ_KMAX) return SLDQMC_OK;  // FP64 path outside the exact range
+    if (c->N < OBM) return SLDQMC_OK;  // tiles are 128 rows
     OzWs *w = new OzWs();
     const int N = c->N;
     w->ldp = (N + 63) / 64 * 64;

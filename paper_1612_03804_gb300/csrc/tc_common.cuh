@@ -117,6 +117,17 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t r[8])
                  : "r"(taddr));
 }
 
+// Waits for outstanding tcgen05.ld and makes two 8-register loads outputs of
+// the wait.
+__device__ __forceinline__ void tmem_wait_ld8x2(uint32_t a[8], uint32_t b[8])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                   "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7])
+                 :
+                 : "memory");
+}
+
 // Waits for outstanding tcgen05.ld and makes the 16 loaded registers outputs
 // of the wait.
 __device__ __forceinline__ void tmem_wait_ld16(uint32_t a[16])
