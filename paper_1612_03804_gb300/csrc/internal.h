@@ -79,6 +79,14 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
 void oz_chol_begin(sldqmc_ctx *c, const double *W, long long sW, int B);
 void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, double *Y, int B);
 void oz_chol_slice(sldqmc_ctx *c, int k0, int kb, const double *R, const double *Y, int B);
+// R = R2 R1 of the two passes on the tensor cores (tiles on or above the
+// diagonal written); oz_keep_bounds saves the first pass's column bounds of R
+// before the second pass replaces them.
+void oz_keep_bounds(sldqmc_ctx *c, int B);
+// V <- (D^-1 R D_p) P^T V, FP64-accurate on the tensor cores (R upper
+// triangular; D, D_p, P from the context; Ts an N x N FP64 scratch per item).
+void oz_update_V(sldqmc_ctx *c, const double *R, double *V, double *Ts, int B);
+void oz_r2r1(sldqmc_ctx *c, const double *R2, const double *R1, double *R, int B);
 
 // Event-bracketed timing of launches (sldqmc_profile_*).
 struct ProfRec {

@@ -147,24 +147,33 @@ __global__ void __launch_bounds__(128) k_oz_slice(const double *X, long long sX,
     }
 }
 
-// Digits of a block of kb <= 32 rows of a row-major matrix (row stride ld),
-// stored as K-block koff/32 of the planes: plane row j (j0 <= j < Nc) gets the
-// values src[l * ld + j], l < kb, at K positions koff + l (0 for l >= kb).
+// Digits of krows rows of a row-major matrix (row stride ld), in blocks of 32
+// rows (blockIdx.z), stored from K-block koff/32 of the planes on: plane row
+// j (j0 <= j < Nc) gets src[l * ld + j] at K position koff + l (0 beyond
+// krows within the last block).
 // The exponents are given (Ej[b * sE + j]; sE = 0 for one shared row of
 // exponents), chosen by the caller as bounds known before the values exist;
 // a value at or above its bound raises the numerical flag.  One CTA converts
 // 32 plane rows; eight threads share a row.
 __global__ void __launch_bounds__(256) k_oz_slice_fixed(const double *src, long long sS, long long ld, int j0, int Nc,
-                                                        int kb, int koff, long long plane_stride, int rows_cap,
+                                                        int krows, int koff, long long plane_stride, int rows_cap,
                                                         int ldk, __nv_bfloat16 *planes, const int *Ej, long long sE,
-                                                        int *flag)
+                                                        int *flag, const int *rowidx = nullptr, long long sR = 0)
 {
     __shared__ double tile[32][33];
     const int b = blockIdx.y, c0 = j0 + blockIdx.x * 32;
+    // blockIdx.z: the 32-row block of the krows source rows (K positions koff + 32 z ..);
+    // source row l is rowidx[b * sR + l] when a row index is given
+    const int kz = 32 * blockIdx.z;
+    const int kb = krows - kz < 32 ? krows - kz : 32;
+    koff += kz;
     const double *s = src + (long long)b * sS;
+    const int *ri = rowidx ? rowidx + (long long)b * sR + kz : nullptr;
     for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
         const int l = idx >> 5, r = idx & 31;
-        tile[l][r] = (l < kb && c0 + r < Nc) ? s[(long long)l * ld + c0 + r] : 0.0;
+        double v = 0.0;
+        if (l < kb && c0 + r < Nc) v = s[(long long)(ri ? ri[l] : kz + l) * ld + c0 + r];
+        tile[l][r] = v;
     }
     __syncthreads();
     const int r = threadIdx.x >> 3, q = threadIdx.x & 7;
@@ -203,6 +212,34 @@ __global__ void k_oz_col_exponents(const double *W, long long sW, int ldw, int N
         const int e = ef > 0 ? ef - 1022 : -1022;
         E[(long long)b * N + j] = ((e + 1) >> 1) + 1;
     }
+}
+
+// E[b][j] = frexp exponent of max_r |src[r][j]| (|src[r][j]| < 2^E; 0 for a
+// zero column): one thread per column, rows read coalesced across threads.
+__global__ void k_oz_col_max_exponents(const double *src, long long sS, int rows, int cols, int *E)
+{
+    const int b = blockIdx.y;
+    const double *s = src + (long long)b * sS;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cols; j += gridDim.x * blockDim.x) {
+        unsigned long long mx = 0;
+        for (int r = 0; r < rows; ++r) {
+            const unsigned long long u = (unsigned long long)__double_as_longlong(s[(long long)r * cols + j]) & 0x7FFFFFFFFFFFFFFFull;
+            mx = u > mx ? u : mx;
+        }
+        const int ef = (int)(mx >> 52);
+        E[(long long)b * cols + j] = ef > 0 ? ef - 1022 : 0;
+    }
+}
+
+// T[m][k] = R[m][k] Dp[k] / D[m] for k >= m, 0 below (FP64), the triangular
+// factor of the V update V <- T P^T V.
+__global__ void k_oz_make_T(const double *R, long long nn, int N, const double *D, const double *Dp, double *T)
+{
+    const int b = blockIdx.z, m = blockIdx.y;
+    const double rd = 1.0 / D[(long long)b * N + m];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x)
+        T[(long long)b * nn + (long long)m * N + k] =
+            k >= m ? R[(long long)b * nn + (long long)m * N + k] * Dp[(long long)b * N + k] * rd : 0.0;
 }
 
 struct OzArgs {
@@ -441,6 +478,7 @@ struct OzWs {
     // (bounds from the Gram diagonal) and EQ = 1 for Q's rows (|Q_lj| < 2)
     __nv_bfloat16 *rplanes;
     int *ER, *EQ;
+    int *ER1;  // column bounds of the first pass's R (kept for R = R2 R1)
     CUtensorMap mapRA, mapRB;  // 128-row and 32-row boxes
     int num_sms;
 };
@@ -471,7 +509,7 @@ int oz_prepare(sldqmc_ctx *c)
     const size_t pbytes = (size_t)OZ_S * w->plane_stride * sizeof(__nv_bfloat16);
     const size_t ebytes = sizeof(int) * (size_t)c->cap * N;
     void *mem = nullptr;
-    if (cudaMalloc(&mem, 2 * pbytes + 2 * ebytes + sizeof(int) * N) != cudaSuccess) {
+    if (cudaMalloc(&mem, 2 * pbytes + 3 * ebytes + sizeof(int) * N) != cudaSuccess) {
         cudaGetLastError();
         delete w;
         return SLDQMC_ERR_OOM;
@@ -480,8 +518,9 @@ int oz_prepare(sldqmc_ctx *c)
     w->rplanes = (__nv_bfloat16 *)((uint8_t *)mem + pbytes);
     w->E = (int *)((uint8_t *)mem + 2 * pbytes);
     w->ER = w->E + (size_t)c->cap * N;
-    w->EQ = w->ER + (size_t)c->cap * N;
-    cudaMemsetAsync(mem, 0, 2 * pbytes + 2 * ebytes, c->st);  // zero pads: never written
+    w->ER1 = w->ER + (size_t)c->cap * N;
+    w->EQ = w->ER1 + (size_t)c->cap * N;
+    cudaMemsetAsync(mem, 0, 2 * pbytes + 3 * ebytes, c->st);  // zero pads: never written
     {
         std::vector<int> ones((size_t)N, 1);
         if (cudaMemcpyAsync(w->EQ, ones.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
@@ -503,6 +542,7 @@ int oz_prepare(sldqmc_ctx *c)
     if (cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || w->num_sms < 1)
         w->num_sms = 148;
     cudaFuncSetAttribute(k_oz_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    cudaFuncSetAttribute(k_oz_gemm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
     cudaFuncSetAttribute(k_oz_gemm<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)oz_smem_bytes());
     c->oz_ws = w;
@@ -603,6 +643,80 @@ void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, doub
     k_oz_gemm<false, true, true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapRA, w->mapRB, a);
     prof_end(c);
     c->launches += 2;
+}
+
+// V <- T P^T V with T = D^-1 R D_p (upper triangular; R row stride N),
+// FP64-accurate on the tensor cores: T's rows split with their own maxima,
+// the gathered rows V[p_k] split column-wise with each column's maximum.
+// Ts: an N x N FP64 scratch per item (item stride N*N).
+void oz_update_V(sldqmc_ctx *c, const double *R, double *V, double *Ts, int B)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    const int N = c->N;
+    k_oz_make_T<<<dim3((N + 255) / 256, N, B), 256, 0, c->st>>>(R, c->nn, N, c->d_D, c->d_Dp, Ts);
+    k_oz_slice<<<dim3(N, B), 128, 0, c->st>>>(Ts, c->nn, N, w->ldp, w->plane_stride, w->planes, w->E);
+    k_oz_col_max_exponents<<<dim3((N + 127) / 128, B), 128, 0, c->st>>>(V, c->nn, N, N, w->ER1);
+    k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
+        V, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag, c->d_perm, N);
+    OzArgs a{};
+    a.M = N;
+    a.Nn = N;
+    a.batch = B;
+    a.nk = w->ldp / OKE;
+    a.EA = w->E;
+    a.EB = w->ER1;
+    a.sEA = N;
+    a.sEB = N;
+    a.C = V;
+    a.sC = c->nn;
+    a.ldc = N;
+    a.flag = c->d_flag;
+    const int tiles = oz_per_item<false>((N + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
+    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B);
+    k_oz_gemm<false, false><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRB, a);
+    prof_end(c);
+    c->launches += 5;
+}
+
+// Keeps the current column bounds of R (a first Cholesky-QR pass) for the
+// product R = R2 R1 after the second pass.
+void oz_keep_bounds(sldqmc_ctx *c, int B)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    cudaMemcpyAsync(w->ER1, w->ER, sizeof(int) * (size_t)B * c->N, cudaMemcpyDeviceToDevice, c->st);
+}
+
+// R = R2 R1 of the two Cholesky-QR passes (upper triangular, row stride N,
+// item stride N*N; only the tiles on or above the diagonal of R are
+// written), FP64-accurate on the tensor cores: R2's rows with their own
+// maxima as exponents, R1's columns with the first pass's bounds.
+void oz_r2r1(sldqmc_ctx *c, const double *R2, const double *R1, double *R, int B)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    const int N = c->N;
+    k_oz_slice<<<dim3(N, B), 128, 0, c->st>>>(R2, c->nn, N, w->ldp, w->plane_stride, w->planes, w->E);
+    k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
+        R1, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag);
+    OzArgs a{};
+    a.M = N;
+    a.Nn = N;
+    a.batch = B;
+    a.nk = w->ldp / OKE;
+    a.EA = w->E;
+    a.EB = w->ER1;
+    a.sEA = N;
+    a.sEB = N;
+    a.C = R;
+    a.sC = c->nn;
+    a.ldc = N;
+    a.flag = c->d_flag;
+    const int tiles = oz_per_item<true>((N + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
+    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * N / 3.0 * B);
+    k_oz_gemm<true, false><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRB, a);
+    prof_end(c);
+    c->launches += 3;
 }
 
 void oz_chol_slice(sldqmc_ctx *c, int k0, int kb, const double *R, const double *Y, int B)

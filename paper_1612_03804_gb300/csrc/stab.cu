@@ -643,6 +643,7 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B, int pass
     if (passes == 2) {
         // second pass: W = Q1^T Q1 (as Y Y^T), upper triangle; Q = Q1 R2^{-1}, R = R2 R1
         if (c->oz_ws) {
+            oz_keep_bounds(c, B);
             oz_gram(c, Y, nn, W, 2 * nn, N, B);
         } else {
             GemmF64 g2 = gemm_desc(N, N, N, Y, N, nn, Y, N, nn, W, N, 2 * nn, B);
@@ -650,18 +651,22 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B, int pass
             gemm_ctx(c, g2, false, true);
         }
         chol_pass(c, W, 2 * nn, Y, R2, B);
-        GemmF64 g3 = gemm_desc(N, N, N, R2, N, nn, R1, N, nn, Xt, N, nn, B);
-        g3.a_upper = 1;
-        g3.b_upper = 1;
-        gemm_ctx(c, g3, false, false);
+        if (c->oz_ws) {
+            oz_r2r1(c, R2, R1, Xt, B);
+        } else {
+            GemmF64 g3 = gemm_desc(N, N, N, R2, N, nn, R1, N, nn, Xt, N, nn, B);
+            g3.a_upper = 1;
+            g3.b_upper = 1;
+            gemm_ctx(c, g3, false, false);
+        }
         R = Xt;
     }
     dim3 gd(cdiv(N, 256), B);
     k_new_D<<<gd, 256, 0, c->st>>>(R, nn, N, c->d_Dp, c->d_D, c->d_flag);
     c->launches++;
-    if (c->tc_ws) {
-        // mixed-precision modes: V = (D^{-1} R D_p) P^T V on the tensor cores
-        tc_update_V(c, R, V, B);
+    if (c->oz_ws) {
+        // mixed-precision modes: V = (D^{-1} R D_p) P^T V, FP64-accurate on the tensor cores
+        oz_update_V(c, R, V, Vg, B);
         return;
     }
     k_gather_V<<<gg, 256, 0, c->st>>>(V, Vg, nn, N, c->d_perm, c->d_Dp);
