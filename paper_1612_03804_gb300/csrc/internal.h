@@ -59,10 +59,6 @@ GemmF64 gemm_desc(int M, int N, int K, const double *A, long long lda, long long
                   const double *B, long long ldb, long long sB, double *C, long long ldc,
                   long long sC, int batch);
 
-// Mixed-precision modes: V <- D^{-1} R D_p P^T V on the tensor cores (R upper
-// triangular, D = c->d_D, D_p = c->d_Dp, P = c->d_perm; row stride N, batch
-// stride nn; result in FP64).  Defined in tc_gemm.cu.
-void tc_update_V(sldqmc_ctx *c, const double *R, double *V, int B);
 // Mixed-precision modes, N >= 128: W = X X^T to FP64 accuracy on the
 // BF16 tensor cores (Ozaki splitting; X row stride N, batch stride sX; W row
 // stride ldw, batch stride sW; tiles on or above the diagonal written).

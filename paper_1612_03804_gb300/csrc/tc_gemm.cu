@@ -10,6 +10,8 @@
 //           (E_h + E_m + E_l) so that its representation error (systematic
 //           across slices) falls to 2^-33; A E ~ A_h E_h + A_h E_m + A_l E_h
 //           + A_h E_l + A_l E_m, five kind::tf32 MMAs per K-step;
+//   split BF16 ("bf16x3" mode): both operands in three BF16 parts, the six
+//           products a0e0 + a0e1 + a1e0 + a0e2 + a1e1 + a2e0 as kind::f16 MMAs;
 //   BF16:   one kind::f16 MMA with BF16 operands.
 //
 // The tensor cores accumulate in FP32 with a rounding that is not
@@ -57,8 +59,6 @@ struct TcArgs {
     long long sSn;
     float cu_h, cu_l, cd_h, cd_l;  // scale constants as float pairs
     int *flag;
-    int a_upper;    // A upper triangular: a 128-row tile starts at its first nonzero K-block
-    int b_batched;  // B has a batch coordinate (3D tensor map) instead of one shared matrix
 };
 
 // Exercises the bounded-wait path: waits on an mbarrier that nothing
@@ -143,17 +143,6 @@ constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 static_assert(EPI_COLS % 16 == 0, "epilogue warps drain 16-column chunks");
 
 __device__ __forceinline__ __nv_bfloat16 bf16_rn(float x) { return __float2bfloat16_rn(x); }
-
-// First K-block of a tile.  With an upper-triangular A the K-blocks left of
-// the tile's first row are zero and skipped, but at least two remain (eight
-// K-steps), so that every accumulator receives an MMA.
-template <int MODE>
-__device__ __forceinline__ int first_kblock(const TcArgs &a, int m0)
-{
-    if (!a.a_upper) return 0;
-    const int kb = m0 / ModeCfg<MODE>::KELEM;
-    return kb < a.nk - 2 ? kb : a.nk - 2;
-}
 
 // Stores one 16-column row segment of an operand part: FP32 (split TF32) or
 // BF16 (rounded here; the leading parts are BF16 values already).  `full`
@@ -243,7 +232,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
                 const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
                 const int n0 = tn * BN, m0 = tm * BM;
-                for (int kb = first_kblock<MODE>(a, m0); kb < a.nk; ++kb, ++it) {
+                for (int kb = 0; kb < a.nk; ++kb, ++it) {
                     const int s = it % STAGES;
                     if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, a.flag)) { ok = false; break; }
                     mbar_expect_tx(&full[s], STAGE_BYTES);
@@ -253,9 +242,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int p = 0; p < C::NPA; ++p) tma_load_3d(st + p * TILE_A, mA[p], k0, m0, b, &full[s]);
 #pragma unroll
                     for (int q = 0; q < C::NPB; ++q) {
-                        uint8_t *dst = st + C::NPA * TILE_A + q * TILE_B;
-                        if (a.b_batched) tma_load_3d(dst, mB[q], k0, n0, b, &full[s]);
-                        else tma_load_2d(dst, mB[q], k0, n0, &full[s]);
+                        tma_load_2d(st + C::NPA * TILE_A + q * TILE_B, mB[q], k0, n0, &full[s]);
                     }
                 }
             }
@@ -265,12 +252,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int it = 0, ti = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++ti) {
-                const int m0 = ((t / tiles_n) % tiles_m) * BM;
-                const int kb0 = first_kblock<MODE>(a, m0);
                 // the epilogue must have drained the previous tile's accumulators
                 if (ti > 0 && !mbar_wait(tmem_free, (ti - 1) & 1, a.flag)) { ok = false; break; }
                 fence_after();
-                for (int kb = kb0; kb < a.nk; ++kb, ++it) {
+                for (int kb = 0; kb < a.nk; ++kb, ++it) {
                     const int s = it % STAGES;
                     if (!mbar_wait(&full[s], (it / STAGES) & 1, a.flag)) { ok = false; break; }
                     fence_after();
@@ -279,7 +264,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int k = 0; k < KSTEPS; ++k) {
                         const uint32_t off = k * 32;
-                        const int g = (kb - kb0) * KSTEPS + k;
+                        const int g = kb * KSTEPS + k;
                         if (SPLIT) {
                             // The leading product round-robin over accumulators 0..6; the
                             // small correction products all go to accumulator 7, where their
@@ -445,66 +430,6 @@ __global__ void k_tc_split(const double *X, long long sX, int N, int ldp, const 
     }
 }
 
-// Writes the parts of one FP64 value in a mode's operand format: split TF32
-// (np = 2: v ~ h + m; np = 3: v ~ h + m + l), BF16, or split BF16 (3 parts).
-template <int MODE>
-__device__ __forceinline__ void split_write(double v, void *o0, void *o1, void *o2, long long o, int np)
-{
-    if (MODE == 0) {
-        const float h = to_tf32((float)v);
-        const double r1 = v - (double)h;
-        const float mid = to_tf32((float)r1);
-        static_cast<float *>(o0)[o] = h;
-        static_cast<float *>(o1)[o] = mid;
-        if (np == 3) static_cast<float *>(o2)[o] = to_tf32((float)(r1 - (double)mid));
-    } else if (MODE == 1) {
-        static_cast<__nv_bfloat16 *>(o0)[o] = bf16_rn((float)v);
-    } else {
-        const __nv_bfloat16 p0 = bf16_rn((float)v);
-        const double r1 = v - (double)__bfloat162float(p0);
-        const __nv_bfloat16 p1 = bf16_rn((float)r1);
-        static_cast<__nv_bfloat16 *>(o0)[o] = p0;
-        static_cast<__nv_bfloat16 *>(o1)[o] = p1;
-        static_cast<__nv_bfloat16 *>(o2)[o] = bf16_rn((float)(r1 - (double)__bfloat162float(p1)));
-    }
-}
-
-// A operand of the V update: T[m][k] = R[m][k] Dp[k] / D[m] for k >= m (R is
-// upper triangular; its strictly lower part is not read), 0 below.
-template <int MODE>
-__global__ void k_tc_prep_T(const double *R, long long nn, int N, int ldp, const double *D, const double *Dp,
-                            void *o0, void *o1, void *o2, long long s_out, int np)
-{
-    const int b = blockIdx.z, m = blockIdx.y;
-    const double rd = 1.0 / D[(long long)b * N + m];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
-        const double v = k >= m ? R[(long long)b * nn + (long long)m * N + k] * Dp[(long long)b * N + k] * rd : 0.0;
-        split_write<MODE>(v, o0, o1, o2, (long long)b * s_out + (long long)m * ldp + k, np);
-    }
-}
-
-// B operand of the V update, K-major: Bt[n][k] = V[perm[k]][n], through a
-// 32 x 32 shared-memory tile (coalesced reads along n, writes along k).
-template <int MODE>
-__global__ void k_tc_prep_Vt(const double *V, long long nn, int N, int ldp, const int *perm, void *o0, void *o1,
-                             void *o2, long long s_out, int np)
-{
-    __shared__ double tile[32][33];
-    const int b = blockIdx.z, k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-    for (int r = ty; r < 32; r += 8) {
-        const int k = k0 + r, n = n0 + tx;
-        double v = 0.0;
-        if (k < N && n < N) v = V[(long long)b * nn + (long long)perm[(long long)b * N + k] * N + n];
-        tile[r][tx] = v;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int n = n0 + r, k = k0 + tx;
-        if (n < N && k < N) split_write<MODE>(tile[tx][r], o0, o1, o2, (long long)b * s_out + (long long)n * ldp + k, np);
-    }
-}
-
 struct TcWs {
     int mode, ldp, npa, npb, esz;
     size_t part_elems;       // per operand part: cap * N * ldp
@@ -512,8 +437,6 @@ struct TcWs {
     void *Ep[3];             // E in parts
     CUtensorMap mapA[2][3];  // [buffer][part]
     CUtensorMap mapB[3];     // [part]
-    void *vb[3];             // batched B operand of the V update (parts), aliasing op[1] where it can
-    CUtensorMap mapVB[3];
     void *mem;
     int num_sms;
 };
@@ -587,9 +510,7 @@ int tc_prepare(sldqmc_ctx *c)
     w->esz = w->mode == 0 ? 4 : 2;
     const bool bf = w->mode != 0;
     w->part_elems = (size_t)c->cap * N * w->ldp;
-    const int extra = w->npb > w->npa ? w->npb - w->npa : 0;  // V-update B parts beyond op[1]'s
-    const size_t bytes =
-        (size_t)w->esz * ((2 * w->npa + extra) * w->part_elems + (size_t)w->npb * N * w->ldp);
+    const size_t bytes = (size_t)w->esz * (2 * w->npa * w->part_elems + (size_t)w->npb * N * w->ldp);
     if (cudaMalloc(&w->mem, bytes) != cudaSuccess) {
         cudaGetLastError();
         w->mem = nullptr;
@@ -618,20 +539,6 @@ int tc_prepare(sldqmc_ctx *c)
         } else {
             w->Ep[p] = nullptr;
             w->mapB[p] = w->mapB[0];
-        }
-    }
-    for (int p = 0; p < 3; ++p) {
-        if (p < w->npb) {
-            if (p < w->npa) {
-                w->vb[p] = w->op[1][p];
-            } else {
-                w->vb[p] = q;
-                q += w->esz * w->part_elems;
-            }
-            if (!encode(&w->mapVB[p], w->vb[p], bf, 3, w->ldp, N, c->cap, BN)) return SLDQMC_ERR_CUDA;
-        } else {
-            w->vb[p] = nullptr;
-            w->mapVB[p] = w->mapVB[0];
         }
     }
     cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<0>());
@@ -704,54 +611,6 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
         prof_end(c);
         c->launches++;
     }
-}
-
-// V <- D^{-1} R D_p P^T V on the tensor cores: C[m][n] = sum_k T[m][k] V[p_k][n]
-// with T = D^{-1} R D_p upper triangular (its zero K-blocks skipped), result
-// in FP64.  R, V: row stride N, batch stride nn.
-void tc_update_V(sldqmc_ctx *c, const double *R, double *V, int B)
-{
-    TcWs *w = (TcWs *)c->tc_ws;
-    const int N = c->N;
-    const long long s_out = (long long)N * w->ldp;
-    void *oa[3] = {w->op[0][0], w->op[0][1], w->op[0][2]};
-    void *ob[3] = {w->vb[0], w->vb[1], w->vb[2]};
-    const dim3 ga((N + 255) / 256, N, B), gb((N + 31) / 32, (N + 31) / 32, B);
-    if (w->mode == 0) {
-        k_tc_prep_T<0><<<ga, 256, 0, c->st>>>(R, c->nn, N, w->ldp, c->d_D, c->d_Dp, oa[0], oa[1], oa[2], s_out, 2);
-        k_tc_prep_Vt<0><<<gb, 256, 0, c->st>>>(V, c->nn, N, w->ldp, c->d_perm, ob[0], ob[1], ob[2], s_out, 3);
-    } else if (w->mode == 1) {
-        k_tc_prep_T<1><<<ga, 256, 0, c->st>>>(R, c->nn, N, w->ldp, c->d_D, c->d_Dp, oa[0], oa[1], oa[2], s_out, 1);
-        k_tc_prep_Vt<1><<<gb, 256, 0, c->st>>>(V, c->nn, N, w->ldp, c->d_perm, ob[0], ob[1], ob[2], s_out, 1);
-    } else {
-        k_tc_prep_T<2><<<ga, 256, 0, c->st>>>(R, c->nn, N, w->ldp, c->d_D, c->d_Dp, oa[0], oa[1], oa[2], s_out, 3);
-        k_tc_prep_Vt<2><<<gb, 256, 0, c->st>>>(V, c->nn, N, w->ldp, c->d_perm, ob[0], ob[1], ob[2], s_out, 3);
-    }
-    c->launches += 2;
-    TcArgs a{};
-    a.N = N;
-    a.ldp = w->ldp;
-    a.nk = w->ldp / (w->mode == 0 ? 32 : 64);
-    a.batch = B;
-    a.s_out = s_out;
-    a.s_f64 = c->nn;
-    a.flag = c->d_flag;
-    a.out_f64 = V;
-    a.a_upper = 1;
-    a.b_batched = 1;
-    const int tiles = ((N + BN - 1) / BN) * ((N + BM - 1) / BM) * B;
-    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
-    const CUtensorMap *A = w->mapA[0];
-    // triangular A: about half of the dense 2 N^3 per item
-    prof_begin(c, SLDQMC_KC_GEMM_TC, (double)N * N * (N + 1) * B);
-    if (w->mode == 0)
-        k_tc_gemm<0><<<grid, NTHREADS, smem_bytes<0>(), c->st>>>(A[0], A[1], A[2], w->mapVB[0], w->mapVB[1], w->mapVB[2], a);
-    else if (w->mode == 1)
-        k_tc_gemm<1><<<grid, NTHREADS, smem_bytes<1>(), c->st>>>(A[0], A[1], A[2], w->mapVB[0], w->mapVB[1], w->mapVB[2], a);
-    else
-        k_tc_gemm<2><<<grid, NTHREADS, smem_bytes<2>(), c->st>>>(A[0], A[1], A[2], w->mapVB[0], w->mapVB[1], w->mapVB[2], a);
-    prof_end(c);
-    c->launches++;
 }
 
 }  // namespace sldqmc
