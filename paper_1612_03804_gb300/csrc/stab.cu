@@ -265,197 +265,324 @@ __global__ void k_mmid(const double *Ut, const double *V, const double *D, doubl
     }
 }
 
-// Panel of the right-looking blocked LU with partial pivoting (one CTA per
-// matrix).  Row interchanges are applied across the full row width ncols.
-__global__ void __launch_bounds__(1024) k_lu_panel(double *A, long long sA, int lda, int N, int ncols,
-                                                   int k0, int kb, int *piv, double *logacc,
-                                                   int *lusgn, int *flag)
+// Row interchanges of one LU panel, as the rows of its block row receive
+// them.  Partial pivoting swaps row j with row p_j >= j for j = 0..kb-1 (rows
+// relative to k0).  Composed, the new row j < kb is the original row src_j
+// (any row), and a row i >= kb changes only if it is some p_j, when it
+// receives an original row below kb.  The panel kernels record this per item
+// in the kb + kb ints of piv from position k0: src_j for j < kb, then one
+// entry i * 64 + src(i) per changed row i >= kb (ascending i), closed by -1
+// when the list ends before N.  Only the columns right of the panel still
+// need the interchange (those left of it hold L factors whose trailing
+// updates are done; nothing reads them again), and k_lu_trsm_row applies it
+// as it loads the block row.
+__device__ __forceinline__ bool lu_key_better(unsigned long long k, int i, unsigned long long bk, int bi)
 {
-    const int b = blockIdx.x;
-    double *Ab = A + (long long)b * sA;
-    __shared__ double wv[32];
-    __shared__ int wi[32];
-    __shared__ int s_p;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = k0; j < k0 + kb; ++j) {
-        double best = -1.0;
-        int bi = N;
-        for (int i = j + threadIdx.x; i < N; i += blockDim.x) {
-            double v = fabs(Ab[(long long)i * lda + j]);
-            if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            double ov = __shfl_down_sync(0xffffffffu, best, o);
-            int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double bv = wv[0];
-            int bidx = wi[0];
-            for (int w = 1; w < nw; ++w)
-                if (wv[w] > bv || (wv[w] == bv && wi[w] < bidx)) { bv = wv[w]; bidx = wi[w]; }
-            s_p = bidx < N ? bidx : j;
-        }
-        __syncthreads();
-        const int p = s_p;
-        if (p != j)
-            for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-                double t = Ab[(long long)j * lda + c];
-                Ab[(long long)j * lda + c] = Ab[(long long)p * lda + c];
-                Ab[(long long)p * lda + c] = t;
-            }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            piv[(long long)b * N + j] = p;
-            double v = Ab[(long long)j * lda + j];
-            int sg = (p != j) ? -1 : 1;
-            if (v == 0.0 || !isfinite(v)) {
-                atomicOr(flag, FLAG_NUMERICAL);
-                v = 1.0;
-                Ab[(long long)j * lda + j] = 1.0;
-            }
-            if (v < 0.0) sg = -sg;
-            logacc[b] += log(fabs(v));
-            lusgn[b] *= sg;
-        }
-        __syncthreads();
-        const double vinv = 1.0 / Ab[(long long)j * lda + j];
-        for (int i = j + 1 + threadIdx.x; i < N; i += blockDim.x) Ab[(long long)i * lda + j] *= vinv;
-        __syncthreads();
-        const int w = k0 + kb - j - 1;
-        if (w > 0) {
-            const long long tot = (long long)(N - j - 1) * w;
-            for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
-                int i = j + 1 + (int)(e / w), c = j + 1 + (int)(e % w);
-                Ab[(long long)i * lda + c] -= Ab[(long long)i * lda + j] * Ab[(long long)j * lda + c];
-            }
-        }
-        __syncthreads();
+    return k > bk || (k == bk && i < bi);
+}
+
+// |v| as an integer key: for non-negative doubles the bit pattern orders as
+// the value, so the pivot search runs on the integer pipe.  The largest |v|
+// wins, the lowest row on ties.
+__device__ __forceinline__ unsigned long long lu_key(double v)
+{
+    return (unsigned long long)__double_as_longlong(fabs(v));
+}
+
+__device__ __forceinline__ void lu_warp_argmax(unsigned long long &k, int &i)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_down_sync(0xffffffffu, k, o);
+        const int oi = __shfl_down_sync(0xffffffffu, i, o);
+        if (lu_key_better(ok, oi, k, i)) { k = ok; i = oi; }
     }
 }
 
-// The same panel factorisation with the panel (rows k0..N-1, kb <= 32
-// columns) held in shared memory: pivot search, row swap, scaling and rank-1
-// update run on shared memory, the row interchanges are applied to the
-// columns outside the panel afterwards (in pivot order), and the logarithms
-// of the pivots are taken in parallel and added in pivot order.  Same pivot
-// choice (largest |v|, lowest row on ties) and the same arithmetic as
-// k_lu_panel.  Dynamic shared memory: (N - k0) * 33 doubles + 2 * 32 values.
-constexpr int LU_SMEM_MAX_ROWS = 800;
-__global__ void __launch_bounds__(1024) k_lu_panel_smem(double *A, long long sA, int lda, int N, int ncols, int k0,
-                                                        int kb, int *piv, double *logacc, int *lusgn, int *flag)
+// Logarithm, sign and the interchange record of a factored panel (pr[j]: the
+// pivot row of step j, src[j]: the original row now at j; changed rows >= kb
+// listed by warp 0 in ascending order from org[]).
+__device__ void lu_panel_close(int *pv_out, int R, int kb, const int *org, const double *pvv, const int *pr,
+                               double *logacc, int *lusgn, int b, int N, int k0)
 {
-    extern __shared__ double P[];  // [R][33]
-    __shared__ double wv[32], pv[32], lg[32];
-    __shared__ int wi[32], pr[32];
-    __shared__ int s_p;
+    __shared__ double lg[32];
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane < kb) {
+            lg[lane] = log(fabs(pvv[lane]));
+            pv_out[lane] = org[lane];
+        }
+        int e = 0;
+        for (int i0 = kb; i0 < R; i0 += 32) {
+            const int i = i0 + lane;
+            const bool ch = i < R && org[i] != i;
+            const unsigned m = __ballot_sync(0xffffffffu, ch);
+            if (ch) pv_out[kb + e + __popc(m & ((1u << lane) - 1u))] = i * 64 + org[i];
+            e += __popc(m);
+        }
+        if (lane == 0 && k0 + kb + e < N) pv_out[kb + e] = -1;
+        __syncwarp();
+        if (lane == 0) {
+            double acc = logacc[b];
+            int sg = 1;
+            for (int j = 0; j < kb; ++j) {
+                acc += lg[j];
+                if (pr[j] != j) sg = -sg;
+                if (pvv[j] < 0.0) sg = -sg;
+            }
+            logacc[b] = acc;
+            lusgn[b] *= sg;
+        }
+    }
+}
+
+// Panel of the right-looking blocked LU with partial pivoting, one CTA of
+// 256 threads per matrix, the panel (rows k0..N-1, kb <= 32 columns) in
+// shared memory.  Per column j: the pivot (found during the previous
+// column's update, integer keys), the swap of rows j and p inside the panel
+// by warp 0 with one reciprocal of the pivot, then one pass in which each
+// thread scales its rows' multipliers and updates their remaining columns.
+// Dynamic shared memory: (N - k0) * 33 doubles + (N - k0) ints.
+constexpr int LU_SMEM_MAX_ROWS = 800;
+constexpr int LU_THREADS = 256;
+__global__ void __launch_bounds__(LU_THREADS) k_lu_panel_smem(double *A, long long sA, int lda, int N, int k0,
+                                                              int kb, int *piv, double *logacc, int *lusgn,
+                                                              int *flag)
+{
+    extern __shared__ double P[];  // [R][33], then org[R]
+    __shared__ unsigned long long wk[LU_THREADS / 32];
+    __shared__ int wi[LU_THREADS / 32];
+    __shared__ double pvv[32];
+    __shared__ int pr[32];
+    __shared__ double s_vinv;
     const int b = blockIdx.x;
     double *Ab = A + (long long)b * sA;
     const int R = N - k0;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = wid; r < R; r += nw) P[r * 33 + lane] = lane < kb ? Ab[(long long)(k0 + r) * lda + k0 + lane] : 0.0;
+    int *org = reinterpret_cast<int *>(P + (size_t)R * 33);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int e = tid; e < R * 32; e += LU_THREADS) {
+        const int r = e >> 5, l = e & 31;
+        P[r * 33 + l] = l < kb ? Ab[(long long)(k0 + r) * lda + k0 + l] : 0.0;
+    }
+    for (int i = tid; i < R; i += LU_THREADS) org[i] = i;
     __syncthreads();
+    unsigned long long bk = 0;
+    int bi = R;
+    for (int r = tid; r < R; r += LU_THREADS) {
+        const unsigned long long k = lu_key(P[r * 33]);
+        if (lu_key_better(k, r, bk, bi)) { bk = k; bi = r; }
+    }
     for (int j = 0; j < kb; ++j) {
-        double best = -1.0;
-        int bi = R;
-        for (int r = j + threadIdx.x; r < R; r += blockDim.x) {
-            const double v = fabs(P[r * 33 + j]);
-            if (v > best || (v == best && r < bi)) { best = v; bi = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, best, o);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
+        lu_warp_argmax(bk, bi);
+        if (lane == 0) { wk[wid] = bk; wi[wid] = bi; }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double bv = wv[0];
-            int bidx = wi[0];
-            for (int w = 1; w < nw; ++w)
-                if (wv[w] > bv || (wv[w] == bv && wi[w] < bidx)) { bv = wv[w]; bidx = wi[w]; }
-            const int p = bidx < R ? bidx : j;
-            s_p = p;
-            pr[j] = p;
-        }
-        __syncthreads();
-        const int p = s_p;
-        if (p != j && threadIdx.x < 32) {
-            const double t = P[j * 33 + threadIdx.x];
-            P[j * 33 + threadIdx.x] = P[p * 33 + threadIdx.x];
-            P[p * 33 + threadIdx.x] = t;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double v = P[j * 33 + j];
-            if (v == 0.0 || !isfinite(v)) {
-                atomicOr(flag, FLAG_NUMERICAL);
-                v = 1.0;
-                P[j * 33 + j] = 1.0;
+        if (wid == 0) {
+            unsigned long long k = lane < LU_THREADS / 32 ? wk[lane] : 0ull;
+            int i = lane < LU_THREADS / 32 ? wi[lane] : R;
+            lu_warp_argmax(k, i);
+            const int p = __shfl_sync(0xffffffffu, i, 0) < R ? __shfl_sync(0xffffffffu, i, 0) : j;
+            if (p != j) {
+                const double t = P[j * 33 + lane];
+                P[j * 33 + lane] = P[p * 33 + lane];
+                P[p * 33 + lane] = t;
+                if (lane == 0) {
+                    const int o = org[j];
+                    org[j] = org[p];
+                    org[p] = o;
+                }
             }
-            pv[j] = v;
+            __syncwarp();
+            if (lane == 0) {
+                double v = P[j * 33 + j];
+                if (v == 0.0 || !isfinite(v)) {
+                    atomicOr(flag, FLAG_NUMERICAL);
+                    v = 1.0;
+                    P[j * 33 + j] = 1.0;
+                }
+                pvv[j] = v;
+                pr[j] = p;
+                s_vinv = 1.0 / v;
+            }
         }
         __syncthreads();
-        const double vinv = 1.0 / P[j * 33 + j];
-        for (int r = j + 1 + threadIdx.x; r < R; r += blockDim.x) P[r * 33 + j] *= vinv;
+        const double vinv = s_vinv;
+        bk = 0;
+        bi = R;
+        for (int r = j + 1 + tid; r < R; r += LU_THREADS) {
+            double *row = P + r * 33;
+            const double m = row[j] * vinv;
+            row[j] = m;
+#pragma unroll 4
+            for (int l = j + 1; l < kb; ++l) row[l] -= m * P[j * 33 + l];
+            if (j + 1 < kb) {
+                const unsigned long long k = lu_key(row[j + 1]);
+                if (lu_key_better(k, r, bk, bi)) { bk = k; bi = r; }
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < R * 32; e += LU_THREADS) {
+        const int r = e >> 5, l = e & 31;
+        if (l < kb) Ab[(long long)(k0 + r) * lda + k0 + l] = P[r * 33 + l];
+    }
+    lu_panel_close(piv + (long long)b * N + k0, R, kb, org, pvv, pr, logacc, lusgn, b, N, k0);
+}
+
+// The same panel factorisation on global memory, for panels of more than
+// LU_SMEM_MAX_ROWS rows: same pivot choice and arithmetic, the swaps inside
+// the panel's columns only.  Thread 0 composes the interchanges on the list
+// of changed rows (at most 2 kb) afterwards.
+__global__ void __launch_bounds__(1024) k_lu_panel(double *A, long long sA, int lda, int N, int k0, int kb,
+                                                   int *piv, double *logacc, int *lusgn, int *flag)
+{
+    const int b = blockIdx.x;
+    double *Ab = A + (long long)b * sA + (long long)k0 * lda + k0;  // panel origin
+    const int R = N - k0;
+    __shared__ unsigned long long wk[32];
+    __shared__ int wi[32];
+    __shared__ double pvv[32];
+    __shared__ int pr[32];
+    __shared__ double s_vinv;
+    __shared__ int lpos[64], lorg[64], s_n;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < kb; ++j) {
+        unsigned long long bk = 0;
+        int bi = R;
+        for (int i = j + tid; i < R; i += blockDim.x) {
+            const unsigned long long k = lu_key(Ab[(long long)i * lda + j]);
+            if (lu_key_better(k, i, bk, bi)) { bk = k; bi = i; }
+        }
+        lu_warp_argmax(bk, bi);
+        if (lane == 0) { wk[wid] = bk; wi[wid] = bi; }
         __syncthreads();
-        if (j + 1 < kb)
-            for (int r = j + 1 + wid; r < R; r += nw)
-                if (lane > j && lane < kb) P[r * 33 + lane] -= P[r * 33 + j] * P[j * 33 + lane];
+        if (wid == 0) {
+            unsigned long long k = lane < nw ? wk[lane] : 0ull;
+            int i = lane < nw ? wi[lane] : R;
+            lu_warp_argmax(k, i);
+            i = __shfl_sync(0xffffffffu, i, 0);
+            const int p = i < R ? i : j;
+            if (p != j && lane < kb) {
+                const double t = Ab[(long long)j * lda + lane];
+                Ab[(long long)j * lda + lane] = Ab[(long long)p * lda + lane];
+                Ab[(long long)p * lda + lane] = t;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                double v = Ab[(long long)j * lda + j];
+                if (v == 0.0 || !isfinite(v)) {
+                    atomicOr(flag, FLAG_NUMERICAL);
+                    v = 1.0;
+                    Ab[(long long)j * lda + j] = 1.0;
+                }
+                pvv[j] = v;
+                pr[j] = p;
+                s_vinv = 1.0 / v;
+            }
+        }
+        __syncthreads();
+        const double vinv = s_vinv;
+        for (int i = j + 1 + tid; i < R; i += blockDim.x) {
+            double *row = Ab + (long long)i * lda;
+            const double m = row[j] * vinv;
+            row[j] = m;
+            for (int l = j + 1; l < kb; ++l) row[l] -= m * Ab[(long long)j * lda + l];
+        }
         __syncthreads();
     }
-    // the factored panel back to global memory
-    for (int r = wid; r < R; r += nw)
-        if (lane < kb) Ab[(long long)(k0 + r) * lda + k0 + lane] = P[r * 33 + lane];
-    // row interchanges of the columns outside the panel, in pivot order
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-        if (c >= k0 && c < k0 + kb) continue;
+    // compose the swaps on the changed rows: lpos[t] now holds original row lorg[t]
+    if (tid == 0) {
+        int n = 0;
         for (int j = 0; j < kb; ++j) {
             const int p = pr[j];
-            if (p != j) {
-                const double t = Ab[(long long)(k0 + j) * lda + c];
-                Ab[(long long)(k0 + j) * lda + c] = Ab[(long long)(k0 + p) * lda + c];
-                Ab[(long long)(k0 + p) * lda + c] = t;
+            if (p == j) continue;
+            int a = -1, c = -1;
+            for (int t = 0; t < n; ++t) {
+                if (lpos[t] == j) a = t;
+                if (lpos[t] == p) c = t;
             }
+            if (a < 0) { a = n++; lpos[a] = j; lorg[a] = j; }
+            if (c < 0) { c = n++; lpos[c] = p; lorg[c] = p; }
+            const int o = lorg[a];
+            lorg[a] = lorg[c];
+            lorg[c] = o;
         }
-    }
-    if (threadIdx.x < kb) {
-        lg[threadIdx.x] = log(fabs(pv[threadIdx.x]));
-        piv[(long long)b * N + k0 + threadIdx.x] = k0 + pr[threadIdx.x];
+        s_n = n;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double acc = logacc[b];
-        int sg = 1;
-        for (int j = 0; j < kb; ++j) {
-            acc += lg[j];
-            if (pr[j] != j) sg = -sg;
-            if (pv[j] < 0.0) sg = -sg;
+    if (wid == 0) {
+        int *out = piv + (long long)b * N + k0;
+        if (lane < kb) {
+            int s = lane;
+            for (int t = 0; t < s_n; ++t)
+                if (lpos[t] == lane) s = lorg[t];
+            out[lane] = s;
         }
-        logacc[b] = acc;
-        lusgn[b] *= sg;
+        // changed rows >= kb in ascending order (selection over the short list)
+        if (lane == 0) {
+            int e = 0, last = kb - 1;
+            for (;;) {
+                int nxt = R, o = 0;
+                for (int t = 0; t < s_n; ++t)
+                    if (lpos[t] > last && lpos[t] < nxt && lorg[t] != lpos[t]) { nxt = lpos[t]; o = lorg[t]; }
+                if (nxt == R) break;
+                out[kb + e++] = nxt * 64 + o;
+                last = nxt;
+            }
+            if (k0 + kb + e < N) out[kb + e] = -1;
+            double acc = logacc[b];
+            int sg = 1;
+            for (int j = 0; j < kb; ++j) {
+                acc += log(fabs(pvv[j]));
+                if (pr[j] != j) sg = -sg;
+                if (pvv[j] < 0.0) sg = -sg;
+            }
+            logacc[b] = acc;
+            lusgn[b] *= sg;
+        }
     }
 }
 
-// U12 = L11^{-1} A12 for the block row k0..k0+kb (L11 unit lower).
+// U12 = L11^{-1} A12 for the block row k0..k0+kb (L11 unit lower), with the
+// panel's row interchanges applied to these columns on the way (the record
+// in piv, see above): each thread owns one column, reads the kb source rows
+// and the sources of the changed rows below the block before it writes.
 template <int KB>
-__global__ void __launch_bounds__(128) k_lu_trsm_row(double *A, long long sA, int lda, int ncols, int k0, int kb)
+__global__ void __launch_bounds__(128) k_lu_trsm_row(double *A, long long sA, int lda, int N, int ncols, int k0,
+                                                     int kb, const int *piv)
 {
     __shared__ double Lk[KB][KB + 1];
+    __shared__ int src[KB], edst[KB], esrc[KB];
+    __shared__ int s_E;
     const int b = blockIdx.y;
     double *Ab = A + (long long)b * sA;
+    const int *rec = piv + (long long)b * N + k0;
     for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
         int r = e / KB, c = e % KB;
         Lk[r][c] = (r < kb && c < r) ? Ab[(long long)(k0 + r) * lda + k0 + c] : 0.0;
     }
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        src[lane] = lane < kb ? rec[lane] : 0;
+        const int v = (lane < KB && k0 + kb + lane < N) ? rec[kb + lane] : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, v >= 0);
+        const int E = ~m ? __ffs(~m) - 1 : 32;
+        if (lane < E) {
+            edst[lane] = v >> 6;
+            esrc[lane] = v & 63;
+        }
+        if (lane == 0) s_E = E;
+    }
     __syncthreads();
     const int c = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
-    double w[KB];
+    const int E = s_E;
+    double *col = Ab + (long long)k0 * lda + c;
+    double w[KB], x[KB];
 #pragma unroll
-    for (int r = 0; r < KB; ++r) w[r] = (r < kb) ? Ab[(long long)(k0 + r) * lda + c] : 0.0;
+    for (int r = 0; r < KB; ++r) w[r] = (r < kb) ? col[(long long)src[r] * lda] : 0.0;
+#pragma unroll
+    for (int e = 0; e < KB; ++e)
+        if (e < E) x[e] = col[(long long)esrc[e] * lda];
 #pragma unroll
     for (int r = 0; r < KB; ++r) {
         double acc = w[r];
@@ -464,8 +591,11 @@ __global__ void __launch_bounds__(128) k_lu_trsm_row(double *A, long long sA, in
         w[r] = acc;
     }
 #pragma unroll
+    for (int e = 0; e < KB; ++e)
+        if (e < E) col[(long long)edst[e] * lda] = x[e];
+#pragma unroll
     for (int r = 0; r < KB; ++r)
-        if (r < kb) Ab[(long long)(k0 + r) * lda + c] = w[r];
+        if (r < kb) col[(long long)r * lda] = w[r];
 }
 
 // X_k = U_kk^{-1} Y_k for the block row k0..k0+kb of the right-hand side
@@ -554,7 +684,7 @@ void stab_set_limits(int Npad)
     static bool lu_set = false;
     if (!lu_set) {
         cudaFuncSetAttribute(k_lu_panel_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * 33 * LU_SMEM_MAX_ROWS));
+                             (int)((sizeof(double) * 33 + sizeof(int)) * LU_SMEM_MAX_ROWS));
         lu_set = true;
     }
 }
@@ -698,10 +828,10 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
         int kb = N - k0 < 32 ? N - k0 : 32;
         prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * (N - k0) * kb * kb);
         if (N - k0 <= LU_SMEM_MAX_ROWS)
-            k_lu_panel_smem<<<B, 1024, sizeof(double) * 33 * (N - k0), c->st>>>(
-                A, sItem, lda, N, ncols, k0, kb, c->d_piv, c->d_logacc, c->d_sgn + c->cap, c->d_flag);
+            k_lu_panel_smem<<<B, LU_THREADS, (sizeof(double) * 33 + sizeof(int)) * (N - k0), c->st>>>(
+                A, sItem, lda, N, k0, kb, c->d_piv, c->d_logacc, c->d_sgn + c->cap, c->d_flag);
         else
-            k_lu_panel<<<B, 1024, 0, c->st>>>(A, sItem, lda, N, ncols, k0, kb, c->d_piv, c->d_logacc,
+            k_lu_panel<<<B, 1024, 0, c->st>>>(A, sItem, lda, N, k0, kb, c->d_piv, c->d_logacc,
                                               c->d_sgn + c->cap, c->d_flag);
         prof_end(c);
         c->launches++;
@@ -709,7 +839,7 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
         if (rest > 0) {
             dim3 gt(cdiv(rest, 128), B);
             prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * rest * kb * kb);
-            k_lu_trsm_row<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, ncols, k0, kb);
+            k_lu_trsm_row<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, N, ncols, k0, kb, c->d_piv);
             prof_end(c);
             c->launches++;
             int m2 = N - (k0 + kb);
