@@ -69,12 +69,13 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
 // Left-looking Cholesky-QR on the tensor cores (mixed modes, same N range):
 // oz_chol_begin fixes the digit exponents of R's columns from diag(W);
 // oz_chol_update subtracts the finished rows' contributions from the panel's
-// rows k0..k0+kb of W and of Y = Q^T (k0 > 0); oz_chol_slice splits the
-// panel's finished rows of R and Q^T for the later panels.  W row stride N,
+// rows k0..k0+kb of W and of Y = Q^T (k0 > 0); oz_chol_panel factors the
+// panel's diagonal block, forms its rows of R and Q^T as products with the
+// block's inverse and splits them for the later panels.  W row stride N,
 // item stride sW; R, Y row stride N, item stride N*N.
 void oz_chol_begin(sldqmc_ctx *c, const double *W, long long sW, int B);
 void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, double *Y, int B);
-void oz_chol_slice(sldqmc_ctx *c, int k0, int kb, const double *R, const double *Y, int B);
+void oz_chol_panel(sldqmc_ctx *c, int k0, int kb, const double *W, long long sW, double *Y, double *R, int B);
 // R = R2 R1 of the two passes on the tensor cores (tiles on or above the
 // diagonal written); oz_keep_bounds saves the first pass's column bounds of R
 // before the second pass replaces them.

@@ -153,15 +153,18 @@ __global__ void __launch_bounds__(128) k_oz_slice(const double *X, long long sX,
 // krows within the last block).
 // The exponents are given (Ej[b * sE + j]; sE = 0 for one shared row of
 // exponents), chosen by the caller as bounds known before the values exist;
-// a value at or above its bound raises the numerical flag.  One CTA converts
-// 32 plane rows; eight threads share a row.
-__global__ void __launch_bounds__(256) k_oz_slice_fixed(const double *src, long long sS, long long ld, int j0, int Nc,
-                                                        int krows, int koff, long long plane_stride, int rows_cap,
-                                                        int ldk, __nv_bfloat16 *planes, const int *Ej, long long sE,
-                                                        int *flag, const int *rowidx = nullptr, long long sR = 0)
+// a value at or above its bound raises the numerical flag.  LOCAL: krows <=
+// 32 (one block), and each plane row takes the exponent of its own largest
+// entry, written to Ej.  One CTA converts 32 plane rows; eight threads share
+// a row.
+template <bool LOCAL>
+__device__ __forceinline__ void oz_slice_block(int bx, const double *src, long long sS, long long ld, int j0, int Nc,
+                                               int krows, int koff, long long plane_stride, int rows_cap, int ldk,
+                                               __nv_bfloat16 *planes, int *Ej, long long sE, int *flag,
+                                               const int *rowidx, long long sR)
 {
     __shared__ double tile[32][33];
-    const int b = blockIdx.y, c0 = j0 + blockIdx.x * 32;
+    const int b = blockIdx.y, c0 = j0 + bx * 32;
     // blockIdx.z: the 32-row block of the krows source rows (K positions koff + 32 z ..);
     // source row l is rowidx[b * sR + l] when a row index is given
     const int kz = 32 * blockIdx.z;
@@ -178,18 +181,40 @@ __global__ void __launch_bounds__(256) k_oz_slice_fixed(const double *src, long 
     __syncthreads();
     const int r = threadIdx.x >> 3, q = threadIdx.x & 7;
     const int j = c0 + r;
-    if (j >= Nc) return;
-    const int E = Ej[(long long)b * sE + j];
-    const unsigned long long bound = (unsigned long long)(E + 1023) << 52;  // bit pattern of 2^E
     int dg[4][OZ_S];
-    bool over = false;
+    if (LOCAL) {
+        // the row's largest |entry| over its eight threads (lanes 8r'..8r'+7)
+        unsigned long long mx = 0;
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-        const double x = tile[4 * q + jj][r];
-        over |= ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) >= bound;
-        oz_digits(x, E, 1, dg[jj]);
+        for (int jj = 0; jj < 4; ++jj) {
+            const unsigned long long u =
+                (unsigned long long)__double_as_longlong(tile[4 * q + jj][r]) & 0x7FFFFFFFFFFFFFFFull;
+            mx = u > mx ? u : mx;
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = v > mx ? v : mx;
+        }
+        if (j >= Nc) return;
+        const int ef_max = (int)(mx >> 52);
+        const int E = ef_max > 0 ? ef_max - 1022 : 0;
+        if (q == 0) Ej[(long long)b * sE + j] = E;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) oz_digits(tile[4 * q + jj][r], E, ef_max, dg[jj]);
+    } else {
+        if (j >= Nc) return;
+        const int E = Ej[(long long)b * sE + j];
+        const unsigned long long bound = (unsigned long long)(E + 1023) << 52;  // bit pattern of 2^E
+        bool over = false;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const double x = tile[4 * q + jj][r];
+            over |= ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) >= bound;
+            oz_digits(x, E, 1, dg[jj]);
+        }
+        if (over) atomicOr(flag, FLAG_NUMERICAL);
     }
-    if (over) atomicOr(flag, FLAG_NUMERICAL);
     const long long row = ((long long)b * rows_cap + j) * ldk + koff + 4 * q;
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p) {
@@ -197,6 +222,37 @@ __global__ void __launch_bounds__(256) k_oz_slice_fixed(const double *src, long 
                                 __floats2bfloat162_rn((float)dg[2][p], (float)dg[3][p])};
         *reinterpret_cast<uint2 *>(planes + (long long)p * plane_stride + row) = *reinterpret_cast<const uint2 *>(h2);
     }
+}
+
+__global__ void __launch_bounds__(256) k_oz_slice_fixed(const double *src, long long sS, long long ld, int j0, int Nc,
+                                                        int krows, int koff, long long plane_stride, int rows_cap,
+                                                        int ldk, __nv_bfloat16 *planes, int *Ej, long long sE,
+                                                        int *flag, const int *rowidx = nullptr, long long sR = 0)
+{
+    oz_slice_block<false>(blockIdx.x, src, sS, ld, j0, Nc, krows, koff, plane_stride, rows_cap, ldk, planes, Ej, sE,
+                          flag, rowidx, sR);
+}
+
+// The unsolved rows k0..k0+kb of a Cholesky-QR panel in one launch, each
+// plane row with its own maximum (LOCAL): blocks x < nb0 split Y's rows (all
+// N columns, into the Q^T planes), the others W's (columns j0.., into the R
+// planes).
+struct OzPanelSlice {
+    const double *src[2];
+    long long sS[2];
+    int j0[2], nb0;
+    __nv_bfloat16 *planes[2];
+    int *E[2];
+};
+
+__global__ void __launch_bounds__(256) k_oz_slice_panel(OzPanelSlice a, int N, int kb, int k0, long long plane_stride,
+                                                        int ldk, int *flag)
+{
+    const int part = blockIdx.x < a.nb0 ? 0 : 1;
+    const int bx = part ? blockIdx.x - a.nb0 : blockIdx.x;
+    oz_slice_block<true>(bx, part ? a.src[1] : a.src[0], part ? a.sS[1] : a.sS[0], N, part ? a.j0[1] : a.j0[0], N,
+                         kb, k0, plane_stride, N, ldk, part ? a.planes[1] : a.planes[0], part ? a.E[1] : a.E[0], N,
+                         flag, nullptr, 0);
 }
 
 // Bounds for the entries of R's columns in a Cholesky factorisation of the
@@ -242,15 +298,128 @@ __global__ void k_oz_make_T(const double *R, long long nn, int N, const double *
             k >= m ? R[(long long)b * nn + (long long)m * N + k] * Dp[(long long)b * N + k] * rd : 0.0;
 }
 
-struct OzArgs {
-    int M, Nn;              // rows of A (rows of C) and rows of B (columns of C)
-    int arow0, brow0;       // first plane rows of A and B (tensor-map row coordinates)
-    int batch, nk;          // items, 32-wide K-blocks
-    const int *EA, *EB;     // row exponents of A and B
-    long long sEA, sEB;     // their item strides
-    double *C;              // result: row stride ldc, item stride sC
+// Cholesky factor of a panel's diagonal block, W_kk = R_kk^T R_kk (R_kk
+// upper triangular, written to R), and the digit planes of T = R_kk^-T
+// (lower triangular; each row with its own maximum as exponent, ET) for the
+// panel's product [R_k,k+ | Q_k^T] = T [W_k,k+ | Y_k] on the tensor cores.
+// One CTA of 128 threads per item; rows and columns kb..31 of R_kk are the
+// identity.  The factor is the right-looking one of the FP64 panel kernel;
+// T is formed column-oriented with the same operations per entry as a
+// forward substitution of R_kk^T t = e_c (the terms l = 0, 1, ... in order,
+// then the reciprocal of the pivot).
+__global__ void __launch_bounds__(128) k_oz_chol_factor(const double *W, long long sW, int ldw, double *R, long long sR,
+                                                        int N, int k0, int kb, __nv_bfloat16 *tplanes, long long tps,
+                                                        int *ET, int *flag)
+{
+    __shared__ double Rk[32][33];
+    __shared__ double Tm[32][33];
+    __shared__ double rinv[32];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const double *Wb = W + (long long)b * sW;
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
+        const int r = e >> 5, c = e & 31;
+        double v = 0.0;
+        if (r < kb && c < kb) {
+            if (c >= r) v = Wb[(long long)(k0 + r) * ldw + k0 + c];
+        } else if (r == c) {
+            v = 1.0;
+        }
+        Rk[r][c] = v;
+        Tm[r][c] = r == c ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < 32; ++j) {
+        if (tid == 0) {
+            double d = Rk[j][j];
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (j < kb) atomicOr(flag, FLAG_NUMERICAL);
+                d = 1.0;
+            }
+            d = sqrt(d);
+            Rk[j][j] = d;
+            rinv[j] = 1.0 / d;
+        }
+        __syncthreads();
+        const double ri = rinv[j];
+        for (int c = j + 1 + tid; c < 32; c += blockDim.x) Rk[j][c] *= ri;
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+            const int r = e >> 5, c = e & 31;
+            if (r > j && c >= r) Rk[r][c] -= Rk[j][r] * Rk[j][c];
+        }
+        __syncthreads();
+    }
+    double *Rb = R + (long long)b * sR;
+    for (int e = tid; e < kb * kb; e += blockDim.x) {
+        const int r = e / kb, c = e % kb;
+        Rb[(long long)(k0 + r) * N + k0 + c] = c >= r ? Rk[r][c] : 0.0;
+    }
+    // R_kk^T T = I: step l finalises row l of T, then removes its share from the rows below
+    for (int l = 0; l < 32; ++l) {
+        if (tid <= l) Tm[l][tid] *= rinv[l];
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+            const int r = e >> 5, c = e & 31;
+            if (r > l && c <= l) Tm[r][c] -= Rk[l][r] * Tm[l][c];
+        }
+        __syncthreads();
+    }
+    // digits of T's rows: four threads per row, eight K positions each
+    const int r = tid >> 2, q = tid & 3;
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(Tm[r][8 * q + i]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = u > mx ? u : mx;
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+    }
+    const int ef_max = (int)(mx >> 52);
+    const int E = ef_max > 0 ? ef_max - 1022 : 0;
+    if (q == 0) ET[b * 32 + r] = E;
+    int dg[8][OZ_S];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) oz_digits(Tm[r][8 * q + i], E, ef_max, dg[i]);
+    const long long row = ((long long)b * 32 + r) * 32 + 8 * q;
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) {
+        __nv_bfloat162 h2[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h2[i] = __floats2bfloat162_rn((float)dg[2 * i][p], (float)dg[2 * i + 1][p]);
+        *reinterpret_cast<uint4 *>(tplanes + (long long)p * tps + row) = *reinterpret_cast<const uint4 *>(h2);
+    }
+}
+
+// One part of a product's rows: rows m of C (rows of A, starting at plane row
+// arow0 of the part's A map), their exponents, and where C goes; with SLICE,
+// where the digits of C's values go as well (plane rows srow0 + m, K
+// positions skoff + n, exponents SE[b * sSE + srow0 + m]).
+struct OzPart {
+    int M, arow0;
+    const int *EA;
+    long long sEA;
+    double *C;
     long long sC;
     int ldc;
+    __nv_bfloat16 *sp;
+    const int *SE;
+    long long sSE;
+    int srow0;
+};
+
+struct OzArgs {
+    OzPart pt[2];           // pt[1] only with nparts = 2 (its A rows through the second A map)
+    int nparts;
+    int Nn, brow0;          // rows of B (columns of C), first plane row of B
+    int batch, nk;          // items, 32-wide K-blocks
+    int kA0, kB0;           // first K positions (elements) of A and B in their planes
+    const int *EB;          // row exponents of B
+    long long sEB;
+    long long splane_stride;  // SLICE: plane stride, leading dimension, plane rows per item,
+    int sldp, srows, skoff;   // and the K position of n = 0
     int *flag;
 };
 
@@ -286,13 +455,36 @@ __host__ __device__ inline int oz_per_item(int tiles_m, int tiles_n)
     return n;
 }
 
+// Tiles of the whole launch: part 0's for all items, then part 1's.
+template <bool UPPER>
+__host__ __device__ inline int oz_part_tiles(const OzArgs &a, int part)
+{
+    const int M = part ? a.pt[1].M : a.pt[0].M;
+    return oz_per_item<UPPER>((M + OBM - 1) / OBM, (a.Nn + OBN - 1) / OBN) * a.batch;
+}
+
+template <bool UPPER>
+__device__ __forceinline__ void oz_locate(const OzArgs &a, int t, int tiles0, int &part, int &b, int &m0, int &n0)
+{
+    part = t < tiles0 ? 0 : 1;
+    if (part) t -= tiles0;
+    const int M = part ? a.pt[1].M : a.pt[0].M;
+    const int tiles_m = (M + OBM - 1) / OBM, tiles_n = (a.Nn + OBN - 1) / OBN;
+    oz_tile<UPPER>(t, tiles_m, tiles_n, oz_per_item<UPPER>(tiles_m, tiles_n), b, m0, n0);
+}
+
 // UPPER: only the tiles on or above the diagonal (C square, A and B the same
 // rows); SUB: C -= A B^T, otherwise C = A B^T; TRANS: element (m, n) of the
-// product lives at C[n * ldc + m] (a warp's 32 rows m are then contiguous).
-template <bool UPPER, bool SUB, bool TRANS = false>
+// product lives at C[n * ldc + m] (a warp's 32 rows m are then contiguous);
+// SLICE (with TRANS, not SUB): the results are also split into digit planes
+// with given exponents, the value (m, n) at K position skoff + n of plane row
+// srow0 + m (zero digits for n >= Nn up to the tile's 32).
+template <bool UPPER, bool SUB, bool TRANS = false, bool SLICE = false>
 __global__ void __launch_bounds__(OTHREADS, 1)
-    k_oz_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzArgs a)
+    k_oz_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+              const __grid_constant__ CUtensorMap tB, OzArgs a)
 {
+    static_assert(!SLICE || (TRANS && !SUB), "SLICE needs TRANS and C = A B^T");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(base + OSTAGES * OSTAGE);
@@ -302,9 +494,8 @@ __global__ void __launch_bounds__(OTHREADS, 1)
     uint32_t *tmem_slot = (uint32_t *)(tmem_free + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_m = (a.M + OBM - 1) / OBM, tiles_n = (a.Nn + OBN - 1) / OBN;
-    const int per_item = oz_per_item<UPPER>(tiles_m, tiles_n);
-    const int tiles = per_item * a.batch;
+    const int tiles0 = oz_part_tiles<UPPER>(a, 0);
+    const int tiles = tiles0 + (a.nparts > 1 ? oz_part_tiles<UPPER>(a, 1) : 0);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OSTAGES; ++s) {
@@ -333,8 +524,10 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             int it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-                int b, m0, n0;
-                oz_tile<UPPER>(t, tiles_m, tiles_n, per_item, b, m0, n0);
+                int part, b, m0, n0;
+                oz_locate<UPPER>(a, t, tiles0, part, b, m0, n0);
+                const CUtensorMap *mA = part ? &tA1 : &tA0;
+                const int arow0 = part ? a.pt[1].arow0 : a.pt[0].arow0;
                 for (int kb = 0; kb < a.nk; ++kb, ++it) {
                     const int s = it % OSTAGES;
                     if (it >= OSTAGES && !mbar_wait(&empty[s], ((it / OSTAGES) - 1) & 1, a.flag)) { ok = false; break; }
@@ -343,8 +536,8 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                     const int k0 = kb * OKE;
 #pragma unroll
                     for (int p = 0; p < OZ_S; ++p) {
-                        tma_load_4d(st + p * OTILE_A, &tA, k0, a.arow0 + m0, b, p, &full[s]);
-                        tma_load_4d(st + OZ_S * OTILE_A + p * OTILE_B, &tB, k0, a.brow0 + n0, b, p, &full[s]);
+                        tma_load_4d(st + p * OTILE_A, mA, a.kA0 + k0, arow0 + m0, b, p, &full[s]);
+                        tma_load_4d(st + OZ_S * OTILE_A + p * OTILE_B, &tB, a.kB0 + k0, a.brow0 + n0, b, p, &full[s]);
                     }
                 }
             }
@@ -395,19 +588,25 @@ __global__ void __launch_bounds__(OTHREADS, 1)
         int cc = 0;  // chunk counter, in step with the MMA thread's
         bool ok = true;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-            int b, m0, n0;
-            oz_tile<UPPER>(t, tiles_m, tiles_n, per_item, b, m0, n0);
+            int part, b, m0, n0;
+            oz_locate<UPPER>(a, t, tiles0, part, b, m0, n0);
+            const int M = part ? a.pt[1].M : a.pt[0].M;
+            const int *EA = part ? a.pt[1].EA : a.pt[0].EA;
+            const long long sEA = part ? a.pt[1].sEA : a.pt[0].sEA;
+            double *C = part ? a.pt[1].C : a.pt[0].C;
+            const long long sC = part ? a.pt[1].sC : a.pt[0].sC;
+            const int ldc = part ? a.pt[1].ldc : a.pt[0].ldc;
             const int mm = m0 + q4 * 32 + lane;
-            const int Ei = mm < a.M ? a.EA[(long long)b * a.sEA + mm] : 0;
+            const int Ei = mm < M ? EA[(long long)b * sEA + mm] : 0;
             // element (mm, n) at o[n * cs]; for an update, the old values of this
             // thread's row segment, fetched while the MMAs run
-            double *o = a.C + (long long)b * a.sC + (TRANS ? (long long)mm : (long long)mm * a.ldc);
-            const long long cs = TRANS ? a.ldc : 1;
+            double *o = C + (long long)b * sC + (TRANS ? (long long)mm : (long long)mm * ldc);
+            const long long cs = TRANS ? ldc : 1;
             const int nb = n0 + hc;
             const int *eb = a.EB + (long long)b * a.sEB;
             double cold[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) cold[j] = (SUB && mm < a.M && nb + j < a.Nn) ? o[(nb + j) * cs] : 0.0;
+            for (int j = 0; j < 16; ++j) cold[j] = (SUB && mm < M && nb + j < a.Nn) ? o[(nb + j) * cs] : 0.0;
             // sum over K-chunks of the exactly accumulated chunk products
             double w[16];
 #pragma unroll
@@ -447,16 +646,46 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                 if (!ok) break;
             }
             if (!ok) break;
-            if (mm >= a.M) continue;
+            if (mm >= M) continue;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int n = nb + j;
+                double v = 0.0;
                 if (n < a.Nn) {
                     const int e = Ei + eb[n] - 35;
-                    const double v = (e > -1000 && e < 1000) ? w[j] * __longlong_as_double((long long)(e + 1023) << 52)
-                                                             : scalbn(w[j], e);
+                    v = (e > -1000 && e < 1000) ? w[j] * __longlong_as_double((long long)(e + 1023) << 52)
+                                                : scalbn(w[j], e);
                     o[n * cs] = SUB ? cold[j] - v : v;
                 }
+                if (SLICE) w[j] = v;
+            }
+            if (SLICE) {
+                const int srow = (part ? a.pt[1].srow0 : a.pt[0].srow0) + mm;
+                const int *SE = part ? a.pt[1].SE : a.pt[0].SE;
+                const long long sSE = part ? a.pt[1].sSE : a.pt[0].sSE;
+                __nv_bfloat16 *sp = part ? a.pt[1].sp : a.pt[0].sp;
+                const int E = SE[(long long)b * sSE + srow];
+                const unsigned long long bound = (unsigned long long)(E + 1023) << 52;  // bit pattern of 2^E
+                bool over = false;
+                __nv_bfloat16 *dst = sp + ((long long)b * a.srows + srow) * a.sldp + a.skoff + nb;
+#pragma unroll
+                for (int g4 = 0; g4 < 4; ++g4) {
+                    int dg[4][OZ_S];
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const double x = w[4 * g4 + jj];
+                        over |= ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) >= bound;
+                        oz_digits(x, E, 1, dg[jj]);
+                    }
+#pragma unroll
+                    for (int p = 0; p < OZ_S; ++p) {
+                        __nv_bfloat162 h2[2] = {__floats2bfloat162_rn((float)dg[0][p], (float)dg[1][p]),
+                                                __floats2bfloat162_rn((float)dg[2][p], (float)dg[3][p])};
+                        *reinterpret_cast<uint2 *>(dst + (long long)p * a.splane_stride + 4 * g4) =
+                            *reinterpret_cast<const uint2 *>(h2);
+                    }
+                }
+                if (over) atomicOr(a.flag, FLAG_NUMERICAL);
             }
         }
     }
@@ -480,6 +709,13 @@ struct OzWs {
     int *ER, *EQ;
     int *ER1;  // column bounds of the first pass's R (kept for R = R2 R1)
     CUtensorMap mapRA, mapRB;  // 128-row and 32-row boxes
+    // Cholesky-QR panels: digit planes of T = R_kk^-T (32 x 32 per item) and
+    // their row exponents; column exponents of the unsolved panel rows of Y
+    // (EPY) and of W (EPW)
+    __nv_bfloat16 *tplanes;
+    long long tplane_stride;
+    int *ET, *EPY, *EPW;
+    CUtensorMap mapT;
     int num_sms;
 };
 
@@ -508,19 +744,27 @@ int oz_prepare(sldqmc_ctx *c)
     w->plane_stride = (long long)c->cap * N * w->ldp;
     const size_t pbytes = (size_t)OZ_S * w->plane_stride * sizeof(__nv_bfloat16);
     const size_t ebytes = sizeof(int) * (size_t)c->cap * N;
+    w->tplane_stride = (long long)c->cap * 32 * 32;
+    const size_t tbytes = (size_t)OZ_S * w->tplane_stride * sizeof(__nv_bfloat16);
+    const size_t tebytes = sizeof(int) * (size_t)c->cap * 32;
+    const size_t eoff = 2 * pbytes + tbytes;  // the int arrays follow the planes
     void *mem = nullptr;
-    if (cudaMalloc(&mem, 2 * pbytes + 3 * ebytes + sizeof(int) * N) != cudaSuccess) {
+    if (cudaMalloc(&mem, eoff + 5 * ebytes + tebytes + sizeof(int) * N) != cudaSuccess) {
         cudaGetLastError();
         delete w;
         return SLDQMC_ERR_OOM;
     }
     w->planes = (__nv_bfloat16 *)mem;
     w->rplanes = (__nv_bfloat16 *)((uint8_t *)mem + pbytes);
-    w->E = (int *)((uint8_t *)mem + 2 * pbytes);
+    w->tplanes = (__nv_bfloat16 *)((uint8_t *)mem + 2 * pbytes);
+    w->E = (int *)((uint8_t *)mem + eoff);
     w->ER = w->E + (size_t)c->cap * N;
     w->ER1 = w->ER + (size_t)c->cap * N;
-    w->EQ = w->ER1 + (size_t)c->cap * N;
-    cudaMemsetAsync(mem, 0, 2 * pbytes + 3 * ebytes, c->st);  // zero pads: never written
+    w->EPY = w->ER1 + (size_t)c->cap * N;
+    w->EPW = w->EPY + (size_t)c->cap * N;
+    w->ET = w->EPW + (size_t)c->cap * N;
+    w->EQ = w->ET + (size_t)c->cap * 32;
+    cudaMemsetAsync(mem, 0, eoff + 5 * ebytes + tebytes, c->st);  // zero pads: never written
     {
         std::vector<int> ones((size_t)N, 1);
         if (cudaMemcpyAsync(w->EQ, ones.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
@@ -532,7 +776,8 @@ int oz_prepare(sldqmc_ctx *c)
     }
     if (!encode4(&w->mapA, w->planes, w->ldp, N, c->cap, OBM) || !encode4(&w->mapB, w->planes, w->ldp, N, c->cap, OBN) ||
         !encode4(&w->mapRA, w->rplanes, w->ldp, N, c->cap, OBM) ||
-        !encode4(&w->mapRB, w->rplanes, w->ldp, N, c->cap, OBN)) {
+        !encode4(&w->mapRB, w->rplanes, w->ldp, N, c->cap, OBN) ||
+        !encode4(&w->mapT, w->tplanes, 32, 32, c->cap, OBN)) {
         cudaFree(mem);
         delete w;
         return SLDQMC_ERR_CUDA;
@@ -544,6 +789,8 @@ int oz_prepare(sldqmc_ctx *c)
     cudaFuncSetAttribute(k_oz_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
     cudaFuncSetAttribute(k_oz_gemm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
     cudaFuncSetAttribute(k_oz_gemm<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)oz_smem_bytes());
+    cudaFuncSetAttribute(k_oz_gemm<false, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)oz_smem_bytes());
     c->oz_ws = w;
     return SLDQMC_OK;
@@ -558,6 +805,30 @@ void oz_release(sldqmc_ctx *c)
     c->oz_ws = nullptr;
 }
 
+namespace {
+
+OzPart oz_part(int M, int arow0, const int *EA, long long sEA, double *C, long long sC, int ldc)
+{
+    OzPart p{};
+    p.M = M;
+    p.arow0 = arow0;
+    p.EA = EA;
+    p.sEA = sEA;
+    p.C = C;
+    p.sC = sC;
+    p.ldc = ldc;
+    return p;
+}
+
+template <bool UPPER>
+int oz_grid(const OzWs *w, const OzArgs &a)
+{
+    const int tiles = oz_part_tiles<UPPER>(a, 0) + (a.nparts > 1 ? oz_part_tiles<UPPER>(a, 1) : 0);
+    return tiles < w->num_sms ? tiles : w->num_sms;
+}
+
+}  // namespace
+
 // W = X X^T (rows of X: row stride N, batch stride sX); W row stride ldw,
 // batch stride sW.  Tiles on or above the diagonal are written in full.
 void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long sW, int ldw, int B)
@@ -566,22 +837,16 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
     const int N = c->N;
     k_oz_slice<<<dim3(N, B), 128, 0, c->st>>>(X, sX, N, w->ldp, w->plane_stride, w->planes, w->E);
     OzArgs a{};
-    a.M = N;
+    a.pt[0] = oz_part(N, 0, w->E, N, W, sW, ldw);
+    a.nparts = 1;
     a.Nn = N;
     a.batch = B;
     a.nk = w->ldp / OKE;
-    a.EA = w->E;
     a.EB = w->E;
-    a.sEA = N;
     a.sEB = N;
-    a.C = W;
-    a.sC = sW;
-    a.ldc = ldw;
     a.flag = c->d_flag;
-    const int tiles = oz_per_item<true>((N + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
-    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
     prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B);
-    k_oz_gemm<true, false><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapB, a);
+    k_oz_gemm<true, false><<<oz_grid<true>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapA, w->mapB, a);
     prof_end(c);
     c->launches += 2;
 }
@@ -590,12 +855,13 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
 // forms Q^T = R^-T X^T in Y (row stride N, item stride N*N): before the panel
 // of rows k0..k0+kb the products of all finished rows are subtracted from the
 // panel's rows,
-//   W[k0+r][k0+n] -= sum_{l<k0} R[l][k0+n] R[l][k0+r],
 //   Y[k0+r][n]    -= sum_{l<k0} Q^T[l][n] R[l][k0+r],
-// both FP64-accurate on the tensor cores (the product computed with rows n and
-// columns r, stored transposed so that a warp's stores are contiguous); after
-// the panel its rows of R and Q^T are split into K-block k0/32 of the digit
-// planes.  oz_chol_begin fixes the exponents of R's columns from W's diagonal.
+//   W[k0+r][k0+n] -= sum_{l<k0} R[l][k0+n] R[l][k0+r],
+// FP64-accurate on the tensor cores in one launch of two parts (the product
+// computed with rows n and columns r, stored transposed so that a warp's
+// stores are contiguous); the panel then splits its finished rows of R and
+// Q^T into K-block k0/32 of the digit planes.  oz_chol_begin fixes the
+// exponents of R's columns from W's diagonal.
 void oz_chol_begin(sldqmc_ctx *c, const double *W, long long sW, int B)
 {
     OzWs *w = (OzWs *)c->oz_ws;
@@ -609,40 +875,85 @@ void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, doub
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
     OzArgs a{};
+    a.pt[0] = oz_part(N, 0, w->EQ, 0, Y + (long long)k0 * N, c->nn, N);                    // rows n: columns of Q^T
+    a.pt[1] = oz_part(N - k0, k0, w->ER + k0, N, W + (long long)k0 * N + k0, sW, N);      // rows n: columns k0.. of R
+    a.nparts = 2;
+    a.Nn = kb;
+    a.brow0 = k0;
     a.batch = B;
     a.nk = k0 / OKE;
-    a.flag = c->d_flag;
-    a.brow0 = k0;
     a.EB = w->ER + k0;
     a.sEB = N;
+    a.flag = c->d_flag;
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * (2 * N - k0) * kb * k0 * B);
+    k_oz_gemm<false, true, true>
+        <<<oz_grid<false>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRA, w->mapRB, a);
+    prof_end(c);
+    c->launches++;
+}
+
+// The panel of rows k0..k0+kb once its rows of W and Y are up to date: the
+// unsolved rows are split with each column's own maximum, the diagonal block
+// is factored and inverted (FP64, one CTA per item), and
+//   Y[k0+n][j] = sum_l T[n][l] Y[k0+l][j]   (all j: the rows of Q^T),
+//   R[k0+n][j] = sum_l T[n][l] W[k0+l][j]   (j >= k0 + kb),
+// run FP64-accurate on the tensor cores (K = 32, one exactly accumulated
+// chunk) in place of the triangular solves, in one launch of two parts whose
+// epilogue also splits the finished rows into K-block k0/32 of the digit
+// planes (fixed exponents: EQ for Q^T, ER for R) for the later panels.
+void oz_chol_panel(sldqmc_ctx *c, int k0, int kb, const double *W, long long sW, double *Y, double *R, int B)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    const int N = c->N;
+    const int j0 = k0 + kb, nW = N - j0;
+    OzPanelSlice sl{};
+    sl.src[0] = Y + (long long)k0 * N;
+    sl.sS[0] = c->nn;
+    sl.j0[0] = 0;
+    sl.planes[0] = w->planes;
+    sl.E[0] = w->EPY;
+    sl.nb0 = (N + 31) / 32;
+    sl.src[1] = W + (long long)k0 * N;
+    sl.sS[1] = sW;
+    sl.j0[1] = j0;
+    sl.planes[1] = w->rplanes;
+    sl.E[1] = w->EPW;
+    k_oz_slice_panel<<<dim3(sl.nb0 + (nW + 31) / 32, B), 256, 0, c->st>>>(sl, N, kb, k0, w->plane_stride, w->ldp,
+                                                                           c->d_flag);
+    prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * 2.0 * kb * kb * kb / 3.0);
+    k_oz_chol_factor<<<B, 128, 0, c->st>>>(W, sW, N, R, c->nn, N, k0, kb, w->tplanes, w->tplane_stride, w->ET,
+                                           c->d_flag);
+    prof_end(c);
+    OzArgs a{};
+    a.pt[0] = oz_part(N, 0, w->EPY, N, Y + (long long)k0 * N, c->nn, N);
+    a.pt[0].sp = w->planes;
+    a.pt[0].SE = w->EQ;
+    a.pt[0].sSE = 0;
+    a.pt[0].srow0 = 0;
+    a.pt[1] = oz_part(nW, j0, w->EPW + j0, N, R + (long long)k0 * N + j0, c->nn, N);
+    a.pt[1].sp = w->rplanes;
+    a.pt[1].SE = w->ER;
+    a.pt[1].sSE = N;
+    a.pt[1].srow0 = j0;
+    a.nparts = nW > 0 ? 2 : 1;
     a.Nn = kb;
-    // Y rows k0.. : product rows n = columns of Q^T (all N)
-    a.M = N;
-    a.arow0 = 0;
-    a.EA = w->EQ;
-    a.sEA = 0;
-    a.C = Y + (long long)k0 * N;
-    a.sC = c->nn;
-    a.ldc = N;
-    int tiles = oz_per_item<false>((N + OBM - 1) / OBM, 1) * B;
-    int grid = tiles < w->num_sms ? tiles : w->num_sms;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * N * kb * k0 * B);
-    k_oz_gemm<false, true, true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRB, a);
+    a.brow0 = 0;
+    a.batch = B;
+    a.nk = 1;
+    a.kA0 = k0;
+    a.kB0 = 0;
+    a.EB = w->ET;
+    a.sEB = 32;
+    a.splane_stride = w->plane_stride;
+    a.sldp = w->ldp;
+    a.srows = N;
+    a.skoff = k0;
+    a.flag = c->d_flag;
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * (N + nW) * kb * kb * B);
+    k_oz_gemm<false, false, true, true>
+        <<<oz_grid<false>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRA, w->mapT, a);
     prof_end(c);
-    // W rows k0.. : product rows n = columns k0.. of R
-    const int M = N - k0;
-    a.M = M;
-    a.arow0 = k0;
-    a.EA = w->ER + k0;
-    a.sEA = N;
-    a.C = W + (long long)k0 * N + k0;
-    a.sC = sW;
-    tiles = oz_per_item<false>((M + OBM - 1) / OBM, 1) * B;
-    grid = tiles < w->num_sms ? tiles : w->num_sms;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * M * kb * k0 * B);
-    k_oz_gemm<false, true, true><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapRA, w->mapRB, a);
-    prof_end(c);
-    c->launches += 2;
+    c->launches += 3;
 }
 
 // V <- T P^T V with T = D^-1 R D_p (upper triangular; R row stride N),
@@ -659,22 +970,16 @@ void oz_update_V(sldqmc_ctx *c, const double *R, double *V, double *Ts, int B)
     k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
         V, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag, c->d_perm, N);
     OzArgs a{};
-    a.M = N;
+    a.pt[0] = oz_part(N, 0, w->E, N, V, c->nn, N);
+    a.nparts = 1;
     a.Nn = N;
     a.batch = B;
     a.nk = w->ldp / OKE;
-    a.EA = w->E;
     a.EB = w->ER1;
-    a.sEA = N;
     a.sEB = N;
-    a.C = V;
-    a.sC = c->nn;
-    a.ldc = N;
     a.flag = c->d_flag;
-    const int tiles = oz_per_item<false>((N + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
-    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
     prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B);
-    k_oz_gemm<false, false><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRB, a);
+    k_oz_gemm<false, false><<<oz_grid<false>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapA, w->mapRB, a);
     prof_end(c);
     c->launches += 5;
 }
@@ -699,40 +1004,18 @@ void oz_r2r1(sldqmc_ctx *c, const double *R2, const double *R1, double *R, int B
     k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
         R1, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag);
     OzArgs a{};
-    a.M = N;
+    a.pt[0] = oz_part(N, 0, w->E, N, R, c->nn, N);
+    a.nparts = 1;
     a.Nn = N;
     a.batch = B;
     a.nk = w->ldp / OKE;
-    a.EA = w->E;
     a.EB = w->ER1;
-    a.sEA = N;
     a.sEB = N;
-    a.C = R;
-    a.sC = c->nn;
-    a.ldc = N;
     a.flag = c->d_flag;
-    const int tiles = oz_per_item<true>((N + OBM - 1) / OBM, (N + OBN - 1) / OBN) * B;
-    const int grid = tiles < w->num_sms ? tiles : w->num_sms;
     prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * N / 3.0 * B);
-    k_oz_gemm<true, false><<<grid, OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRB, a);
+    k_oz_gemm<true, false><<<oz_grid<true>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapA, w->mapRB, a);
     prof_end(c);
     c->launches += 3;
-}
-
-void oz_chol_slice(sldqmc_ctx *c, int k0, int kb, const double *R, const double *Y, int B)
-{
-    OzWs *w = (OzWs *)c->oz_ws;
-    const int N = c->N;
-    // R's rows k0..k0+kb, columns k0+kb.. (the ones later panels read)
-    const int j0 = k0 + kb;
-    k_oz_slice_fixed<<<dim3((N - j0 + 31) / 32, B), 256, 0, c->st>>>(R + (long long)k0 * N, c->nn, N, j0, N, kb, k0,
-                                                                    w->plane_stride, N, w->ldp, w->rplanes, w->ER, N,
-                                                                    c->d_flag);
-    // Q^T's rows k0..k0+kb, all columns
-    k_oz_slice_fixed<<<dim3((N + 31) / 32, B), 256, 0, c->st>>>(Y + (long long)k0 * N, c->nn, N, 0, N, kb, k0,
-                                                               w->plane_stride, N, w->ldp, w->planes, w->EQ, 0,
-                                                               c->d_flag);
-    c->launches += 2;
 }
 
 }  // namespace sldqmc

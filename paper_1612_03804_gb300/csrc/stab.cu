@@ -705,37 +705,39 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
     const long long nn = c->nn;
     cudaMemsetAsync(R, 0, sizeof(double) * nn * B, c->st);
     // Tensor-core path (mixed modes): left-looking, the panel's rows of W and
-    // Y are brought up to date just before the panel (FP64-accurate digit
-    // splitting), and the panel's finished rows of R and Q^T are split for the
-    // later panels.  Otherwise right-looking with FP64 trailing updates.
+    // Y are brought up to date just before the panel, the panel's rows of R
+    // and Q^T are its rows of W and Y multiplied by the inverse of the
+    // diagonal block's factor (all FP64-accurate digit splitting), and that
+    // product also splits the finished rows for the later panels.  Otherwise
+    // right-looking with FP64 triangular solves and trailing updates.
     const bool oz = c->oz_ws != nullptr;
     if (oz) oz_chol_begin(c, W, sW, B);
     for (int k0 = 0; k0 < N; k0 += 32) {
         int kb = N - k0 < 32 ? N - k0 : 32;
         int nW = N - (k0 + kb);
-        if (oz && k0 > 0) oz_chol_update(c, k0, kb, W, sW, Y, B);
-        dim3 grid(cdiv(nW + N, CHOL_THREADS * CHOL_CPT), B);
-        // algorithmic flops: factor of the kb x kb block, triangular solves of nW + N columns
-        prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * ((double)kb * kb * kb / 3.0 + (double)(nW + N) * kb * kb));
-        k_chol_panel<32, CHOL_CPT><<<grid, CHOL_THREADS, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
-        prof_end(c);
-        c->launches++;
-        if (nW == 0) continue;
         if (oz) {
-            oz_chol_slice(c, k0, kb, R, Y, B);
+            if (k0 > 0) oz_chol_update(c, k0, kb, W, sW, Y, B);
+            oz_chol_panel(c, k0, kb, W, sW, Y, R, B);
         } else {
-            // W[k0+kb:, k0+kb:] -= R_blk^T R_blk   (upper triangle only)
-            GemmF64 g = gemm_desc(nW, nW, kb, R + (long long)k0 * N + k0 + kb, N, nn,
-                                  R + (long long)k0 * N + k0 + kb, N, nn,
-                                  W + (long long)(k0 + kb) * N + k0 + kb, N, sW, B);
-            g.alpha = -1.0; g.beta = 1.0; g.c_upper = 1;
-            gemm_ctx(c, g, true, false);
-            // Y[k0+kb:, :] -= R_blk^T Qt_blk
-            GemmF64 h = gemm_desc(nW, N, kb, R + (long long)k0 * N + k0 + kb, N, nn,
-                                  Y + (long long)k0 * N, N, nn, Y + (long long)(k0 + kb) * N, N, nn, B);
-            h.alpha = -1.0; h.beta = 1.0;
-            gemm_ctx(c, h, true, false);
+            dim3 grid(cdiv(nW + N, CHOL_THREADS * CHOL_CPT), B);
+            // algorithmic flops: factor of the kb x kb block, triangular solves of nW + N columns
+            prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * ((double)kb * kb * kb / 3.0 + (double)(nW + N) * kb * kb));
+            k_chol_panel<32, CHOL_CPT><<<grid, CHOL_THREADS, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
+            prof_end(c);
+            c->launches++;
         }
+        if (nW == 0 || oz) continue;
+        // W[k0+kb:, k0+kb:] -= R_blk^T R_blk   (upper triangle only)
+        GemmF64 g = gemm_desc(nW, nW, kb, R + (long long)k0 * N + k0 + kb, N, nn,
+                              R + (long long)k0 * N + k0 + kb, N, nn,
+                              W + (long long)(k0 + kb) * N + k0 + kb, N, sW, B);
+        g.alpha = -1.0; g.beta = 1.0; g.c_upper = 1;
+        gemm_ctx(c, g, true, false);
+        // Y[k0+kb:, :] -= R_blk^T Qt_blk
+        GemmF64 h = gemm_desc(nW, N, kb, R + (long long)k0 * N + k0 + kb, N, nn,
+                              Y + (long long)k0 * N, N, nn, Y + (long long)(k0 + kb) * N, N, nn, B);
+        h.alpha = -1.0; h.beta = 1.0;
+        gemm_ctx(c, h, true, false);
     }
 }
 
