@@ -303,18 +303,21 @@ __global__ void k_oz_make_T(const double *R, long long nn, int N, const double *
 // (lower triangular; each row with its own maximum as exponent, ET) for the
 // panel's product [R_k,k+ | Q_k^T] = T [W_k,k+ | Y_k] on the tensor cores.
 // One CTA of 128 threads per item; rows and columns kb..31 of R_kk are the
-// identity.  The factor is the right-looking one of the FP64 panel kernel;
-// T is formed column-oriented with the same operations per entry as a
-// forward substitution of R_kk^T t = e_c (the terms l = 0, 1, ... in order,
-// then the reciprocal of the pivot).
+// identity.  Step j of the right-looking factor takes y = 1/sqrt(d) of the
+// updated pivot d (every warp computes it, so no broadcast waits on it),
+// finalises row j of R (R_jj = d y, R_jc = W_jc y) and row j of T (forward
+// substitution of R_kk^T T = I: row j has received its terms l < j and is
+// scaled by y), then each warp updates whole rows r > j of both with one FMA
+// per row: the upper part c >= r of R, the finished columns c <= j of T.
+// Every FP64 instruction occupies the pipe for a whole warp, so the work is
+// grouped by rows.
 __global__ void __launch_bounds__(128) k_oz_chol_factor(const double *W, long long sW, int ldw, double *R, long long sR,
                                                         int N, int k0, int kb, __nv_bfloat16 *tplanes, long long tps,
                                                         int *ET, int *flag)
 {
     __shared__ double Rk[32][33];
     __shared__ double Tm[32][33];
-    __shared__ double rinv[32];
-    const int b = blockIdx.x, tid = threadIdx.x;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const double *Wb = W + (long long)b * sW;
     for (int e = tid; e < 32 * 32; e += blockDim.x) {
         const int r = e >> 5, c = e & 31;
@@ -329,23 +332,23 @@ __global__ void __launch_bounds__(128) k_oz_chol_factor(const double *W, long lo
     }
     __syncthreads();
     for (int j = 0; j < 32; ++j) {
-        if (tid == 0) {
-            double d = Rk[j][j];
-            if (!(d > 0.0) || !isfinite(d)) {
-                if (j < kb) atomicOr(flag, FLAG_NUMERICAL);
-                d = 1.0;
-            }
-            d = sqrt(d);
-            Rk[j][j] = d;
-            rinv[j] = 1.0 / d;
+        double d = Rk[j][j];
+        if (!(d > 0.0) || !isfinite(d)) {
+            if (tid == 0 && j < kb) atomicOr(flag, FLAG_NUMERICAL);
+            d = 1.0;
+        }
+        const double y = rsqrt(d);
+        if (wid == 0) {
+            if (lane > j) Rk[j][lane] *= y;
+            if (lane <= j) Tm[j][lane] *= y;
         }
         __syncthreads();
-        const double ri = rinv[j];
-        for (int c = j + 1 + tid; c < 32; c += blockDim.x) Rk[j][c] *= ri;
-        __syncthreads();
-        for (int e = tid; e < 32 * 32; e += blockDim.x) {
-            const int r = e >> 5, c = e & 31;
-            if (r > j && c >= r) Rk[r][c] -= Rk[j][r] * Rk[j][c];
+        // every thread has read the pivot; the updates below do not read R_jj
+        if (tid == j) Rk[j][j] = d * y;
+        for (int r = j + 1 + wid; r < 32; r += 4) {
+            const double rjr = Rk[j][r];
+            if (lane >= r) Rk[r][lane] -= rjr * Rk[j][lane];
+            else if (lane <= j) Tm[r][lane] -= rjr * Tm[j][lane];
         }
         __syncthreads();
     }
@@ -354,17 +357,7 @@ __global__ void __launch_bounds__(128) k_oz_chol_factor(const double *W, long lo
         const int r = e / kb, c = e % kb;
         Rb[(long long)(k0 + r) * N + k0 + c] = c >= r ? Rk[r][c] : 0.0;
     }
-    // R_kk^T T = I: step l finalises row l of T, then removes its share from the rows below
-    for (int l = 0; l < 32; ++l) {
-        if (tid <= l) Tm[l][tid] *= rinv[l];
-        __syncthreads();
-        for (int e = tid; e < 32 * 32; e += blockDim.x) {
-            const int r = e >> 5, c = e & 31;
-            if (r > l && c <= l) Tm[r][c] -= Rk[l][r] * Tm[l][c];
-        }
-        __syncthreads();
-    }
-    // digits of T's rows: four threads per row, eight K positions each
+// digits of T's rows: four threads per row, eight K positions each
     const int r = tid >> 2, q = tid & 3;
     unsigned long long mx = 0;
 #pragma unroll
@@ -409,6 +402,16 @@ struct OzPart {
     long long sSE;
     int srow0;
 };
+
+// x 2^e, exact: through the exponent field while the result stays normal
+// (integer arithmetic, off the FP64 pipe), otherwise scalbn.
+__device__ __forceinline__ double oz_scale2(double x, int e)
+{
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex != 0 && ex + e > 0 && ex + e < 2047) return __longlong_as_double(bits + ((long long)e << 52));
+    return scalbn(x, e);
+}
 
 struct OzArgs {
     OzPart pt[2];           // pt[1] only with nparts = 2 (its A rows through the second A map)
@@ -638,8 +641,14 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                             else l[j] += (v0 << (OZ_BETA * (7 - gg))) + (v1 << (OZ_BETA * (6 - gg)));
                         }
                     }
+                    // the chunk's value (one rounding); the first chunk needs no addition
+                    if (kc0 == 0) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) w[half * 8 + j] += fma((double)l[j], 0x1p-28, (double)h[j]);
+                        for (int j = 0; j < 8; ++j) w[half * 8 + j] = fma((double)l[j], 0x1p-28, (double)h[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) w[half * 8 + j] += fma((double)l[j], 0x1p-28, (double)h[j]);
+                    }
                 }
                 fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tmem_free[u])) : "memory");
@@ -652,9 +661,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                 const int n = nb + j;
                 double v = 0.0;
                 if (n < a.Nn) {
-                    const int e = Ei + eb[n] - 35;
-                    v = (e > -1000 && e < 1000) ? w[j] * __longlong_as_double((long long)(e + 1023) << 52)
-                                                : scalbn(w[j], e);
+                    v = oz_scale2(w[j], Ei + eb[n] - 35);
                     o[n * cs] = SUB ? cold[j] - v : v;
                 }
                 if (SLICE) w[j] = v;
