@@ -113,37 +113,39 @@ __device__ __forceinline__ void oz_digits(double x, int E, int ef_max, int dg[OZ
 
 // Digits of every row of X (row-major N x N per item): E[b][i] and the planes
 // (plane p at p * plane_stride, leading dimension ldp; columns N..ldp-1 stay
-// zero).
-__global__ void __launch_bounds__(128) k_oz_slice(const double *X, long long sX, int N, int ldp,
+// zero).  One warp per row, eight rows per CTA: the row's maximum by warp
+// shuffles, then each lane converts pairs of adjacent entries and stores
+// each plane's pair as one BF16x2.
+__global__ void __launch_bounds__(256) k_oz_slice(const double *X, long long sX, int N, int ldp,
                                                   long long plane_stride, __nv_bfloat16 *planes, int *E)
 {
-    const int b = blockIdx.y, i = blockIdx.x;
+    const int b = blockIdx.y, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= N) return;  // whole warps
     const double *x = X + (long long)b * sX + (long long)i * N;
     // the largest |x_ik| (non-negative doubles order like their bit patterns)
     unsigned long long mx = 0;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    for (int k = lane; k < N; k += 32) {
         const unsigned long long u = (unsigned long long)__double_as_longlong(x[k]) & 0x7FFFFFFFFFFFFFFFull;
         mx = u > mx ? u : mx;
     }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
         mx = v > mx ? v : mx;
     }
-    __shared__ unsigned long long red[4];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    mx = red[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = red[w] > mx ? red[w] : mx;
     const int ef_max = (int)(mx >> 52);
     const int Ei = ef_max > 0 ? ef_max - 1022 : 0;
-    if (threadIdx.x == 0) E[(long long)b * N + i] = Ei;
+    if (lane == 0) E[(long long)b * N + i] = Ei;
     const long long row = (long long)b * N * ldp + (long long)i * ldp;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        int dg[OZ_S];
-        oz_digits(x[k], Ei, ef_max, dg);
+    for (int k = 2 * lane; k < N; k += 64) {
+        int d0[OZ_S], d1[OZ_S];
+        oz_digits(x[k], Ei, ef_max, d0);
+        oz_digits(k + 1 < N ? x[k + 1] : 0.0, Ei, ef_max, d1);
 #pragma unroll
         for (int p = 0; p < OZ_S; ++p)
-            planes[(long long)p * plane_stride + row + k] = __float2bfloat16_rn((float)dg[p]);
+            *reinterpret_cast<__nv_bfloat162 *>(planes + (long long)p * plane_stride + row + k) =
+                __floats2bfloat162_rn((float)d0[p], (float)d1[p]);
     }
 }
 
@@ -271,17 +273,29 @@ __global__ void k_oz_col_exponents(const double *W, long long sW, int ldw, int N
 }
 
 // E[b][j] = frexp exponent of max_r |src[r][j]| (|src[r][j]| < 2^E; 0 for a
-// zero column): one thread per column, rows read coalesced across threads.
-__global__ void k_oz_col_max_exponents(const double *src, long long sS, int rows, int cols, int *E)
+// zero column).  A CTA covers 32 columns with eight row groups (each warp
+// reads one 256-byte row segment per row); the eight partial maxima meet in
+// shared memory.
+__global__ void __launch_bounds__(256) k_oz_col_max_exponents(const double *src, long long sS, int rows, int cols,
+                                                              int *E)
 {
-    const int b = blockIdx.y;
+    __shared__ unsigned long long part[8][32];
+    const int b = blockIdx.y, lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
     const double *s = src + (long long)b * sS;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cols; j += gridDim.x * blockDim.x) {
-        unsigned long long mx = 0;
-        for (int r = 0; r < rows; ++r) {
+    unsigned long long mx = 0;
+    if (j < cols) {
+#pragma unroll 4
+        for (int r = g; r < rows; r += 8) {
             const unsigned long long u = (unsigned long long)__double_as_longlong(s[(long long)r * cols + j]) & 0x7FFFFFFFFFFFFFFFull;
             mx = u > mx ? u : mx;
         }
+    }
+    part[g][lane] = mx;
+    __syncthreads();
+    if (g == 0 && j < cols) {
+#pragma unroll
+        for (int q = 1; q < 8; ++q) mx = part[q][lane] > mx ? part[q][lane] : mx;
         const int ef = (int)(mx >> 52);
         E[(long long)b * cols + j] = ef > 0 ? ef - 1022 : 0;
     }
@@ -292,7 +306,10 @@ __global__ void k_oz_col_max_exponents(const double *src, long long sS, int rows
 __global__ void k_oz_make_T(const double *R, long long nn, int N, const double *D, const double *Dp, double *T)
 {
     const int b = blockIdx.z, m = blockIdx.y;
-    const double rd = 1.0 / D[(long long)b * N + m];
+    __shared__ double s_rd;  // one division per row (FP64 division is a long chain on this pipe)
+    if (threadIdx.x == 0) s_rd = 1.0 / D[(long long)b * N + m];
+    __syncthreads();
+    const double rd = s_rd;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x)
         T[(long long)b * nn + (long long)m * N + k] =
             k >= m ? R[(long long)b * nn + (long long)m * N + k] * Dp[(long long)b * N + k] * rd : 0.0;
@@ -842,7 +859,7 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
-    k_oz_slice<<<dim3(N, B), 128, 0, c->st>>>(X, sX, N, w->ldp, w->plane_stride, w->planes, w->E);
+    k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(X, sX, N, w->ldp, w->plane_stride, w->planes, w->E);
     OzArgs a{};
     a.pt[0] = oz_part(N, 0, w->E, N, W, sW, ldw);
     a.nparts = 1;
@@ -972,8 +989,8 @@ void oz_update_V(sldqmc_ctx *c, const double *R, double *V, double *Ts, int B)
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
     k_oz_make_T<<<dim3((N + 255) / 256, N, B), 256, 0, c->st>>>(R, c->nn, N, c->d_D, c->d_Dp, Ts);
-    k_oz_slice<<<dim3(N, B), 128, 0, c->st>>>(Ts, c->nn, N, w->ldp, w->plane_stride, w->planes, w->E);
-    k_oz_col_max_exponents<<<dim3((N + 127) / 128, B), 128, 0, c->st>>>(V, c->nn, N, N, w->ER1);
+    k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(Ts, c->nn, N, w->ldp, w->plane_stride, w->planes, w->E);
+    k_oz_col_max_exponents<<<dim3((N + 31) / 32, B), 256, 0, c->st>>>(V, c->nn, N, N, w->ER1);
     k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
         V, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag, c->d_perm, N);
     OzArgs a{};
@@ -1007,7 +1024,7 @@ void oz_r2r1(sldqmc_ctx *c, const double *R2, const double *R1, double *R, int B
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
-    k_oz_slice<<<dim3(N, B), 128, 0, c->st>>>(R2, c->nn, N, w->ldp, w->plane_stride, w->planes, w->E);
+    k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(R2, c->nn, N, w->ldp, w->plane_stride, w->planes, w->E);
     k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
         R1, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag);
     OzArgs a{};

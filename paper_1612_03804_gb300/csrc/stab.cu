@@ -254,12 +254,17 @@ __global__ void k_mmid(const double *Ut, const double *V, const double *D, doubl
 {
     const int b = blockIdx.z, i = blockIdx.y;
     const double d = D[(long long)b * N + i];
-    const double db = d > 1.0 ? d : 1.0, ds = d > 1.0 ? 1.0 : d;
+    const double ds = d > 1.0 ? 1.0 : d;
+    // 1 / D_b once per row (FP64 division is a long chain on this pipe)
+    __shared__ double s_rdb;
+    if (threadIdx.x == 0) s_rdb = d > 1.0 ? 1.0 / d : 1.0;
+    __syncthreads();
+    const double rdb = s_rdb;
     const double *u = Ut + (long long)b * nn + (long long)i * N;
     const double *v = V + (long long)b * nn + (long long)i * N;
     double *o = Out + (long long)b * N * ldo + (long long)i * ldo;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-        double uu = u[j] / db;
+        double uu = u[j] * rdb;
         o[j] = uu + ds * v[j];
         if (rhs) o[N + j] = uu;
     }
