@@ -76,6 +76,10 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
 void oz_chol_begin(sldqmc_ctx *c, const double *W, long long sW, int B);
 void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, double *Y, int B);
 void oz_chol_panel(sldqmc_ctx *c, int k0, int kb, const double *W, long long sW, double *Y, double *R, int B);
+// Trailing update of the finalisation's blocked LU without a right-hand side
+// (A row stride lda, item stride sA; panel k0..k0+kb with kb = 32), FP64-
+// accurate on the tensor cores.
+void oz_lu_update(sldqmc_ctx *c, double *A, long long sA, int lda, int k0, int kb, int B);
 // R = R2 R1 of the two passes on the tensor cores (tiles on or above the
 // diagonal written); oz_keep_bounds saves the first pass's column bounds of R
 // before the second pass replaces them.

@@ -111,18 +111,21 @@ __device__ __forceinline__ void oz_digits(double x, int E, int ef_max, int dg[OZ
         for (int p = 0; p < OZ_S; ++p) dg[p] = -dg[p];
 }
 
-// Digits of every row of X (row-major N x N per item): E[b][i] and the planes
-// (plane p at p * plane_stride, leading dimension ldp; columns N..ldp-1 stay
-// zero).  One warp per row, eight rows per CTA: the row's maximum by warp
-// shuffles, then each lane converts pairs of adjacent entries and stores
-// each plane's pair as one BF16x2.
-__global__ void __launch_bounds__(256) k_oz_slice(const double *X, long long sX, int N, int ldp,
-                                                  long long plane_stride, __nv_bfloat16 *planes, int *E)
+// Digits of the rows of X (rows x cols, row stride ld, item stride sX): row i
+// becomes plane row i (prow plane rows per item, leading dimension ldp) with
+// K positions 0..cols-1 and exponent E[b * prow + i]; the planes' columns
+// beyond cols are left as they are (zero pads of the buffer).  One warp per
+// row, eight rows per CTA: the row's maximum by warp shuffles, then each lane
+// converts pairs of adjacent entries and stores each plane's pair as one
+// BF16x2.
+__global__ void __launch_bounds__(256) k_oz_slice(const double *X, long long sX, int rows, int cols, int ld, int prow,
+                                                  int ldp, long long plane_stride, __nv_bfloat16 *planes, int *E)
 {
     const int b = blockIdx.y, lane = threadIdx.x & 31;
     const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (i >= N) return;  // whole warps
-    const double *x = X + (long long)b * sX + (long long)i * N;
+    if (i >= rows) return;  // whole warps
+    const int N = cols;
+    const double *x = X + (long long)b * sX + (long long)i * ld;
     // the largest |x_ik| (non-negative doubles order like their bit patterns)
     unsigned long long mx = 0;
     for (int k = lane; k < N; k += 32) {
@@ -136,8 +139,8 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *X, long long sX,
     }
     const int ef_max = (int)(mx >> 52);
     const int Ei = ef_max > 0 ? ef_max - 1022 : 0;
-    if (lane == 0) E[(long long)b * N + i] = Ei;
-    const long long row = (long long)b * N * ldp + (long long)i * ldp;
+    if (lane == 0) E[(long long)b * prow + i] = Ei;
+    const long long row = ((long long)b * prow + i) * ldp;
     for (int k = 2 * lane; k < N; k += 64) {
         int d0[OZ_S], d1[OZ_S];
         oz_digits(x[k], Ei, ef_max, d0);
@@ -247,13 +250,13 @@ struct OzPanelSlice {
     int *E[2];
 };
 
-__global__ void __launch_bounds__(256) k_oz_slice_panel(OzPanelSlice a, int N, int kb, int k0, long long plane_stride,
-                                                        int ldk, int *flag)
+__global__ void __launch_bounds__(256) k_oz_slice_panel(OzPanelSlice a, int N, int ld, int kb, int koff,
+                                                        long long plane_stride, int ldk, int *flag)
 {
     const int part = blockIdx.x < a.nb0 ? 0 : 1;
     const int bx = part ? blockIdx.x - a.nb0 : blockIdx.x;
-    oz_slice_block<true>(bx, part ? a.src[1] : a.src[0], part ? a.sS[1] : a.sS[0], N, part ? a.j0[1] : a.j0[0], N,
-                         kb, k0, plane_stride, N, ldk, part ? a.planes[1] : a.planes[0], part ? a.E[1] : a.E[0], N,
+    oz_slice_block<true>(bx, part ? a.src[1] : a.src[0], part ? a.sS[1] : a.sS[0], ld, part ? a.j0[1] : a.j0[0], N,
+                         kb, koff, plane_stride, N, ldk, part ? a.planes[1] : a.planes[0], part ? a.E[1] : a.E[0], N,
                          flag, nullptr, 0);
 }
 
@@ -816,6 +819,8 @@ int oz_prepare(sldqmc_ctx *c)
                          (int)oz_smem_bytes());
     cudaFuncSetAttribute(k_oz_gemm<false, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)oz_smem_bytes());
+    cudaFuncSetAttribute(k_oz_gemm<false, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)oz_smem_bytes());
     c->oz_ws = w;
     return SLDQMC_OK;
 }
@@ -859,7 +864,8 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
-    k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(X, sX, N, w->ldp, w->plane_stride, w->planes, w->E);
+    k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(X, sX, N, N, N, N, w->ldp, w->plane_stride, w->planes,
+                                                         w->E);
     OzArgs a{};
     a.pt[0] = oz_part(N, 0, w->E, N, W, sW, ldw);
     a.nparts = 1;
@@ -942,8 +948,8 @@ void oz_chol_panel(sldqmc_ctx *c, int k0, int kb, const double *W, long long sW,
     sl.j0[1] = j0;
     sl.planes[1] = w->rplanes;
     sl.E[1] = w->EPW;
-    k_oz_slice_panel<<<dim3(sl.nb0 + (nW + 31) / 32, B), 256, 0, c->st>>>(sl, N, kb, k0, w->plane_stride, w->ldp,
-                                                                           c->d_flag);
+    k_oz_slice_panel<<<dim3(sl.nb0 + (nW + 31) / 32, B), 256, 0, c->st>>>(sl, N, N, kb, k0, w->plane_stride,
+                                                                           w->ldp, c->d_flag);
     prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * 2.0 * kb * kb * kb / 3.0);
     k_oz_chol_factor<<<B, 128, 0, c->st>>>(W, sW, N, R, c->nn, N, k0, kb, w->tplanes, w->tplane_stride, w->ET,
                                            c->d_flag);
@@ -980,6 +986,43 @@ void oz_chol_panel(sldqmc_ctx *c, int k0, int kb, const double *W, long long sW,
     c->launches += 3;
 }
 
+// Trailing update of the finalisation's blocked LU without a right-hand
+// side, A[i][j] -= sum_l L[i][k0+l] U[k0+l][j] for i, j >= k0 + kb (A row
+// stride lda, item stride sA), FP64-accurate on the tensor cores: the rows of
+// L21 and the columns of U12 each split with their own maximum (K = kb = 32,
+// one exactly accumulated chunk).
+void oz_lu_update(sldqmc_ctx *c, double *A, long long sA, int lda, int k0, int kb, int B)
+{
+    OzWs *w = (OzWs *)c->oz_ws;
+    const int N = c->N;
+    const int j0 = k0 + kb, M = N - j0;
+    k_oz_slice<<<dim3((M + 7) / 8, B), 256, 0, c->st>>>(A + (long long)j0 * lda + k0, sA, M, kb, lda, N, w->ldp,
+                                                         w->plane_stride, w->planes, w->E);
+    OzPanelSlice sl{};
+    sl.src[0] = A + (long long)k0 * lda;
+    sl.sS[0] = sA;
+    sl.j0[0] = j0;
+    sl.planes[0] = w->rplanes;
+    sl.E[0] = w->EPW;
+    sl.nb0 = (M + 31) / 32;
+    k_oz_slice_panel<<<dim3(sl.nb0, B), 256, 0, c->st>>>(sl, N, lda, kb, 0, w->plane_stride, w->ldp, c->d_flag);
+    OzArgs a{};
+    a.pt[0] = oz_part(M, 0, w->E, N, A + (long long)j0 * lda + j0, sA, lda);
+    a.nparts = 1;
+    a.Nn = M;
+    a.brow0 = j0;
+    a.batch = B;
+    a.nk = 1;
+    a.EB = w->EPW + j0;
+    a.sEB = N;
+    a.flag = c->d_flag;
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * M * M * kb * B);
+    k_oz_gemm<false, true, false, false>
+        <<<oz_grid<false>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapA, w->mapRB, a);
+    prof_end(c);
+    c->launches += 3;
+}
+
 // V <- T P^T V with T = D^-1 R D_p (upper triangular; R row stride N),
 // FP64-accurate on the tensor cores: T's rows split with their own maxima,
 // the gathered rows V[p_k] split column-wise with each column's maximum.
@@ -989,7 +1032,8 @@ void oz_update_V(sldqmc_ctx *c, const double *R, double *V, double *Ts, int B)
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
     k_oz_make_T<<<dim3((N + 255) / 256, N, B), 256, 0, c->st>>>(R, c->nn, N, c->d_D, c->d_Dp, Ts);
-    k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(Ts, c->nn, N, w->ldp, w->plane_stride, w->planes, w->E);
+    k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(Ts, c->nn, N, N, N, N, w->ldp, w->plane_stride, w->planes,
+                                                         w->E);
     k_oz_col_max_exponents<<<dim3((N + 31) / 32, B), 256, 0, c->st>>>(V, c->nn, N, N, w->ER1);
     k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
         V, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag, c->d_perm, N);
@@ -1024,7 +1068,8 @@ void oz_r2r1(sldqmc_ctx *c, const double *R2, const double *R1, double *R, int B
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
-    k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(R2, c->nn, N, w->ldp, w->plane_stride, w->planes, w->E);
+    k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(R2, c->nn, N, N, N, N, w->ldp, w->plane_stride, w->planes,
+                                                         w->E);
     k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
         R1, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag);
     OzArgs a{};

@@ -850,7 +850,9 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
             prof_end(c);
             c->launches++;
             int m2 = N - (k0 + kb);
-            if (m2 > 0) {
+            if (m2 > 0 && c->oz_ws && !rhs) {
+                oz_lu_update(c, A, sItem, lda, k0, kb, B);
+            } else if (m2 > 0) {
                 GemmF64 g = gemm_desc(m2, rest, kb, A + (long long)(k0 + kb) * lda + k0, lda, sItem,
                                       A + (long long)k0 * lda + k0 + kb, lda, sItem,
                                       A + (long long)(k0 + kb) * lda + k0 + kb, lda, sItem, B);
