@@ -279,11 +279,11 @@ int sldqmc_wait_selftest(sldqmc_ctx *ctx, int max_polls);
 /* Kernel classes for the timing hooks below. */
 #define SLDQMC_KC_GEMM_F64 0   /* FP64 GEMM (slice products in FP64 mode, Gram, trailing updates) */
 #define SLDQMC_KC_GEMM_TC 1    /* tensor-core slice products (3xTF32 / BF16) */
-#define SLDQMC_KC_PANEL_F64 2  /* FP64 panel kernels (Cholesky, LU, triangular solves, pivot sort) */
+#define SLDQMC_KC_PANEL_F64 2  /* FP64 panel kernels (32x32 Cholesky blocks and inverses, LU panels, triangular solves, pivot sort) */
 #define SLDQMC_KC_EFF 3        /* effective-model sweeps */
 #define SLDQMC_KC_LOCAL 4      /* local-update flips */
 #define SLDQMC_KC_OTHER 5      /* everything else */
-#define SLDQMC_KC_GEMM_OZ 6    /* FP64-accurate Gram matrices on the BF16 tensor cores (mixed modes) */
+#define SLDQMC_KC_GEMM_OZ 6    /* FP64-accurate digit-split products on the BF16 tensor cores (mixed modes): Gram matrices, Cholesky-QR updates and panels, R2 R1, V update, LU updates */
 #define SLDQMC_KC_COUNT 7
 
 /* Timing hooks (off by default): when on, every launch on the context's

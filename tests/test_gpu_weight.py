@@ -103,6 +103,26 @@ def test_green_ragged_and_device_batch():
             np.testing.assert_allclose(d_G[k].cpu().numpy(), Gref, rtol=0, atol=G_ATOL)
 
 
+def test_lu_large_panels_and_interchanges():
+    """29x29 (N = 841): the first LU panels have more than 800 rows (the global-memory panel
+    kernel) and the last has 9 columns.  A random field against the oracle: the weight (LU
+    without a right-hand side; in split-TF32 with digit-split trailing updates) and G (LU with
+    one), so that the composed row interchanges of every panel reach the right columns."""
+    m = O.Model(29, 29, mu=-0.3, xi=1.0, beta=0.5, dtau=0.1, n_wrap=5)
+    s = uniform_field(5, m.M, m.N)
+    ref_p, sp = O.weight(m, s, 1)
+    ref_m, sm, Gref = O.weight(m, s, -1, tau0=2, want_G=True)
+    with _ctx(m, 5, max_batch=1) as ctx:
+        ld, sg = ctx.weight(s, 1)
+        assert sg == sp and abs(ld - ref_p) <= LD_RTOL * abs(ref_p)
+        G, ldg, sgg = ctx.green(s, -1, 2)
+        assert sgg == sm and abs(ldg - ref_m) <= LD_RTOL * abs(ref_m)
+        np.testing.assert_allclose(G, Gref, rtol=0, atol=G_ATOL)
+    with _ctx(m, 5, max_batch=1, prec="3xtf32") as ctx:
+        ld, sg = ctx.weight(s, 1)
+        assert sg == sp and abs(ld - ref_p) <= 1e-6 * abs(ref_p)
+
+
 def test_build_K_matches_oracle():
     m = O.Model(6, 5, t=1.3, mu=-0.4, beta=1.0, dtau=0.1)
     with _ctx(m, 10) as ctx:
