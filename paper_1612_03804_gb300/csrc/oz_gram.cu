@@ -630,6 +630,11 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             double cold[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) cold[j] = (SUB && mm < M && nb + j < a.Nn) ? o[(nb + j) * cs] : 0.0;
+            // the columns' exponents, also fetched while the MMAs run (not for an
+            // update, whose old values already take those registers)
+            int ebv[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) ebv[j] = (!SUB && nb + j < a.Nn) ? eb[nb + j] : 0;
             // sum over K-chunks of the exactly accumulated chunk products
             double w[16];
 #pragma unroll
@@ -681,7 +686,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                 const int n = nb + j;
                 double v = 0.0;
                 if (n < a.Nn) {
-                    v = oz_scale2(w[j], Ei + eb[n] - 35);
+                    v = oz_scale2(w[j], Ei + (SUB ? eb[n] : ebv[j]) - 35);
                     o[n * cs] = SUB ? cold[j] - v : v;
                 }
                 if (SLICE) w[j] = v;
@@ -695,21 +700,26 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                 const unsigned long long bound = (unsigned long long)(E + 1023) << 52;  // bit pattern of 2^E
                 bool over = false;
                 __nv_bfloat16 *dst = sp + ((long long)b * a.srows + srow) * a.sldp + a.skoff + nb;
+                // eight K positions per 16-byte store: each lane writes its own plane row,
+                // so the stores cannot coalesce across lanes; wider stores halve the
+                // sector writes
 #pragma unroll
-                for (int g4 = 0; g4 < 4; ++g4) {
-                    int dg[4][OZ_S];
+                for (int g8 = 0; g8 < 2; ++g8) {
+                    int dg[8][OZ_S];
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const double x = w[4 * g4 + jj];
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const double x = w[8 * g8 + jj];
                         over |= ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) >= bound;
                         oz_digits(x, E, 1, dg[jj]);
                     }
 #pragma unroll
                     for (int p = 0; p < OZ_S; ++p) {
-                        __nv_bfloat162 h2[2] = {__floats2bfloat162_rn((float)dg[0][p], (float)dg[1][p]),
-                                                __floats2bfloat162_rn((float)dg[2][p], (float)dg[3][p])};
-                        *reinterpret_cast<uint2 *>(dst + (long long)p * a.splane_stride + 4 * g4) =
-                            *reinterpret_cast<const uint2 *>(h2);
+                        __nv_bfloat162 h2[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            h2[i] = __floats2bfloat162_rn((float)dg[2 * i][p], (float)dg[2 * i + 1][p]);
+                        *reinterpret_cast<uint4 *>(dst + (long long)p * a.splane_stride + 8 * g8) =
+                            *reinterpret_cast<const uint4 *>(h2);
                     }
                 }
                 if (over) atomicOr(a.flag, FLAG_NUMERICAL);
