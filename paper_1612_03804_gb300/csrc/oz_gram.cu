@@ -1,6 +1,9 @@
-// oz_gram.cu -- FP64-accurate Gram matrices on the BF16 tensor cores
-// (Ozaki's error-free splitting), for the Cholesky-QR of the mixed-precision
-// modes.
+// oz_gram.cu -- FP64-accurate products on the BF16 tensor cores (Ozaki's
+// error-free splitting) for the stabilisation and the determinant of the
+// mixed-precision modes: Gram matrices, the left-looking Cholesky-QR updates
+// and panel products (with the inverse of each 32 x 32 diagonal factor,
+// formed here in FP64), R = R2 R1, the V update and the trailing updates of
+// the determinant's LU.  The Gram matrix shows the scheme:
 //
 // W = X X^T for the rows x_i of X (N x N per batch item).  Each row is
 // scaled by a power of two, 2^-E_i with |x_ik| < 2^E_i, and written as eight
@@ -18,12 +21,15 @@
 // group sums to integers, combines them in two 64-bit integers, forms the
 // chunk's FP64 value with one rounding and adds the chunks in FP64.
 //
-// One persistent CTA per SM walks the 128 x 32 tiles on or above the
-// diagonal of every item: warp 0 streams the 8 + 8 digit-plane tiles of a
-// 32-wide K-block by TMA (64-byte swizzle), warp 1 issues the 36 MMAs per
-// 16-wide K-step, and eight epilogue warps drain one of two tensor-memory
-// buffers (8 groups x 32 columns each) while the next tile accumulates into
-// the other.
+// One persistent CTA per SM walks the 128 x 32 output tiles of every item
+// (for a Gram matrix only those on or above the diagonal; a launch may carry
+// two parts with their own A rows and outputs): warp 0 streams the 8 + 8
+// digit-plane tiles of a 32-wide K-block by TMA (64-byte swizzle), warp 1
+// issues the 36 MMAs per 16-wide K-step, and eight epilogue warps drain one
+// of two tensor-memory buffers (8 groups x 32 columns each) while the next
+// tile accumulates into the other.  Every mbarrier wait is bounded; a wait
+// that runs out raises the context's timeout flag and the CTA frees its
+// tensor memory and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
