@@ -324,19 +324,46 @@ __global__ void k_oz_make_T(const double *R, long long nn, int N, const double *
             k >= m ? R[(long long)b * nn + (long long)m * N + k] * Dp[(long long)b * N + k] * rd : 0.0;
 }
 
+// Row j of the diagonal block's factor and of its inverse, finalised by one
+// warp: y = 1/sqrt(d) of the updated pivot d, R_jc = W_jc y (c > j), R_jj =
+// d y, and row j of T scaled by y (it has received its terms l < j).
+__device__ __forceinline__ void oz_chol_finalise_row(double (*Rk)[33], double (*Tm)[33], int j, int lane, int kb,
+                                                     int *flag)
+{
+    double d = Rk[j][j];
+    if (!(d > 0.0) || !isfinite(d)) {
+        if (lane == 0 && j < kb) atomicOr(flag, FLAG_NUMERICAL);
+        d = 1.0;
+    }
+    const double y = rsqrt(d);
+    if (lane > j) Rk[j][lane] *= y;
+    if (lane <= j) Tm[j][lane] *= y;
+    __syncwarp();  // every lane has read the pivot
+    if (lane == j) Rk[j][j] = d * y;
+    __syncwarp();
+}
+
+// Rows r > j of R (upper part c >= r) and of T (finished columns c <= j)
+// lose row j's share: one FMA per warp and row.
+__device__ __forceinline__ void oz_chol_update_row(double (*Rk)[33], double (*Tm)[33], int j, int r, int lane)
+{
+    const double rjr = Rk[j][r];
+    if (lane >= r) Rk[r][lane] -= rjr * Rk[j][lane];
+    else if (lane <= j) Tm[r][lane] -= rjr * Tm[j][lane];
+}
+
 // Cholesky factor of a panel's diagonal block, W_kk = R_kk^T R_kk (R_kk
 // upper triangular, written to R), and the digit planes of T = R_kk^-T
 // (lower triangular; each row with its own maximum as exponent, ET) for the
 // panel's product [R_k,k+ | Q_k^T] = T [W_k,k+ | Y_k] on the tensor cores.
 // One CTA of 128 threads per item; rows and columns kb..31 of R_kk are the
-// identity.  Step j of the right-looking factor takes y = 1/sqrt(d) of the
-// updated pivot d (every warp computes it, so no broadcast waits on it),
-// finalises row j of R (R_jj = d y, R_jc = W_jc y) and row j of T (forward
-// substitution of R_kk^T T = I: row j has received its terms l < j and is
-// scaled by y), then each warp updates whole rows r > j of both with one FMA
-// per row: the upper part c >= r of R, the finished columns c <= j of T.
-// Every FP64 instruction occupies the pipe for a whole warp, so the work is
-// grouped by rows.
+// identity.  Right-looking: once row j of R and of T is final (T by forward
+// substitution of R_kk^T T = I), every later row loses row j's share.  Warp 0
+// updates row j + 1 first and finalises it (the chain of pivots: update,
+// rsqrt, scale) while warps 1..3 update the rows below, so each step costs one
+// barrier and the pivot chain overlaps the other rows' updates.  Every FP64
+// instruction occupies the pipe for a whole warp, so the work is grouped by
+// rows.
 __global__ void __launch_bounds__(128) k_oz_chol_factor(const double *W, long long sW, int ldw, double *R, long long sR,
                                                         int N, int k0, int kb, __nv_bfloat16 *tplanes, long long tps,
                                                         int *ET, int *flag)
@@ -357,24 +384,15 @@ __global__ void __launch_bounds__(128) k_oz_chol_factor(const double *W, long lo
         Tm[r][c] = r == c ? 1.0 : 0.0;
     }
     __syncthreads();
-    for (int j = 0; j < 32; ++j) {
-        double d = Rk[j][j];
-        if (!(d > 0.0) || !isfinite(d)) {
-            if (tid == 0 && j < kb) atomicOr(flag, FLAG_NUMERICAL);
-            d = 1.0;
-        }
-        const double y = rsqrt(d);
+    if (wid == 0) oz_chol_finalise_row(Rk, Tm, 0, lane, kb, flag);
+    __syncthreads();
+    for (int j = 0; j < 31; ++j) {
         if (wid == 0) {
-            if (lane > j) Rk[j][lane] *= y;
-            if (lane <= j) Tm[j][lane] *= y;
-        }
-        __syncthreads();
-        // every thread has read the pivot; the updates below do not read R_jj
-        if (tid == j) Rk[j][j] = d * y;
-        for (int r = j + 1 + wid; r < 32; r += 4) {
-            const double rjr = Rk[j][r];
-            if (lane >= r) Rk[r][lane] -= rjr * Rk[j][lane];
-            else if (lane <= j) Tm[r][lane] -= rjr * Tm[j][lane];
+            oz_chol_update_row(Rk, Tm, j, j + 1, lane);
+            __syncwarp();
+            oz_chol_finalise_row(Rk, Tm, j + 1, lane, kb, flag);
+        } else {
+            for (int r = j + 1 + wid; r < 32; r += 3) oz_chol_update_row(Rk, Tm, j, r, lane);
         }
         __syncthreads();
     }
@@ -383,7 +401,7 @@ __global__ void __launch_bounds__(128) k_oz_chol_factor(const double *W, long lo
         const int r = e / kb, c = e % kb;
         Rb[(long long)(k0 + r) * N + k0 + c] = c >= r ? Rk[r][c] : 0.0;
     }
-// digits of T's rows: four threads per row, eight K positions each
+    // digits of T's rows: four threads per row, eight K positions each
     const int r = tid >> 2, q = tid & 3;
     unsigned long long mx = 0;
 #pragma unroll
