@@ -248,9 +248,11 @@ long long sldqmc_kernel_launches(const sldqmc_ctx *ctx);
  * file-scope device array that every device loading the library keeps until
  * the process exits.  Problems whose workspace exceeds 16 MiB are rejected
  * with SLDQMC_ERR_UNSUPPORTED (about 50 configurations at 8x8, 2 at 16x16;
- * no 32x32).  The first call on a device looks up the array's device address
- * (once per device, with that device current) and should come before any
- * stream capture.  The call waits for its stream before returning its status.
+ * no 32x32; lattices above 16384 sites or more than 100000 slices are
+ * rejected the same way).  The first call on a device looks up the array's
+ * device address (once per device, with that device current).  The call
+ * waits for its stream and reads the status flag back before returning, so
+ * it cannot be called while its stream is being captured into a CUDA graph.
  * All calls share the one array and each call overwrites what the previous
  * one left there: calls that overlap on the GPU (other host threads, other
  * streams) race and must be serialised by the caller. */

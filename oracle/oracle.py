@@ -105,9 +105,12 @@ class Model:
         self.n_wrap = int(n_wrap)
         self.J, self.h = float(J), float(h)
 
+    def kwargs(self):
+        return dict(Lx=self.Lx, Ly=self.Ly, t=self.t, mu=self.mu, xi=self.xi, beta=self.beta,
+                    dtau=self.dtau, n_wrap=self.n_wrap, J=self.J, h=self.h)
+
     def replace(self, **kw):
-        d = dict(Lx=self.Lx, Ly=self.Ly, t=self.t, mu=self.mu, xi=self.xi, beta=self.beta,
-                 dtau=self.dtau, n_wrap=self.n_wrap, J=self.J, h=self.h)
+        d = self.kwargs()
         d.update(kw)
         return Model(**d)
 
@@ -144,6 +147,27 @@ def weight(m, s, eta, tau0=0, n_wrap=None, want_G=False):
     if want_G:
         return float(ld[0]), int(sg[0]), G
     return float(ld[0]), int(sg[0])
+
+
+def _weight_job(job):
+    kw, s, eta, tau0, want_G = job
+    return weight(Model(**kw), s, eta, tau0=tau0, want_G=want_G)
+
+
+def weight_many(m, fields, eta, workers=None, tau0=0, want_G=False):
+    """weight() of every configuration in `fields`, one oracle call per
+    configuration spread over `workers` processes (started with spawn, so a
+    pool may be opened after a CUDA context exists in the caller).  The
+    arithmetic is that of weight(); only the calls run concurrently."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    jobs = [(m.kwargs(), np.ascontiguousarray(f, dtype=np.int8), int(eta), int(tau0), bool(want_G))
+            for f in fields]
+    workers = max(1, min(len(jobs), workers or len(os.sched_getaffinity(0))))
+    if workers == 1:
+        return [_weight_job(j) for j in jobs]
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_weight_job, jobs))
 
 
 def log_bare_weight(m, s):

@@ -18,6 +18,7 @@
 namespace sldqmc {
 void build_K_into(sldqmc_ctx *c, double *ring);
 int weight_run_into(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, double *d_ld, int *d_sign);
+void stab_set_limits(int Npad);
 }  // namespace sldqmc
 
 using namespace sldqmc;
@@ -106,6 +107,11 @@ extern "C" int sldqmc_weight_noalloc(const sldqmc_params *p, void *stream, const
     const long long N = (long long)p->Lx * p->Ly;
     const long long M = llround(p->beta / p->dtau);
     if (M < 1 || fabs((double)M * p->dtau - p->beta) > 1e-12 * p->beta) return SLDQMC_ERR_ARG;
+    // the same limits as a context, then a bound computed in floating point
+    // (the nine N x N work buffers per configuration alone take 80 N^2 B
+    // bytes) so that no size below can overflow
+    if (N > 16384 || M > 100000) return SLDQMC_ERR_UNSUPPORTED;
+    if (80.0 * (double)N * (double)N * (double)B > (double)SCRATCH_BYTES) return SLDQMC_ERR_UNSUPPORTED;
     const double logk = (double)(p->n_wrap < M ? p->n_wrap : M) * p->dtau * (8.0 * fabs(p->t) + 2.0 * fabs(p->xi));
     if (logk > 16.0) return SLDQMC_ERR_UNSUPPORTED;
 
@@ -133,6 +139,14 @@ extern "C" int sldqmc_weight_noalloc(const sldqmc_params *p, void *stream, const
     int rc = scratch_address(&base);
     if (rc) return rc;
     layout(&c, (uintptr_t)base, &ring);
+    // the LU panel kernel needs more than the default 48 KiB of dynamic
+    // shared memory from about N = 184 on; a context sets this at creation,
+    // this call may be the first user of the library on its device
+    {
+        int Npad = 1;
+        while (Npad < N) Npad <<= 1;
+        stab_set_limits(Npad);
+    }
     // the flag must start at zero; every other region is fully written by the
     // kernels before it is read (identity U and V, D = 1, zeroed R factors)
     if (cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.st) != cudaSuccess) return SLDQMC_ERR_CUDA;

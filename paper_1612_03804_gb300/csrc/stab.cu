@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace sldqmc {
@@ -679,18 +681,28 @@ static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b)
 
 void stab_set_limits(int Npad)
 {
-    // attributes only grow, so that a smaller context never lowers a larger one's limit
-    static size_t sort_max = 48 * 1024;
-    const size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
-    if (sh > sort_max) {
-        cudaFuncSetAttribute(k_sort_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        sort_max = sh;
+    // Function attributes belong to the current device's context, so the
+    // limits reached so far are kept per device.  They only grow, so that a
+    // smaller context never lowers a larger one's limit.
+    constexpr int MAX_DEV = 64;
+    static std::mutex mu;
+    static size_t sort_max[MAX_DEV];
+    static bool lu_set[MAX_DEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) {
+        cudaGetLastError();
+        dev = -1;
     }
-    static bool lu_set = false;
-    if (!lu_set) {
+    std::lock_guard<std::mutex> lk(mu);
+    const size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
+    if (dev < 0 || sh > (sort_max[dev] ? sort_max[dev] : (size_t)48 * 1024)) {
+        cudaFuncSetAttribute(k_sort_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (dev >= 0) sort_max[dev] = sh;
+    }
+    if (dev < 0 || !lu_set[dev]) {
         cudaFuncSetAttribute(k_lu_panel_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((sizeof(double) * 33 + sizeof(int)) * LU_SMEM_MAX_ROWS));
-        lu_set = true;
+        if (dev >= 0) lu_set[dev] = true;
     }
 }
 

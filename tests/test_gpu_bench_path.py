@@ -1,0 +1,197 @@
+"""Parity against the FP64 CPU oracle on the launch shapes the benchmark times.
+
+The benchmark's step at 16x16 walks 1024 output tiles of 128x64 per
+tensor-core slice product on 152 persistent CTAs (about seven tiles per CTA:
+the operand pipeline runs across tile boundaries, tensor memory is handed
+back between tiles and the mbarrier phases flip many times), uses the
+autotuned n_wrap = 32 (the largest block the Cholesky-QR condition bound
+admits at dtau = 0.05), and evaluates chains whose Eq. 4 decisions are taken
+on split-precision weights.  Each of those is compared with the oracle here:
+  - log|det| and sign of every configuration of a 128-configuration batch
+    (several tiles per CTA), split-TF32 and split-BF16, n_wrap = 32, to the
+    reduced-precision bound 1e-6 relative; G of two of them at 1e-5;
+  - the benchmark's own workload size (M = 160, n_wrap = 32);
+  - the FP64-product path at a batch large enough for its 64x64 GEMM tiles;
+  - a split-precision cumulative-update chain (Eq. 4): every decision
+    outside the margin that the log-det bound allows is bit-identical;
+  - the local-update trajectory at 8x8, beta = 8 (the training lattice).
+The oracle's own n_wrap is 10 (its stabilisation is independent of the
+GPU's; its n_wrap invariance is pinned in test_oracle_pins.py)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1612_03804_gb300.inputs import batch_uniform, uniform_field
+
+pytestmark = pytest.mark.gpu
+
+SPLIT_LD_RTOL = 1e-6   # reduced-precision log|det| bound (relative)
+SPLIT_G_ATOL = 1e-5    # reduced-precision G bound (absolute)
+FP64_LD_RTOL = 1e-9
+CLASSES = [[(1, 0, 0), (0, 1, 0)], [(1, 1, 0), (1, -1, 0)], [(2, 0, 0), (0, 2, 0)], [(0, 0, 1)]]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    from paper_1612_03804_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _ctx(m, n_wrap, prec, max_batch):
+    from paper_1612_03804_gb300 import sldqmc
+    return sldqmc.Context(m.Lx, m.Ly, t=m.t, mu=m.mu, xi=m.xi, beta=m.beta, dtau=m.dtau, n_wrap=n_wrap,
+                          J=m.J, h=m.h, prec=prec, max_batch=max_batch)
+
+
+def _gpu_weights(ctx, fields, eta):
+    import torch
+    d_s = torch.from_numpy(fields).cuda()
+    B = fields.shape[0]
+    ld = torch.zeros(B, dtype=torch.float64, device="cuda")
+    sg = torch.zeros(B, dtype=torch.int32, device="cuda")
+    ctx.weight_batch_dev(d_s, eta, ld, sg)
+    ctx.sync()
+    return ld.cpu().numpy(), sg.cpu().numpy()
+
+
+def _check(ld, sg, ref, rtol, what):
+    ref_ld = np.array([r[0] for r in ref])
+    ref_sg = np.array([r[1] for r in ref])
+    np.testing.assert_array_equal(sg, ref_sg)
+    rel = np.abs(ld - ref_ld) / np.abs(ref_ld)
+    print(f"{what}: max rel log-det error {rel.max():.2e} over {len(ld)} configurations")
+    assert rel.max() <= rtol, (what, rel.max(), int(rel.argmax()))
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
+def test_many_tiles_per_cta_nwrap32(prec):
+    """16x16, beta = 2 (M = 40: one 32-slice block and a ragged 8-slice block),
+    B = 128: 1024 tiles per slice product on 152 CTAs, as in the benchmark."""
+    m = O.Model(16, 16, mu=-0.5, xi=1.0, beta=2.0, dtau=0.05, n_wrap=10)
+    B = 128
+    fields = batch_uniform(2401, B, m.M, m.N)
+    ref = O.weight_many(m, fields, -1)
+    with _ctx(m, 32, prec, B) as ctx:
+        ld, sg = _gpu_weights(ctx, fields, -1)
+        _check(ld, sg, ref, SPLIT_LD_RTOL, f"{prec} 16x16 M=40 B=128 n_wrap=32")
+        # G of the first and the last configuration of the batch (both ends of the tile walk)
+        import torch
+        d_s = torch.from_numpy(fields).cuda()
+        d_G = torch.zeros((B, m.N, m.N), dtype=torch.float64, device="cuda")
+        ctx.green_batch_dev(d_s, -1, 0, d_G)
+        ctx.sync()
+        for b in (0, B - 1):
+            _, _, Gref = O.weight(m, fields[b], -1, want_G=True)
+            err = float(np.abs(d_G[b].cpu().numpy() - Gref).max())
+            print(f"{prec} item {b}: max|dG| {err:.2e}")
+            assert err <= SPLIT_G_ATOL
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
+def test_benchmark_workload_size(prec):
+    """The benchmark's lattice and imaginary time: 16x16, beta = 8, dtau = 0.05
+    (M = 160), n_wrap = 32 (five blocks), both flavours, random fields."""
+    m = O.Model(16, 16, mu=-0.5, xi=1.0, beta=8.0, dtau=0.05, n_wrap=10)
+    B = 8
+    fields = batch_uniform(2402, B, m.M, m.N)
+    with _ctx(m, 32, prec, B) as ctx:
+        for eta in (1, -1):
+            ref = O.weight_many(m, fields, eta)
+            ld, sg = _gpu_weights(ctx, fields, eta)
+            _check(ld, sg, ref, SPLIT_LD_RTOL, f"{prec} 16x16 M=160 n_wrap=32 eta={eta}")
+
+
+def test_fp64_products_with_64x64_tiles():
+    """FP64 mode at B = 80: (256/64)^2 * 80 = 1280 >= 8 * 152 tiles, so the slice
+    products and the stabilisation GEMMs take the 64x64-tile FP64 kernel."""
+    m = O.Model(16, 16, mu=-0.5, xi=1.0, beta=1.0, dtau=0.05, n_wrap=10)
+    B = 80
+    fields = batch_uniform(2403, B, m.M, m.N)
+    ref = O.weight_many(m, fields, 1)
+    with _ctx(m, 10, "fp64", B) as ctx:
+        ld, sg = _gpu_weights(ctx, fields, 1)
+    _check(ld, sg, ref, FP64_LD_RTOL, "fp64 16x16 M=20 B=80")
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
+def test_split_mode_cumulative_chain(prec):
+    """Eq. 4 decisions on split-precision weights (12x12, N = 144: tensor-core slice
+    products and digit-split stabilisation).  H_eff is the bare Ising action, so log r is
+    the change of the fermion weight, of order one.  A decision is a margin event when
+    |log r - log u| is within twice the log-det bound applied to the fermion part of
+    log omega (both weights of log r carry that error); the oracle then takes the GPU's
+    outcome.  Every other decision, configuration and kept weight must agree."""
+    import torch
+    m = O.Model(12, 12, mu=-0.5, xi=1.0, beta=1.0, dtau=0.05, n_wrap=10, J=1.0, h=2.774)
+    kt = -0.5 * math.log(math.tanh(m.dtau * m.h))
+    J = np.array([-m.dtau * m.J / m.beta, 0.0, 0.0, -kt / m.beta])
+    B, steps, seed = 3, 10, 777
+    s0 = []
+    for b in range(B):
+        s, _, _ = O.eff_sweeps(m, uniform_field(3100 + b, m.M, m.N), CLASSES, J, 50, seed=31, step=b, direction=0)
+        s0.append(s)
+    s0 = np.stack(s0)
+    s_o = [s0[b].copy() for b in range(B)]
+    lw_o = [O.log_weight_total(m, s0[b]) for b in range(B)]
+    outside, margin_events, accepts = 0, 0, 0
+    with _ctx(m, 10, prec, B) as ctx:
+        ctx.set_effective_model(CLASSES, J)
+        d_s = torch.from_numpy(s0).cuda()
+        d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
+        ctx.log_weight_batch_dev(d_s, d_lw)
+        d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+        d_lr = torch.zeros(B, dtype=torch.float64, device="cuda")
+        for step in range(steps):
+            before = d_acc.cpu().numpy().copy()
+            ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, step, 1, d_acc, d_lr)
+            ctx.sync()
+            acc_g = d_acc.cpu().numpy() - before
+            lr_g = d_lr.cpu().numpy()
+            s_g = d_s.cpu().numpy()
+            lw_g = d_lw.cpu().numpy()
+            for b in range(B):
+                fermion = abs(lw_o[b] - O.log_bare_weight(m, s_o[b]))
+                margin = 2.0 * 2.0 * SPLIT_LD_RTOL * fermion
+                so, lwo, ao, lro, _, _ = O.cumulative_update(m, s_o[b], lw_o[b], CLASSES, J, 1,
+                                                             seed=seed + (b << 32), step=step)
+                lu = math.log(O.uniform(seed + (b << 32), 0, 0, step, 4))
+                assert abs(lr_g[b] - lro) <= margin, (step, b, lr_g[b], lro)
+                if abs(lr_g[b] - lu) <= margin:
+                    margin_events += 1
+                    s_o[b] = s_g[b].copy()
+                    lw_o[b] = O.log_weight_total(m, s_g[b])
+                    continue
+                outside += 1
+                accepts += ao
+                assert acc_g[b] == ao, (step, b, lr_g[b], lro, lu)
+                np.testing.assert_array_equal(s_g[b], so)
+                assert abs(lw_g[b] - lwo) <= 2.0 * SPLIT_LD_RTOL * fermion
+                s_o[b], lw_o[b] = so, lwo
+    print(f"{prec}: {outside} decisions compared, {accepts} accepted, {margin_events} margin events")
+    assert outside >= B * steps - 2
+    assert 0 < accepts < outside
+
+
+def test_local_sweeps_at_training_size():
+    """The training lattice of the benchmark: 8x8, beta = 8, dtau = 0.05 (M = 160),
+    n_wrap = 10; two chains, two sweeps each, bit-exact against the oracle."""
+    import torch
+    m = O.Model(8, 8, mu=-0.5, xi=1.0, beta=8.0, dtau=0.05, n_wrap=10, J=1.0, h=2.774)
+    B, seed = 2, 4711
+    fields = batch_uniform(2404, B, m.M, m.N)
+    from paper_1612_03804_gb300 import sldqmc
+    with sldqmc.Context(8, 8, mu=-0.5, xi=1.0, beta=8.0, dtau=0.05, n_wrap=10, J=1.0, h=2.774,
+                        max_batch=B) as ctx:
+        d_s = torch.from_numpy(fields).cuda()
+        st = ctx.local_sweep_batch_dev(d_s, seed, 0, 2)
+        out = d_s.cpu().numpy()
+    for b in range(B):
+        so, sto = O.local_sweep(m, fields[b], seed=seed + (b << 32), sweep0=0, n_sweeps=2)
+        assert sto["margin_events"] == 0 and st[b]["margin_events"] == 0
+        assert st[b]["accepted"] == sto["accepted"]
+        np.testing.assert_array_equal(out[b], so)
+        assert st[b]["max_drift"] < 1e-8

@@ -245,6 +245,94 @@ def test_bare_weight_brute_force():
     assert abs(O.log_bare_weight(m, s) - ref) < 1e-12
 
 
+
+def _tfim_trotter_factors(Lx, Ly, dtau, J, h):
+    """Trotter factors of the transverse-field Ising model H_s = -J sum_<ij> sz sz - h sum_i sx
+    (Eq. 6) on the 2^N spin basis, from scipy's matrix exponential of each term: the
+    full off-diagonal factor expm(dtau h sum_i sx_i) and the diagonal of
+    expm(dtau J sum_<ij> sz_i sz_j).  Basis index bit i set <=> s_i = -1."""
+    N = Lx * Ly
+    sx = np.array([[0.0, 1.0], [1.0, 0.0]])
+    Hx = np.zeros((2 ** N, 2 ** N))
+    for i in range(N):
+        # site i is bit i of the basis index: the kron order puts site N-1 first
+        op = np.array([[1.0]])
+        for j in reversed(range(N)):
+            op = np.kron(op, sx if j == i else np.eye(2))
+        Hx += op
+    Tx = sla.expm(dtau * h * Hx)
+    # periodic adjacency: ring adjacency in each direction (a length-2 ring links its pair twice,
+    # a length-1 ring not at all), A = A_x (x) I + I (x) A_y on site index x + Lx*y
+    def ring(L):
+        A = np.zeros((L, L))
+        if L > 1:
+            for a in range(L):
+                A[a, (a + 1) % L] += 1
+                A[a, (a - 1) % L] += 1
+        return A
+    A = np.kron(np.eye(Ly), ring(Lx)) + np.kron(ring(Ly), np.eye(Lx))
+    spins = np.array([[1 - 2 * ((k >> i) & 1) for i in range(N)] for k in range(2 ** N)], dtype=np.float64)
+    Hzz = 0.5 * np.einsum("ki,ij,kj->k", spins, A, spins)
+    zz = np.diag(sla.expm(np.diag(dtau * J * Hzz)))
+    return Tx, zz
+
+
+def _basis_index(row):
+    return int(sum(1 << i for i, v in enumerate(row) if v < 0))
+
+
+@pytest.mark.parametrize("Lx,Ly,M", [(3, 2, 3), (4, 1, 3)])
+def test_bare_weight_is_the_trotter_decomposition(Lx, Ly, M):
+    """phi(C) is, up to one configuration-independent constant, the product over slices of
+    <s_tau+1| expm(dtau h sum sx) |s_tau> expm(dtau J sum sz sz)[s_tau]: the Suzuki-Trotter
+    path weight of H_s (Eq. 6).  A wrong temporal coupling (sign, factor 2, cosh/sinh
+    swapped) or a missing spatial factor changes the ratio between configurations."""
+    dtau, J, h = 0.2, 0.7, 1.9
+    m = O.Model(Lx, Ly, beta=M * dtau, dtau=dtau, J=J, h=h)
+    Tx, zz = _tfim_trotter_factors(Lx, Ly, dtau, J, h)
+    rng = np.random.default_rng(5)
+    diffs = []
+    for _ in range(200):
+        s = rng.choice(np.array([-1, 1], dtype=np.int8), size=(m.M, m.N))
+        idx = [_basis_index(s[t]) for t in range(m.M)]
+        path = sum(math.log(Tx[idx[(t + 1) % m.M], idx[t]]) + math.log(zz[idx[t]]) for t in range(m.M))
+        diffs.append(O.log_bare_weight(m, s) - path)
+    diffs = np.array(diffs)
+    assert np.ptp(diffs) < 1e-11, np.ptp(diffs)
+    # the constant is the normalisation of a time link: <s|expm(dtau h sx)|s'> = A e^{Kt s s'}
+    # with A^2 = sinh cosh and e^{2 Kt} = cosh / sinh, so log phi - path = -M N log A
+    A = math.sqrt(math.sinh(dtau * h) * math.cosh(dtau * h))
+    assert abs(diffs[0] + m.M * m.N * math.log(A)) < 1e-11
+
+
+def test_bare_weight_time_link_ratio_is_tanh():
+    """Flipping one spin of a single-site chain breaks two time links: phi changes by the
+    square of the off-diagonal / diagonal element of expm(dtau h sx), tanh(dtau h)^2."""
+    dtau, h = 0.1, 2.774
+    m = O.Model(1, 1, beta=0.6, dtau=dtau, J=1.0, h=h)
+    T = sla.expm(dtau * h * np.array([[0.0, 1.0], [1.0, 0.0]]))
+    s = np.ones((m.M, 1), dtype=np.int8)
+    s2 = s.copy()
+    s2[2, 0] = -1
+    ratio = math.exp(O.log_bare_weight(m, s2) - O.log_bare_weight(m, s))
+    assert abs(ratio - (T[0, 1] / T[0, 0]) ** 2) < 1e-14
+
+
+def test_bare_weight_sums_to_trotter_partition_function():
+    """Summing phi(C) over all 2^(N M) configurations gives Tr[(Tx Z)^M] times the same
+    per-link constant (3x1 sites, 4 slices: 4096 configurations)."""
+    Lx, Ly, M, dtau, J, h = 3, 1, 4, 0.25, 0.8, 1.3
+    m = O.Model(Lx, Ly, beta=M * dtau, dtau=dtau, J=J, h=h)
+    Tx, zz = _tfim_trotter_factors(Lx, Ly, dtau, J, h)
+    Z_trotter = np.trace(np.linalg.matrix_power(Tx @ np.diag(zz), M))
+    tot = 0.0
+    for k in range(2 ** (m.N * m.M)):
+        s = np.array([1 - 2 * ((k >> b) & 1) for b in range(m.N * m.M)], dtype=np.int8).reshape(m.M, m.N)
+        tot += math.exp(O.log_bare_weight(m, s))
+    A = math.sqrt(math.sinh(dtau * h) * math.cosh(dtau * h))
+    assert abs(tot * A ** (m.N * m.M) / Z_trotter - 1.0) < 1e-12
+
+
 # ------------------------------------------------------------ local sweeps
 def _bruteforce_sweep(m, s, seed, sweep):
     """One local sweep where every ratio is a quotient of two full weights."""

@@ -6,6 +6,10 @@ synchronisation).  It must give the same result as the context-based
 sldqmc_weight_batch_dev, on two calls in a row (the second call reuses the
 static workspace the first one left behind).  This file is collected last."""
 import ctypes
+import json
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -52,3 +56,49 @@ def test_noalloc_rejects_problems_beyond_its_workspace():
     # 32x32 needs about 80 MB of workspace: rejected before any device work
     assert lib.sldqmc_weight_noalloc(ctypes.byref(p), None, ctypes.c_void_p(1), 1, -1, ctypes.c_void_p(1),
                                      None) == -6
+
+
+# Runs in a fresh interpreter: the allocation-free call is the first use of
+# the library there (no context was created before it), at a lattice size
+# whose LU panels need more than the default 48 KiB of shared memory.
+_FRESH = r"""
+import ctypes, json, sys
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_1612_03804_gb300 import sldqmc
+from paper_1612_03804_gb300.inputs import batch_uniform
+torch.cuda.set_device(0)
+lib = sldqmc.load()
+p = sldqmc.Params(16, 16, 1.0, -0.5, 1.0, 1.0, 0.05, 10, 1.0, 2.774, 0, 2)
+B, M, N = 2, 20, 256
+out = []
+for seed in (21, 22):
+    d_s = torch.from_numpy(batch_uniform(seed, B, M, N)).cuda()
+    ld = torch.full((B,), float("nan"), dtype=torch.float64, device="cuda")
+    sg = torch.zeros(B, dtype=torch.int32, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.sldqmc_weight_noalloc(ctypes.byref(p), st, ctypes.c_void_p(d_s.data_ptr()), B, -1,
+                                   ctypes.c_void_p(ld.data_ptr()), ctypes.c_void_p(sg.data_ptr()))
+    out.append({"rc": rc, "ld": ld.cpu().tolist(), "sg": sg.cpu().tolist()})
+print(json.dumps(out))
+"""
+
+
+def test_noalloc_first_call_in_fresh_process_16x16_matches_oracle():
+    from oracle import oracle as O
+    from paper_1612_03804_gb300 import build
+    from paper_1612_03804_gb300.inputs import batch_uniform
+
+    build.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    calls = json.loads(r.stdout.strip().splitlines()[-1])
+    m = O.Model(16, 16, t=1.0, mu=-0.5, xi=1.0, beta=1.0, dtau=0.05, n_wrap=10)
+    for call, seed in zip(calls, (21, 22)):
+        assert call["rc"] == 0, call
+        fields = batch_uniform(seed, 2, m.M, m.N)
+        for b in range(2):
+            ld, sg = O.weight(m, fields[b], -1)
+            assert call["sg"][b] == sg
+            assert abs(call["ld"][b] - ld) <= LD_RTOL * abs(ld), (call, ld)
