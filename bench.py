@@ -1,36 +1,54 @@
 #!/usr/bin/env python
-"""Benchmark of the self-learning DQMC hot path on GB300.
+"""Benchmark of the self-learning DQMC hot path on one GB300.
 
-Workload (the configuration the headline metric is quoted on): SLDQMC on a
-16x16 lattice, t=1, mu=-0.5, xi=1, beta=8, dtau=0.05 (M=160), n_wrap from the
-autotuner (paper_1612_03804_gb300/tune.py),
-bare Ising weight J=1, h=2.774; effective action with J1/J2/J3 (space) and
-J_tau couplings, fitted (Eq. 3) on local-DQMC configurations of an 8x8
-lattice at the same couplings and transferred to 16x16, as the paper does
-with its L=8 fit.
+Headline workload (the largest single-GPU configuration): one SLDQMC chain on
+a 100x100 periodic lattice (N = 10^4 sites), t=1, mu=-0.5, xi=1, beta=10,
+dtau=0.1 (M = 100 slices), n_wrap=10, dense exp(-dtau K) slice products in
+split-TF32 on the tensor cores with FP64-accurate stabilisation, bare Ising
+weight J=1, h=2.774; effective action with J1/J2/J3 (space) and J_tau
+couplings fitted (Eq. 3) on local-DQMC configurations of an 8x8 lattice at
+the same couplings and transferred to 100x100, as the paper transfers its
+L=8 fit.  Only the running U, D, V factors, the chain buffers and E stay in
+HBM (about 13 GB per flavour).
 
-Training (untimed): 8x8 chains are pre-thermalised by effective sweeps of
-the bare Ising action, run 20 local-DQMC sweeps, then contribute one
-configuration per sweep until 2000 are collected.  The 16x16 chains start in
-equilibrium of the fitted H_eff (300 effective sweeps) before the warm-up.
-
-One step = one cumulative update (steps iii+iv) of B independent chains:
-one sweep of N*M effective-model flips per chain, the exact log weight of
-every proposal (two flavours -> 2B fermion-weight evaluations through the
-stabilised B-chain) and the Eq. 4 acceptance.  The metric is fermion-weight
-evaluations per second (single-flavour det(1+B) evaluations) with the
-slice products in split-TF32 (mixed) precision; the FP64-product path and
-decorrelated samples/s are reported beside it.
+One step = one cumulative update (steps iii+iv): one sweep of N*M = 10^6
+effective-model flips, the exact log weight of the proposal (both flavours,
+i.e. two single-flavour fermion-weight evaluations through the stabilised
+B-chain) and the Eq. 4 acceptance.  value = fermion-weight evaluations/s.
+Beside it, in the same JSON line:
+  fp64           -- the FP64-product path on the same lattice, extrapolated
+                    from one timed block of n_wrap slices (labelled so);
+  precision      -- log|det| relative/absolute error and max|dG| of the
+                    benched mode against the uniform-field closed form;
+  roofline       -- the dominant kernel class of a profiled step against
+                    the peak of its own operand type (of measured);
+  e2e            -- the same metric through the host-buffer C call, with the
+                    copies inside the timed region;
+  cpu_baseline   -- the FP64 CPU oracle on all host cores, extrapolated from
+                    a timed sample of smaller weights by the N^3 M cost law;
+  workloads      -- the other configurations:
+     chains16  : 128 chains at 16x16, beta=8, dtau=0.05 (M=160), n_wrap by
+                 the autotuner, with its own FP64 arm, e2e, decorrelation
+                 and errors against the oracle on sampled configurations;
+     uneven    : 64 chains, L in {12,16,20,24,32}, beta in {4,8}, split-TF32,
+                 n_wrap per bucket by the autotuner, one CUDA graph per step,
+                 with its fill fraction;
+     precision : 32x32, beta=10, dtau=0.05 (M=200), n_wrap in {5,10,20},
+                 FP64 / split-TF32 / split-BF16 / BF16 products;
+     local4    : plain FP64 DQMC on 4x4 (weight, then local sweeps);
+     critical  : decorrelation at the paper's critical point (beta=1).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workloads large,chains16,uneven,precision,local4,critical]
 
 Under torchrun each rank runs its own chains (weak scaling, no data-path
-collective); the timed region is bracketed by a barrier and a device
-synchronisation and the time is the maximum over ranks.
+collective); every timed region is bracketed by a barrier and a device
+synchronisation and its time is the maximum over ranks.
 """
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -41,17 +59,25 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WL = dict(L=16, t=1.0, mu=-0.5, xi=1.0, beta=8.0, dtau=0.05, n_wrap=10, J=1.0, h=2.774)
+LARGE = dict(L=100, t=1.0, mu=-0.5, xi=1.0, beta=10.0, dtau=0.1, n_wrap=10, J=1.0, h=2.774)
+CH16 = dict(L=16, t=1.0, mu=-0.5, xi=1.0, beta=8.0, dtau=0.05, n_wrap=10, J=1.0, h=2.774)
 CLASSES = [[(1, 0, 0), (0, 1, 0)], [(1, 1, 0), (1, -1, 0)], [(2, 0, 0), (0, 2, 0)], [(0, 0, 1)]]
 METRIC = "fermion-weight evals/s and decorrelated samples/s, mixed vs FP64, 1 GB300"
 UNIT = "weight evals/s"
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}  # TFLOP/s, dense, per GPU
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+MMAS = {"3xtf32": 5, "bf16x3": 6, "bf16": 1}
+ALL_WORKLOADS = ("large", "chains16", "uneven", "precision", "local4", "critical")
+# oracle sample for the CPU baseline and the reference arm: single-flavour
+# weights at 16x16 with the headline's beta, dtau and n_wrap
+CPU_SAMPLE = dict(L=16, beta=10.0, dtau=0.1, n_wrap=10)
 
 
-def workload_name():
-    return ("SLDQMC cumulative update, 16x16 lattice, beta=8, dtau=0.05 (M=160), mu=-0.5, xi=1, "
-            "J1/J2/J3/Jtau effective action")
+def workload_name(wl=LARGE):
+    M = int(round(wl["beta"] / wl["dtau"]))
+    return (f"SLDQMC cumulative update, {wl['L']}x{wl['L']} lattice (N={wl['L'] ** 2}), beta={wl['beta']:g}, "
+            f"dtau={wl['dtau']:g} (M={M}), n_wrap={wl['n_wrap']}, mu={wl['mu']:g}, xi={wl['xi']:g}, "
+            "dense exp(-dtau K), J1/J2/J3/Jtau effective action")
 
 
 def env_rank():
@@ -143,15 +169,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_record(kernel_class):
-    """Per-launch DRAM traffic of a kernel class from a committed ncu summary,
-    valid only while the sources it depends on (the kernel, and the code that
-    decides which launches it gets) are unchanged."""
+def traffic_record(kernel_class, workload="chains16"):
+    """Per-launch DRAM traffic of a kernel class on a workload from a committed
+    ncu summary, valid only while the sources it depends on (the kernel, and
+    the code that decides which launches it gets) are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        d = json.load(open(path)).get(kernel_class)
+        d = json.load(open(path)).get(workload, {}).get(kernel_class)
         if not d:
             return None
         h = hashlib.sha256()
@@ -162,6 +188,52 @@ def traffic_record(kernel_class):
         return d
     except Exception:
         return None
+
+
+def roofline_entry(prof, prec, pk, workload):
+    """Roofline of the dominant kernel class of a profiled step.
+
+    achieved = algorithmic flops of the class (2 N^3 per slice product; the
+    FP64-equivalent flops of the digit-split products) / summed CUDA-event
+    time of its launches.  peak = the measured peak of the operand type the
+    class computes in: TF32 (measured BF16 x 1100/2250) for split-TF32 slice
+    products, BF16 for split-BF16 / BF16 products and for the digit-split
+    products (BF16 integer digits), FP64 (x 1.25/2250) for the FP64 pipe.
+    issue_efficiency divides instead by that peak over the MMAs one
+    algorithmic product issues (5 split-TF32, 6 split-BF16, 36 digit
+    products)."""
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    rec = prof[dom]
+    achieved = rec["flops"] / (rec["ms"] * 1e-3) / 1e12 if rec["ms"] > 0 and rec["flops"] > 0 else None
+    issue = None
+    if dom == "gemm_tc":
+        base = pk["tf32_tflops"] if prec == "3xtf32" else pk["bf16_tflops"]
+        dtype = "tf32" if prec == "3xtf32" else "bf16"
+        bound, peak, per = "tensor", base, MMAS.get(prec, 1)
+        note = (f"{prec} slice products: algorithmic 2N^3 per product against the {dtype.upper()} peak; "
+                f"issue_efficiency against {dtype.upper()} peak / {per} MMAs per product")
+    elif dom == "gemm_oz":
+        bound, peak, per, dtype = "tensor", pk["bf16_tflops"], 36, "bf16"
+        note = ("FP64-accurate digit-split products (Gram, Cholesky-QR updates and panels, R2R1, V update, "
+                "LU updates): FP64-equivalent flops against the BF16 peak; issue_efficiency against "
+                "BF16 peak / 36 digit products")
+    else:
+        bound, peak, per, dtype = "alu", pk["fp64_tflops"], 1, "fp64"
+        note = "FP64 pipe (nominal FP64 rate scaled from the measured BF16 peak)"
+    if achieved and per > 1:
+        issue = achieved / (peak / per)
+    tr = traffic_record(dom, workload)
+    return {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "dtype": dtype,
+            "issue_efficiency": issue, "mmas_per_product": per,
+            "traffic": tr["bytes_per_launch"] if tr else None,
+            "peak_source": f"{pk['source']} (fp64 = bf16 x 1.25/2250, tf32 = bf16 x 1100/2250 nominal ratios), of measured",
+            "peak_note": note,
+            "launches": rec["launches"], "ms_per_launch": rec["ms"] / max(rec["launches"], 1),
+            "share": rec["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-30),
+            "breakdown_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+            "breakdown_tflops": {k: (v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 and v["flops"] > 0
+                                     else None) for k, v in prof.items()}}
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -179,61 +251,104 @@ def weak_scaling_value(units_per_rank, world, t_max):
     return units_per_rank * world / t_max
 
 
-def oracle_weight_sample(seed=1):
-    """One single-flavour weight evaluation of the workload by the FP64 CPU
-    oracle (as it stands, with the workload's n_wrap)."""
+def weight_work(N, M, n_wrap):
+    """Algorithmic flops of one single-flavour weight: dense slice products
+    2 M N^3, one stabilisation of about 3.67 N^3 per block, the LU (2/3) N^3."""
+    return 2.0 * M * N ** 3 + math.ceil(M / n_wrap) * 3.67 * N ** 3 + (2.0 / 3.0) * N ** 3
+
+
+def closed_form_logdet(L, beta, t, mu_eff):
+    """log det(1 + e^{-beta (K - shift)}) of the uniform field: sum_k log(1 + e^{-beta (eps_k - mu_eff)})."""
+    import numpy as np
+    k = 2 * np.pi * np.arange(L) / L
+    eps = (-2 * t * (np.cos(k)[None, :] + np.cos(k)[:, None])).ravel() - mu_eff
+    return float(np.sum(np.logaddexp(0.0, -beta * eps)))
+
+
+def closed_form_green_row(L, beta, t, mu_eff):
+    """g[dy, dx] with G_ij = g(r_i - r_j) for the uniform field: the inverse
+    Fourier transform of 1 / (1 + e^{-beta (eps_k - mu_eff)}) on the L x L torus."""
+    import numpy as np
+    k = 2 * np.pi * np.arange(L) / L
+    eps = -2 * t * (np.cos(k)[None, :] + np.cos(k)[:, None]) - mu_eff
+    occ = 1.0 / (1.0 + np.exp(np.clip(-beta * eps, -700, 700)))
+    return np.real(np.fft.ifft2(occ))
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample_rate(n_weights, seed=1):
+    """The FP64 CPU oracle as it stands, timed on every host core: n_weights
+    independent single-flavour weight evaluations of the CPU_SAMPLE lattice,
+    one per process.  Returns (weights/s at the sample size, cores, seconds)."""
     from oracle import oracle as O
-    from paper_1612_03804_gb300.inputs import uniform_field
-    m = O.Model(WL["L"], WL["L"], t=WL["t"], mu=WL["mu"], xi=WL["xi"], beta=WL["beta"], dtau=WL["dtau"],
-                n_wrap=WL["n_wrap"], J=WL["J"], h=WL["h"])
-    s = uniform_field(seed, m.M, m.N)
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    O.build()
+    c = CPU_SAMPLE
+    m = O.Model(c["L"], c["L"], t=1.0, mu=-0.5, xi=1.0, beta=c["beta"], dtau=c["dtau"], n_wrap=c["n_wrap"])
+    fields = batch_uniform(seed, n_weights, m.M, m.N)
+    cores = len(os.sched_getaffinity(0))
     t0 = time.perf_counter()
-    O.weight(m, s, -1)
-    return time.perf_counter() - t0
+    O.weight_many(m, fields, -1, workers=cores)
+    dt = time.perf_counter() - t0
+    return n_weights / dt, min(cores, n_weights), dt
+
+
+def extrapolate_oracle(rate, wl):
+    """Scale an oracle rate at CPU_SAMPLE to the workload by the cost law
+    M N^3 of its dense products and per-slice Householder QR."""
+    c = CPU_SAMPLE
+    Ns, Ms = c["L"] ** 2, int(round(c["beta"] / c["dtau"]))
+    N, M = wl["L"] ** 2, int(round(wl["beta"] / wl["dtau"]))
+    return rate * (Ns / N) ** 3 * (Ms / M)
 
 
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    from oracle import oracle as O
-    O.build()
+    cores = len(os.sched_getaffinity(0))
     for w in range(args.warmup):
-        oracle_weight_sample(100 + w)
-    t0 = time.perf_counter()
+        oracle_sample_rate(cores, seed=100 + w)
+    t_tot = 0.0
     for k in range(args.steps):
-        oracle_weight_sample(200 + k)
-    T = time.perf_counter() - t0
-    value = args.steps / T
-    sample = "one single-flavour weight evaluation (16x16, M=160, n_wrap=10) per step, FP64 CPU oracle"
+        _, _, dt = oracle_sample_rate(cores, seed=200 + k)
+        t_tot += dt
+    rate = args.steps * cores / t_tot
+    value = extrapolate_oracle(rate, LARGE)
+    c = CPU_SAMPLE
+    sample = (f"each step: {cores} independent single-flavour weight evaluations ({c['L']}x{c['L']}, "
+              f"beta={c['beta']:g}, dtau={c['dtau']:g}, n_wrap={c['n_wrap']}) by the FP64 CPU oracle, one per "
+              f"host core; {rate:.4g} weights/s there, extrapolated to 100x100, M=100 by the M N^3 cost law "
+              "(labelled extrapolated)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": workload_name(), "global_batch": 1, "seq_len": 160,
-                                           "parallelism": "cpu-1-thread"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "data": "synthetic", "extrapolated": True,
+           "config": {"workload": workload_name(LARGE), "global_batch": 1, "seq_len": 100,
+                      "parallelism": f"cpu-{cores}-processes"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def bare_couplings():
+# ---------------------------------------------------------------- helpers
+def bare_couplings(wl):
     """The bare Ising action log phi as an effective model over the same classes:
     -beta H = dtau J f_1 + K_tau f_tau, K_tau = -ln tanh(dtau h) / 2."""
-    import math
-    kt = -0.5 * math.log(math.tanh(WL["dtau"] * WL["h"]))
-    return [-WL["dtau"] * WL["J"] / WL["beta"], 0.0, 0.0, -kt / WL["beta"]]
+    kt = -0.5 * math.log(math.tanh(wl["dtau"] * wl["h"]))
+    return [-wl["dtau"] * wl["J"] / wl["beta"], 0.0, 0.0, -kt / wl["beta"]]
 
 
-def train_effective_model(torch, sldqmc, args, dev_seed):
+def train_effective_model(torch, sldqmc, wl, args, dev_seed, n_wrap=None):
     """Steps i-ii: local DQMC on 8x8 at the workload couplings (started from
     configurations pre-thermalised under the bare Ising action), then the Eq. 3 fit."""
     import numpy as np
     from paper_1612_03804_gb300.inputs import batch_uniform
     Bt = args.train_chains
-    ctx8 = sldqmc.Context(8, 8, t=WL["t"], mu=WL["mu"], xi=WL["xi"], beta=WL["beta"], dtau=WL["dtau"],
-                          n_wrap=WL["n_wrap"], J=WL["J"], h=WL["h"], prec="fp64", max_batch=Bt)
+    ctx8 = sldqmc.Context(8, 8, t=wl["t"], mu=wl["mu"], xi=wl["xi"], beta=wl["beta"], dtau=wl["dtau"],
+                          n_wrap=n_wrap or wl["n_wrap"], J=wl["J"], h=wl["h"], prec="fp64", max_batch=Bt)
     s = torch.from_numpy(batch_uniform(dev_seed, Bt, ctx8.M, ctx8.N)).cuda()
-    ctx8.set_effective_model(CLASSES, np.array(bare_couplings()))
+    ctx8.set_effective_model(CLASSES, np.array(bare_couplings(wl)))
     for k in range(args.bare_sweeps):
         ctx8.eff_sweeps_batch_dev(s, 1, dev_seed, k, -1)
     ctx8.local_sweep_batch_dev(s, dev_seed, 0, args.thermalize, want_stats=False)
@@ -243,89 +358,19 @@ def train_effective_model(torch, sldqmc, args, dev_seed):
         ctx8.local_sweep_batch_dev(s, dev_seed, sweep, 1, want_stats=False)
         sweep += 1
         cfgs.append(s.cpu().numpy().copy())
-    import numpy as np
     cfgs = np.concatenate(cfgs)[: args.train_configs]
     J, E0, r2 = ctx8.fit_effective_action(cfgs)
     ctx8.close()
     return J, E0, r2, len(cfgs)
 
 
-def critical_point_context(torch, sldqmc, args, rank):
-    """Decorrelation at the paper's finite-temperature critical point (beta=1,
-    dtau=0.05, M=20, h=2.774, 16x16; fit on 8x8 as in the paper): acceptance and
-    tau_int of |sum s| for 16 chains over args.tau_steps cumulative updates, with
-    1, 10 and 100 effective-model sweeps per update (the paper moves the
-    proposal through many effective sweeps so that one exact accept step
-    decorrelates the chain)."""
-    import math
-    import numpy as np
-    from paper_1612_03804_gb300.analysis import tau_int
-    from paper_1612_03804_gb300.inputs import batch_uniform
-    wl = dict(WL, beta=1.0)
-    kt = -0.5 * math.log(math.tanh(wl["dtau"] * wl["h"]))
-    bare = np.array([-wl["dtau"] * wl["J"] / wl["beta"], 0.0, 0.0, -kt / wl["beta"]])
-    Bt = args.train_chains
-    c8 = sldqmc.Context(8, 8, t=wl["t"], mu=wl["mu"], xi=wl["xi"], beta=wl["beta"], dtau=wl["dtau"], n_wrap=20,
-                        J=wl["J"], h=wl["h"], prec="fp64", max_batch=Bt)
-    s = torch.from_numpy(batch_uniform(8100 + rank, Bt, c8.M, c8.N)).cuda()
-    c8.set_effective_model(CLASSES, bare)
-    for k in range(args.bare_sweeps):
-        c8.eff_sweeps_batch_dev(s, 1, 81, k, -1)
-    c8.local_sweep_batch_dev(s, 81, 0, args.thermalize, want_stats=False)
-    cfgs, sw = [], args.thermalize
-    while len(cfgs) * Bt < args.train_configs:
-        c8.local_sweep_batch_dev(s, 81, sw, 1, want_stats=False)
-        sw += 1
-        cfgs.append(s.cpu().numpy().copy())
-    J, E0, r2 = c8.fit_effective_action(np.concatenate(cfgs)[: args.train_configs])
-    c8.close()
-    B = min(args.tau_chains, args.batch)
-    ctx = sldqmc.Context(wl["L"], wl["L"], t=wl["t"], mu=wl["mu"], xi=wl["xi"], beta=wl["beta"], dtau=wl["dtau"],
-                         n_wrap=20, J=wl["J"], h=wl["h"], prec=args.prec, max_batch=B)
-    ctx.set_effective_model(CLASSES, J, E0)
-    d_s = torch.from_numpy(batch_uniform(8200 + rank, B, ctx.M, ctx.N)).cuda()
-    for k in range(args.eff_thermalize):
-        ctx.eff_sweeps_batch_dev(d_s, 1, 82, k, -1)
-    d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
-    ctx.log_weight_batch_dev(d_s, d_lw)
-    d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
-    for w in range(args.warmup):
-        ctx.cumulative_batch_dev(d_s, d_lw, 1, 83, w, 1, d_acc)
-    # the same equilibrated start for every number of effective sweeps per update
-    s0, lw0 = d_s.clone(), d_lw.clone()
-    scan = []
-    for n_eff in (1, 10, 100):
-        d_s.copy_(s0)
-        d_lw.copy_(lw0)
-        d_acc.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        series = magnetisation_series(torch, ctx, d_s, d_lw, d_acc, 83 + n_eff, 100, args.tau_steps,
-                                      n_eff).astype(np.float64)
-        dt = time.perf_counter() - t0
-        tau, window = tau_int(series)
-        scan.append({"n_eff": n_eff, "accept_rate": float(d_acc.sum().item()) / (B * args.tau_steps),
-                     "tau_int": tau, "tau_window": window, "steps_per_s": args.tau_steps / dt,
-                     "decorrelated_samples_per_s": B * args.tau_steps / dt / tau,
-                     "note": ("window reached" if window < args.tau_steps - 1 else
-                              "window not reached: tau_int is a lower bound")})
-    ctx.close()
-    first = scan[0]
-    return {"point": "16x16, beta=1, dtau=0.05 (M=20), h=2.774, mu=-0.5 (the paper's critical point), "
-                     f"{B} chains, effective model fitted on 8x8 (R^2={r2:.6f})",
-            "accept_rate": first["accept_rate"], "tau_int": first["tau_int"],
-            "tau_window": first["tau_window"], "tau_steps": args.tau_steps,
-            "steps_per_s": first["steps_per_s"],
-            "n_eff_scan": scan}
-
-
-def steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, step0, K):
+def steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, step0, K, n_eff=1):
     st = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for k in range(K):
-        ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, step0 + k, 1, d_acc)
+        ctx.cumulative_batch_dev(d_s, d_lw, n_eff, seed, step0 + k, 1, d_acc)
     e1.record(st)
     e1.synchronize()
     return e0.elapsed_time(e1) / 1e3
@@ -341,213 +386,585 @@ def magnetisation_series(torch, ctx, d_s, d_lw, d_acc, seed, step0, K, n_eff=1):
     return out.cpu().numpy()
 
 
-def run_ours(args):
+def make_ctx(sldqmc, wl, prec, B, n_wrap, J=None, E0=0.0, beta=None):
+    c = sldqmc.Context(wl["L"], wl["L"], t=wl["t"], mu=wl["mu"], xi=wl["xi"], beta=beta or wl["beta"],
+                       dtau=wl["dtau"], n_wrap=n_wrap, J=wl["J"], h=wl["h"], prec=prec, max_batch=B)
+    if J is not None:
+        c.set_effective_model(CLASSES, J, E0)
+    return c
+
+
+class Env:
+    """Per-process state shared by the workloads: torch, the binding, the
+    process group and the timing helpers."""
+
+    def __init__(self, args):
+        import torch
+        self.args = args
+        self.torch = torch
+        self.rank, self.world, self.local = env_rank()
+        torch.cuda.set_device(self.local)
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+            self.dist = dist
+        if self.rank == 0:
+            import __graft_entry__
+            __graft_entry__.build()
+        if self.dist:
+            self.dist.barrier()
+        from paper_1612_03804_gb300 import sldqmc
+        self.sldqmc = sldqmc
+        sldqmc.load()
+
+    def barrier_sync(self):
+        self.torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+        self.torch.cuda.synchronize()
+
+    def rank_max(self, x):
+        return max_over_ranks(x, self.dist, "cuda")
+
+
+# --------------------------------------------------------- headline: 100x100
+def run_large(env):
+    """Config 5: one chain on 100x100, the headline line."""
     import numpy as np
-    import torch
-    rank, world, local = env_rank()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    if rank == 0:
-        import __graft_entry__
-        __graft_entry__.build()
-    if dist:
-        dist.barrier()
-    from paper_1612_03804_gb300 import sldqmc
-    from paper_1612_03804_gb300.analysis import tau_int
-    from paper_1612_03804_gb300.inputs import batch_uniform
-    sldqmc.load()
-
-    def barrier_sync():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def rank_max(x):
-        return max_over_ranks(x, dist, "cuda")
-
+    from paper_1612_03804_gb300.inputs import uniform_field
+    torch, sldqmc, args = env.torch, env.sldqmc, env.args
+    wl = LARGE
+    N, M, nw = wl["L"] ** 2, int(round(wl["beta"] / wl["dtau"])), wl["n_wrap"]
+    B = 1
     t_setup = time.perf_counter()
     if args.no_train:
-        J, E0, r2, ncfg = bare_couplings(), 0.0, None, 0
+        J, E0, r2, ncfg = bare_couplings(wl), 0.0, None, 0
     else:
-        J, E0, r2, ncfg = train_effective_model(torch, sldqmc, args, 7000 + rank)
-    t_setup = time.perf_counter() - t_setup
-    B = args.batch
-    seed = 123456789 + (rank << 20)
-    nwrap = {}
-    tune_log = {}
-    for prec in {args.prec, "fp64"}:
-        if args.n_wrap == "auto":
-            from paper_1612_03804_gb300.tune import autotune_nwrap
-            nwrap[prec], res = autotune_nwrap(WL["L"], WL["beta"], WL["dtau"], WL["mu"], prec, t=WL["t"], xi=WL["xi"])
-            tune_log[prec] = [[r[0], round(r[1], 2), r[2]] for r in res]
-        else:
-            nwrap[prec] = int(args.n_wrap)
-
-    def make_ctx(prec):
-        c = sldqmc.Context(WL["L"], WL["L"], t=WL["t"], mu=WL["mu"], xi=WL["xi"], beta=WL["beta"],
-                           dtau=WL["dtau"], n_wrap=nwrap[prec], J=WL["J"], h=WL["h"], prec=prec, max_batch=B)
-        c.set_effective_model(CLASSES, J, E0)
-        return c
-
-    ctx = make_ctx(args.prec)
-    V = ctx.V
-    d_s = torch.from_numpy(batch_uniform(5000 + rank, B, ctx.M, ctx.N)).cuda()
+        J, E0, r2, ncfg = train_effective_model(torch, sldqmc, wl, args, 9000 + env.rank)
+    ctx = make_ctx(sldqmc, wl, args.prec, B, nw, J, E0)
+    seed = 987654321 + (env.rank << 20)
+    d_s = torch.from_numpy(uniform_field(5100 + env.rank, M, N)[None]).cuda()
     d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
     d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
-    # start the chains in equilibrium of H_eff (cheap effective sweeps), where
-    # the fitted model is accurate, then compute their exact log weights
-    for k in range(args.eff_thermalize):
+    for k in range(args.large_eff_thermalize):
         ctx.eff_sweeps_batch_dev(d_s, 1, seed ^ 0x5A5A, k, -1)
     ctx.log_weight_batch_dev(d_s, d_lw)
     ctx.sync()
-    # warm-up cumulative updates
+    t_setup = time.perf_counter() - t_setup
     for w in range(args.warmup):
         ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, w, 1, d_acc)
     ctx.sync()
     d_acc.zero_()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(env.local)
     sampler.start()
     n0 = ctx.kernel_launches()
-    barrier_sync()
+    env.barrier_sync()
     T = steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, args.warmup, args.steps)
-    barrier_sync()
+    env.barrier_sync()
     launches = ctx.kernel_launches() - n0
     clocks = sampler.stop()
     ctx.sync()
-    Tmax = rank_max(T)
-    value = weak_scaling_value(2 * B * args.steps, world, Tmax)
+    Tmax = env.rank_max(T)
+    value = weak_scaling_value(2 * B * args.steps, env.world, Tmax)
     accept_rate = float(d_acc.sum().item()) / (B * args.steps)
-    # decorrelation: |magnetisation| series of a separate set of chains (fewer
-    # chains, more steps; the per-chain dynamics does not depend on the batch)
-    tau, window, tau_note = None, None, None
-    samples_per_s = None
+
+    # roofline: one profiled step (CUDA events around every launch; flavours serialised)
+    ctx.profile(True)
+    ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, 1, d_acc)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    pk = peaks()
+    roof = roofline_entry(prof, args.prec, pk, "large")
+    roof["serialised_step_ms"] = sum(v["ms"] for v in prof.values())
+
+    # error of the benched mode: the uniform field has a closed form (the
+    # oracle's dense FP64 at N = 10^4, ~10^14 flops per weight, is beyond the
+    # host cores); eta = -1, s = +1 shifts mu by -xi
+    u = torch.ones((1, M, N), dtype=torch.int8, device="cuda")
+    ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.weight_batch_dev(u, -1, ld)
+    G = torch.zeros((1, N, N), dtype=torch.float64, device="cuda")
+    ctx.green_batch_dev(u, -1, 0, G)
+    ctx.sync()
+    mu_eff = wl["mu"] - wl["xi"]
+    cf = closed_form_logdet(wl["L"], wl["beta"], wl["t"], mu_eff)
+    g = torch.from_numpy(closed_form_green_row(wl["L"], wl["beta"], wl["t"], mu_eff)).cuda()
+    L = wl["L"]
+    idx = torch.arange(N, device="cuda")
+    x, y = idx % L, idx // L
+    dG = 0.0
+    for r0 in range(0, N, 1000):
+        rows = idx[r0:r0 + 1000]
+        ref = g[(y[rows, None] - y[None, :]) % L, (x[rows, None] - x[None, :]) % L]
+        dG = max(dG, float((G[0, r0:r0 + 1000] - ref).abs().max()))
+    precision = {"reference": "uniform-field closed form sum_k log(1+e^{-beta(eps_k-mu+xi)}) and its "
+                              "translation-invariant G (eta=-1, s=+1)",
+                 "logdet": float(ld.item()), "closed_form": cf,
+                 "logdet_rel_err": abs(float(ld.item()) - cf) / abs(cf),
+                 "logdet_abs_err": abs(float(ld.item()) - cf), "max_abs_dG": dG,
+                 "bound": "1e-6 relative (log det), stated per result"}
+    del G
+
+    # end to end through the host-buffer C call (copies inside the timed region)
+    h_s = torch.empty((B, M, N), dtype=torch.int8).pin_memory()
+    h_s.copy_(d_s.cpu())
+    h_lw = torch.empty(B, dtype=torch.float64).pin_memory()
+    h_lw.copy_(d_lw.cpu())
+    h_acc = np.zeros(B, dtype=np.int32)
+    hs, hl = h_s.numpy(), h_lw.numpy()
+    Ke = max(2, args.steps // 5)
+    env.barrier_sync()
+    t0 = time.perf_counter()
+    for k in range(Ke):
+        ctx.cumulative_batch(hs, hl, 1, seed, 2 * 10 ** 6 + k, 1, h_acc)
+    torch.cuda.synchronize()
+    Te = env.rank_max(time.perf_counter() - t0)
+    e2e = {"value": 2 * B * Ke * env.world / Te, "unit": UNIT, "steps": Ke,
+           "h2d_bytes_per_step": B * M * N + 8 * B, "d2h_bytes_per_step": B * M * N + 8 * B + 4 * B}
+    ctx.close()
+    del d_s, u
+
+    # FP64-product path: one block of n_wrap slices (a beta = n_wrap dtau chain:
+    # products, one stabilisation, the LU) timed, times the M / n_wrap blocks
+    fp64 = None
+    if not args.skip_fp64:
+        c64 = make_ctx(sldqmc, wl, "fp64", 1, nw, beta=nw * wl["dtau"])
+        s1 = torch.from_numpy(uniform_field(5200, nw, N)[None]).cuda()
+        l1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        env.barrier_sync()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        c64.weight_batch_dev(s1, -1, l1)
+        e1.record(st)
+        c64.sync()
+        t_block = env.rank_max(e0.elapsed_time(e1) / 1e3)
+        c64.close()
+        t_w = t_block * (M // nw)
+        fp64 = {"value": env.world / t_w, "unit": UNIT, "extrapolated": True,
+                "s_per_block": t_block, "s_per_weight": t_w,
+                "note": f"one block of {nw} FP64 slice products + stabilisation + LU timed, x {M // nw} blocks"}
+
+    cpu = None
+    if env.rank == 0 and not args.skip_cpu:
+        cores = len(os.sched_getaffinity(0))
+        rate, used, dt = oracle_sample_rate(cores, seed=1)
+        c = CPU_SAMPLE
+        cpu = {"value": extrapolate_oracle(rate, wl), "unit": UNIT, "cores": used, "kind": "oracle",
+               "extrapolated": True,
+               "sample": (f"{cores} independent single-flavour weights ({c['L']}x{c['L']}, beta={c['beta']:g}, "
+                          f"dtau={c['dtau']:g}, n_wrap={c['n_wrap']}) by the FP64 CPU oracle, one per host core, "
+                          f"{dt:.1f} s: {rate:.4g} weights/s, scaled to 100x100, M=100 by the M N^3 cost law")}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": env.world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * Tmax / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "tf32x2/fp32-acc products, f64 stabilisation" if args.prec == "3xtf32" else args.prec,
+           "data": "synthetic (seeded random fields; effective model fitted on seeded local-DQMC runs)",
+           "config": {"workload": workload_name(wl), "global_batch": B * env.world, "seq_len": M,
+                      "lattice": f"{wl['L']}x{wl['L']}", "chains_per_gpu": B, "precision": args.prec,
+                      "n_wrap": nw, "parallelism": f"replicas x{env.world}",
+                      "l2": "working set > L2 (each N x N FP64 matrix is 800 MB; no flush)",
+                      "fit": {"lattice": "8x8", "configs": ncfg, "J": [float(x) for x in J], "E0": E0, "r2": r2},
+                      "setup_s": round(t_setup, 2)},
+           "ms_per_weight": 1e3 * Tmax / (2 * B * args.steps),
+           "ms_per_accept_step": 1e3 * Tmax / args.steps,
+           "accept_rate": accept_rate, "fp64": fp64, "precision": precision,
+           "decorrelated_samples_per_s": None,
+           "decorrelation_note": ("tau_int needs a series of many cumulative steps (seconds each at 100x100); "
+                                  "it is measured on the chains16 workload (workloads.chains16)"),
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
+    return out
+
+
+# ------------------------------------------------ 16x16 x 128 chains (config 2)
+def oracle_errors(torch, ctx, d_s, m_kw, n_sample):
+    """Errors of the context's mode against the FP64 CPU oracle on the first
+    n_sample configurations of d_s (both flavours), and max|dG| on the first."""
+    import numpy as np
+    from oracle import oracle as O
+    fields = d_s[:n_sample].cpu().numpy()
+    m = O.Model(**m_kw)
+    rel, ab = [], []
+    for eta in (1, -1):
+        ref = O.weight_many(m, fields, eta)
+        ld = torch.zeros(n_sample, dtype=torch.float64, device="cuda")
+        ctx.weight_batch_dev(d_s[:n_sample], eta, ld)
+        ctx.sync()
+        ld = ld.cpu().numpy()
+        r = np.array([x[0] for x in ref])
+        rel.append(np.abs(ld - r) / np.abs(r))
+        ab.append(np.abs(ld - r))
+    _, _, Gref = O.weight(m, fields[0], -1, want_G=True)
+    G = torch.zeros((1, m.N, m.N), dtype=torch.float64, device="cuda")
+    ctx.green_batch_dev(d_s[:1], -1, 0, G)
+    ctx.sync()
+    return {"reference": f"FP64 CPU oracle (n_wrap={m.n_wrap}), {n_sample} sampled chain configurations, both flavours",
+            "logdet_rel_err": float(np.max(rel)), "logdet_abs_err": float(np.max(ab)),
+            "max_abs_dG": float(np.abs(G[0].cpu().numpy() - Gref).max())}
+
+
+def run_chains16(env):
+    import numpy as np
+    from paper_1612_03804_gb300.analysis import tau_int
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    torch, sldqmc, args = env.torch, env.sldqmc, env.args
+    wl = CH16
+    t_setup = time.perf_counter()
+    if args.no_train:
+        J, E0, r2, ncfg = bare_couplings(wl), 0.0, None, 0
+    else:
+        J, E0, r2, ncfg = train_effective_model(torch, sldqmc, wl, args, 7000 + env.rank)
+    t_setup = time.perf_counter() - t_setup
+    B = args.batch
+    seed = 123456789 + (env.rank << 20)
+    nwrap, tune_log = {}, {}
+    for prec in {args.prec, "fp64"}:
+        if args.n_wrap == "auto":
+            from paper_1612_03804_gb300.tune import autotune_nwrap
+            nwrap[prec], res = autotune_nwrap(wl["L"], wl["beta"], wl["dtau"], wl["mu"], prec, t=wl["t"], xi=wl["xi"])
+            tune_log[prec] = [[r[0], round(r[1], 2), r[2]] for r in res]
+        else:
+            nwrap[prec] = int(args.n_wrap)
+    ctx = make_ctx(sldqmc, wl, args.prec, B, nwrap[args.prec], J, E0)
+    d_s = torch.from_numpy(batch_uniform(5000 + env.rank, B, ctx.M, ctx.N)).cuda()
+    d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
+    d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+    for k in range(args.eff_thermalize):
+        ctx.eff_sweeps_batch_dev(d_s, 1, seed ^ 0x5A5A, k, -1)
+    ctx.log_weight_batch_dev(d_s, d_lw)
+    ctx.sync()
+    for w in range(args.warmup):
+        ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, w, 1, d_acc)
+    ctx.sync()
+    d_acc.zero_()
+    K = args.steps
+    n0 = ctx.kernel_launches()
+    env.barrier_sync()
+    T = steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, args.warmup, K)
+    env.barrier_sync()
+    launches = ctx.kernel_launches() - n0
+    Tmax = env.rank_max(T)
+    value = weak_scaling_value(2 * B * K, env.world, Tmax)
+    accept_rate = float(d_acc.sum().item()) / (B * K)
+
+    # decorrelation: |magnetisation| series of 16 of the chains, long enough
+    # for the Madras-Sokal window
+    tau = window = tau_note = samples_per_s = None
     if args.tau_steps > 0:
         Bt = min(args.tau_chains, B)
-        t_s = d_s[:Bt].clone()
-        t_lw = d_lw[:Bt].clone()
+        t_s, t_lw = d_s[:Bt].clone(), d_lw[:Bt].clone()
         t_acc = torch.zeros(Bt, dtype=torch.int32, device="cuda")
         series = magnetisation_series(torch, ctx, t_s, t_lw, t_acc, seed ^ 0x77, 10 ** 5,
                                       args.tau_steps).astype(np.float64)
         tau, window = tau_int(series)
         tau_note = ("window reached" if window < args.tau_steps - 1 else
                     "window not reached: tau_int is a lower bound, samples/s an upper bound")
-        samples_per_s = (B * world * args.steps / Tmax) / tau
+        samples_per_s = (B * env.world * K / Tmax) / tau
 
-    # roofline: a profiled pass (CUDA events around every launch)
     ctx.profile(True)
-    ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, args.profile_steps, d_acc)
+    ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, 1, d_acc)
     prof = ctx.profile_read()
     ctx.profile(False)
-    pk = peaks()
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    rec = prof[dom]
-    achieved = rec["flops"] / (rec["ms"] * 1e-3) / 1e12 if rec["ms"] > 0 and rec["flops"] > 0 else None
-    unit, note = "TFLOP/s", None
-    if dom == "gemm_tc":
-        # algorithmic flops (2 N^3 per slice product) against the ceiling of the
-        # split mode: the tensor peak of its operand type / MMAs issued per product
-        mmas = {"3xtf32": 5, "bf16x3": 6, "bf16": 1}[args.prec]
-        base = pk["tf32_tflops"] if args.prec == "3xtf32" else pk["bf16_tflops"]
-        bound, peak = "tensor", base / mmas
-        note = f"{args.prec} ceiling = {'TF32' if args.prec == '3xtf32' else 'BF16'} peak / {mmas} MMAs per product"
-    elif dom == "gemm_oz":
-        # FP64-accurate products by digit splitting: 36 BF16 MMAs per product
-        bound, peak = "tensor", pk["bf16_tflops"] / 36.0
-        note = "FP64-equivalent flops; ceiling = BF16 peak / 36 digit products"
-    else:
-        bound, peak = "alu", pk["fp64_tflops"]
-        note = "FP64 pipe"
-    tr = traffic_record(dom)
-    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": tr["bytes_per_launch"] if tr else None,
-                "peak_source": f"{pk['source']} (fp64 = bf16 x 1.25/2250, tf32 = bf16 x 1100/2250 nominal ratios)",
-                "peak_note": note,
-                "launches": rec["launches"], "ms_per_launch": rec["ms"] / max(rec["launches"], 1),
-                "share": rec["ms"] / sum(v["ms"] for v in prof.values()),
-                "breakdown_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+    roof = roofline_entry(prof, args.prec, peaks(), "chains16")
 
-    # FP64-product path on the same workload
+    errors = None
+    if env.rank == 0 and args.oracle_sample > 0:
+        errors = oracle_errors(torch, ctx, d_s, dict(Lx=wl["L"], Ly=wl["L"], t=wl["t"], mu=wl["mu"], xi=wl["xi"],
+                                                     beta=wl["beta"], dtau=wl["dtau"], n_wrap=10, J=wl["J"],
+                                                     h=wl["h"]), args.oracle_sample)
+
     fp64 = None
     if not args.skip_fp64:
-        c64 = make_ctx("fp64")
+        c64 = make_ctx(sldqmc, wl, "fp64", B, nwrap["fp64"], J, E0)
         d_s64 = d_s.clone()
         d_lw64 = torch.zeros(B, dtype=torch.float64, device="cuda")
         c64.log_weight_batch_dev(d_s64, d_lw64)
         c64.cumulative_batch_dev(d_s64, d_lw64, 1, seed, 0, 1, d_acc)
         c64.sync()
-        K64 = max(2, args.steps // 3)
-        barrier_sync()
-        T64 = steps_timed(torch, c64, d_s64, d_lw64, d_acc, seed, 1, K64)
-        barrier_sync()
-        T64 = rank_max(T64)
-        fp64 = {"value": 2 * B * K64 * world / T64, "unit": UNIT, "steps": K64, "ms_per_step": 1e3 * T64 / K64}
+        K64 = max(2, K // 3)
+        env.barrier_sync()
+        T64 = env.rank_max(steps_timed(torch, c64, d_s64, d_lw64, d_acc, seed, 1, K64))
+        fp64 = {"value": 2 * B * K64 * env.world / T64, "unit": UNIT, "steps": K64, "ms_per_step": 1e3 * T64 / K64}
         c64.close()
 
-    # end to end through the host-buffer C ABI call (copies inside the timed region)
+    V = ctx.V
     h_s = torch.empty((B, ctx.M, ctx.N), dtype=torch.int8).pin_memory()
     h_s.copy_(d_s.cpu())
     h_lw = torch.empty(B, dtype=torch.float64).pin_memory()
     h_lw.copy_(d_lw.cpu())
     h_acc = np.zeros(B, dtype=np.int32)
     hs, hl = h_s.numpy(), h_lw.numpy()
-    Ke = max(2, args.steps // 2)
-    barrier_sync()
+    Ke = max(2, K // 2)
+    env.barrier_sync()
     t0 = time.perf_counter()
     for k in range(Ke):
         ctx.cumulative_batch(hs, hl, 1, seed, 2 * 10 ** 6 + k, 1, h_acc)
     torch.cuda.synchronize()
-    Te = rank_max(time.perf_counter() - t0)
-    e2e = {"value": 2 * B * Ke * world / Te, "unit": UNIT, "h2d_bytes_per_step": B * V + 8 * B,
+    Te = env.rank_max(time.perf_counter() - t0)
+    e2e = {"value": 2 * B * Ke * env.world / Te, "unit": UNIT, "h2d_bytes_per_step": B * V + 8 * B,
            "d2h_bytes_per_step": B * V + 8 * B + 4 * B}
-
-    crit = None
-    if args.tau_steps > 0 and not args.no_train and not args.skip_critical:
-        crit = critical_point_context(torch, sldqmc, args, rank)
+    ctx.close()
 
     cpu = None
-    if rank == 0 and not args.skip_cpu:
+    if env.rank == 0 and not args.skip_cpu:
         from oracle import oracle as O
-        O.build()
-        t1 = oracle_weight_sample(1)
-        cpu = {"value": 1.0 / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one single-flavour weight evaluation (16x16, M=160, n_wrap=10, uniform random field) "
-                         "by the FP64 CPU oracle, one host thread"}
-    if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": 1e3 * Tmax / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None,
-               "dtype": "tf32x2/fp32-acc products, f64 stabilisation" if args.prec == "3xtf32" else args.prec,
-               "data": "synthetic (seeded random fields; effective model fitted on seeded local-DQMC runs)",
-               "config": {"workload": workload_name(), "global_batch": B * world, "seq_len": ctx.M,
-                          "lattice": f"{WL['L']}x{WL['L']}", "chains_per_gpu": B, "precision": args.prec,
-                          "n_wrap": nwrap, "n_wrap_tuning": tune_log or None,
-                          "parallelism": f"replicas x{world}", "l2": "working set > L2 (no flush)",
-                          "fit": {"lattice": "8x8", "configs": ncfg, "J": [float(x) for x in J],
-                                  "E0": E0, "r2": r2}, "setup_s": round(t_setup, 2)},
-               "fp64": fp64, "decorrelated_samples_per_s": samples_per_s, "tau_int": tau,
-               "tau_window": window, "tau_observable": "|sum s| per chain",
-               "tau_series": {"chains": min(args.tau_chains, B), "steps": args.tau_steps, "note": tau_note}, "accept_rate": accept_rate,
-               "critical_point": crit,
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-               "gpu_launches": launches}
-        print(json.dumps(out), flush=True)
+        from paper_1612_03804_gb300.inputs import batch_uniform as bu
+        cores = len(os.sched_getaffinity(0))
+        m = O.Model(wl["L"], wl["L"], t=wl["t"], mu=wl["mu"], xi=wl["xi"], beta=wl["beta"], dtau=wl["dtau"],
+                    n_wrap=10)
+        t0 = time.perf_counter()
+        O.weight_many(m, bu(1, cores, m.M, m.N), -1, workers=cores)
+        dt = time.perf_counter() - t0
+        cpu = {"value": cores / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{cores} single-flavour weights of this workload (n_wrap=10), one per host core, {dt:.1f} s"}
+    return {"workload": workload_name(dict(wl, n_wrap=nwrap[args.prec])), "value": value, "unit": UNIT,
+            "chains": B * env.world, "steps": K, "ms_per_step": 1e3 * Tmax / K, "precision": args.prec,
+            "n_wrap": nwrap, "n_wrap_tuning": tune_log or None, "accept_rate": accept_rate,
+            "fit": {"lattice": "8x8", "configs": ncfg, "J": [float(x) for x in J], "E0": E0, "r2": r2},
+            "setup_s": round(t_setup, 2), "fp64": fp64, "errors_vs_oracle": errors,
+            "decorrelated_samples_per_s": samples_per_s, "tau_int": tau, "tau_window": window,
+            "tau_observable": "|sum s| per chain",
+            "tau_series": {"chains": min(args.tau_chains, B), "steps": args.tau_steps, "note": tau_note},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches}
+
+
+# ------------------------------------------------- 64 uneven chains (config 4)
+UNEVEN_L = (12, 16, 20, 24, 32)
+UNEVEN_BETA = (4.0, 8.0)
+
+
+def uneven_buckets(n_chains=64):
+    """Chain c: L = UNEVEN_L[c mod 5], beta = UNEVEN_BETA[(c div 5) mod 2]."""
+    counts = {}
+    for c in range(n_chains):
+        key = (UNEVEN_L[c % 5], UNEVEN_BETA[(c // 5) % 2])
+        counts[key] = counts.get(key, 0) + 1
+    return counts
+
+
+def fill_fraction(work_uneven, t_uneven, work_full, t_full):
+    """Algorithmic flop rate of the uneven batch relative to that of a full
+    uniform batch measured in the same run (1.0: the uneven chains keep the
+    GPU as busy as the best-filled workload)."""
+    return (work_uneven / t_uneven) / (work_full / t_full)
+
+
+def run_uneven(env, full_rate=None):
+    import numpy as np
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    from paper_1612_03804_gb300.tune import autotune_nwrap
+    torch, sldqmc, args = env.torch, env.sldqmc, env.args
+    dtau, mu = 0.05, -0.5
+    members, tuned, work = [], {}, 0.0
+    t_setup = time.perf_counter()
+    for k, ((L, beta), B) in enumerate(sorted(uneven_buckets().items())):
+        nw, _ = autotune_nwrap(L, beta, dtau, mu, args.prec, batch=2, reps=1)
+        tuned[f"{L}x{L} beta={beta:g}"] = {"chains": B, "n_wrap": nw}
+        wl = dict(CH16, L=L, beta=beta)
+        ctx = make_ctx(sldqmc, wl, args.prec, B, nw, bare_couplings(wl))
+        s = torch.from_numpy(batch_uniform(900 + k + 100 * env.rank, B, ctx.M, ctx.N)).cuda()
+        ctx.eff_sweeps_batch_dev(s, 20, 5, 0, -1)
+        lw = torch.zeros(B, dtype=torch.float64, device="cuda")
+        ctx.log_weight_batch_dev(s, lw)
+        acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+        ctx.sync()
+        members.append((ctx, s, lw, acc, 7000 + k + (env.rank << 20)))
+        work += B * 2 * weight_work(L * L, ctx.M, nw)
+    g = sldqmc.Graph(members, n_eff=1, step0=0)
+    for _ in range(args.warmup):
+        g.launch(1)
+    g.sync()
+    t_setup = time.perf_counter() - t_setup
+    K = max(2, min(args.steps, 10))
+    env.barrier_sync()
+    t0 = time.perf_counter()
+    g.launch(K)
+    g.sync()
+    T = env.rank_max(time.perf_counter() - t0)
+    launches = sum(m[0].kernel_launches() for m in members)
+    accepted = sum(int(m[3].sum().item()) for m in members)
+    g.close()
+    for m in members:
+        m[0].close()
+    out = {"workload": "64 SLDQMC chains, L in {12,16,20,24,32} x beta in {4,8}, dtau=0.05, mu=-0.5, xi=1, "
+                       f"{args.prec} products, FP64 stabilisation, one CUDA graph per step (replay)",
+           "value": 2 * 64 * K * env.world / T, "unit": UNIT, "steps": K, "ms_per_step": 1e3 * T / K,
+           "buckets": tuned, "accept_rate": accepted / (64.0 * (K + args.warmup)),
+           "algorithmic_tflops": work * K / T / 1e12, "setup_s": round(t_setup, 2),
+           "kernel_launches_total": launches}
+    if full_rate:
+        out["fill_fraction"] = (work * K / T) / full_rate
+        out["fill_note"] = ("algorithmic flop rate (2 M N^3 products + 3.67 N^3 per block + 2/3 N^3 LU per weight) "
+                            "relative to the 128-chain 16x16 workload of the same run")
+    return out
+
+
+# ------------------------------------------------ precision sweep (config 3)
+def run_precision(env):
+    import numpy as np
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    torch, sldqmc, args = env.torch, env.sldqmc, env.args
+    L, beta, dtau, mu = 32, 10.0, 0.05, -0.5
+    M = int(round(beta / dtau))
+    nf = args.precision_fields
+    fields = torch.from_numpy(batch_uniform(1003, nf, M, L * L)).cuda()
+    uniform = torch.ones((1, M, L * L), dtype=torch.int8, device="cuda")
+    cf = closed_form_logdet(L, beta, 1.0, mu - 1.0)
+    out = []
+    for nw in (5, 10, 20):
+        res = {}
+        for prec in ("fp64", "3xtf32", "bf16x3", "bf16"):
+            wl = dict(CH16, L=L, beta=beta, dtau=dtau, mu=mu)
+            with make_ctx(sldqmc, wl, prec, nf, nw) as ctx:
+                ld = torch.zeros(nf, dtype=torch.float64, device="cuda")
+                ctx.weight_batch_dev(fields, -1, ld)
+                ctx.sync()
+                st = torch.cuda.current_stream()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                ctx.weight_batch_dev(fields, -1, ld)
+                e1.record(st)
+                ctx.sync()
+                dt = e0.elapsed_time(e1) / 1e3
+                G = torch.zeros((1, L * L, L * L), dtype=torch.float64, device="cuda")
+                ctx.green_batch_dev(fields[:1], -1, 0, G)
+                lu = torch.zeros(1, dtype=torch.float64, device="cuda")
+                ctx.weight_batch_dev(uniform, -1, lu)
+                ctx.sync()
+                res[prec] = (ld.cpu().numpy(), G.cpu().numpy()[0], float(lu.item()), dt)
+        ref_ld, ref_G = res["fp64"][0], res["fp64"][1]
+        for prec in ("fp64", "3xtf32", "bf16x3", "bf16"):
+            ld, G, lu, dt = res[prec]
+            out.append({"n_wrap": nw, "prec": prec,
+                        "logdet_rel_err_max": float(np.max(np.abs(ld - ref_ld) / np.abs(ref_ld))),
+                        "logdet_abs_err_max": float(np.max(np.abs(ld - ref_ld))),
+                        "max_abs_dG": float(np.max(np.abs(G - ref_G))),
+                        "closed_form_rel_err": abs(lu - cf) / abs(cf),
+                        "weights_per_s": nf / dt})
+    return {"workload": f"32x32, beta=10, dtau=0.05 (M=200), mu=-0.5, {nf} seeded random fields; errors against "
+                        "the FP64-product GPU path at the same n_wrap (parity-checked against the oracle at "
+                        "smaller sizes) and the uniform-field closed form", "rows": out}
+
+
+# ------------------------------------------------------- 4x4 DQMC (config 1)
+def run_local4(env):
+    from paper_1612_03804_gb300.inputs import uniform_field
+    torch, sldqmc = env.torch, env.sldqmc
+    wl = dict(CH16, L=4, mu=0.0, beta=2.0, dtau=0.1)
+    n_sw = 1000
+    with make_ctx(sldqmc, wl, "fp64", 1, 10) as ctx:
+        s = torch.from_numpy(uniform_field(1001, ctx.M, ctx.N)[None]).cuda()
+        ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.weight_batch_dev(s, -1, ld)
+        ctx.sync()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(100):
+            ctx.weight_batch_dev(s, -1, ld)
+        e1.record(st)
+        ctx.sync()
+        us_w = e0.elapsed_time(e1) * 10.0
+        ctx.local_sweep_batch_dev(s, 17, 0, 5, want_stats=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = ctx.local_sweep_batch_dev(s, 17, 5, n_sw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    return {"workload": "plain FP64 DQMC, 4x4, mu=0, beta=2, dtau=0.1 (M=20), n_wrap=10, one chain",
+            "us_per_weight": us_w, "us_per_sweep": 1e6 * dt / n_sw, "sweeps": n_sw,
+            "accept_rate": stats[0]["accepted"] / max(stats[0]["proposed"], 1),
+            "max_drift": stats[0]["max_drift"]}
+
+
+# ----------------------------------------- decorrelation at the critical point
+def run_critical(env):
+    """Decorrelation at the paper's finite-temperature critical point (beta=1,
+    dtau=0.05, M=20, h=2.774, 16x16; fit on 8x8 as in the paper): acceptance and
+    tau_int of |sum s| for 16 chains with 1, 10 and 100 effective-model sweeps
+    per cumulative update."""
+    import numpy as np
+    from paper_1612_03804_gb300.analysis import tau_int
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    torch, sldqmc, args = env.torch, env.sldqmc, env.args
+    wl = dict(CH16, beta=1.0)
+    J, E0, r2, _ = train_effective_model(torch, sldqmc, wl, args, 8100 + env.rank, n_wrap=20)
+    B = min(args.tau_chains, args.batch)
+    ctx = make_ctx(sldqmc, wl, args.prec, B, 20, J, E0)
+    d_s = torch.from_numpy(batch_uniform(8200 + env.rank, B, ctx.M, ctx.N)).cuda()
+    for k in range(args.eff_thermalize):
+        ctx.eff_sweeps_batch_dev(d_s, 1, 82, k, -1)
+    d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
+    ctx.log_weight_batch_dev(d_s, d_lw)
+    d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+    for w in range(args.warmup):
+        ctx.cumulative_batch_dev(d_s, d_lw, 1, 83, w, 1, d_acc)
+    s0, lw0 = d_s.clone(), d_lw.clone()
+    scan = []
+    steps = args.critical_steps
+    for n_eff in (1, 10, 100):
+        d_s.copy_(s0)
+        d_lw.copy_(lw0)
+        d_acc.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        series = magnetisation_series(torch, ctx, d_s, d_lw, d_acc, 83 + n_eff, 100, steps, n_eff).astype(np.float64)
+        dt = time.perf_counter() - t0
+        tau, window = tau_int(series)
+        scan.append({"n_eff": n_eff, "accept_rate": float(d_acc.sum().item()) / (B * steps),
+                     "tau_int": tau, "tau_window": window, "steps_per_s": steps / dt,
+                     "decorrelated_samples_per_s": B * steps / dt / tau,
+                     "note": ("window reached" if window < steps - 1 else
+                              "window not reached: tau_int is a lower bound")})
     ctx.close()
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    return {"point": "16x16, beta=1, dtau=0.05 (M=20), h=2.774, mu=-0.5 (the paper's critical point), "
+                     f"{B} chains, effective model fitted on 8x8 (R^2={r2:.6f})", "steps": steps, "n_eff_scan": scan}
+
+
+def run_ours(args):
+    env = Env(args)
+    chosen = ALL_WORKLOADS if args.workloads == "all" else tuple(w for w in args.workloads.split(",") if w)
+    head = run_large(env) if "large" in chosen else None
+    wls = {}
+    if "chains16" in chosen:
+        wls["chains16"] = run_chains16(env)
+    if "uneven" in chosen:
+        full = None
+        if "chains16" in wls:
+            c = wls["chains16"]
+            nw = c["n_wrap"][args.prec]
+            full = c["chains"] / env.world * 2 * weight_work(256, 160, nw) / (c["ms_per_step"] * 1e-3)
+        wls["uneven"] = run_uneven(env, full)
+    if "precision" in chosen:
+        wls["precision"] = run_precision(env)
+    if "local4" in chosen:
+        wls["local4"] = run_local4(env)
+    if "critical" in chosen and not args.no_train:
+        wls["critical"] = run_critical(env)
+    if env.rank == 0:
+        if head is None:
+            # a partial run (no headline workload): the first workload's numbers head the line
+            first = next(iter(wls.values()))
+            head = {"metric": METRIC, "value": first.get("value"), "unit": UNIT, "n_gpus": env.world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": first.get("ms_per_step"),
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+                    "data": "synthetic", "config": {"workload": first.get("workload")},
+                    "partial": "headline workload not run"}
+        head["workloads"] = wls
+        print(json.dumps(head), flush=True)
+    if env.dist:
+        env.dist.barrier()
+        env.dist.destroy_process_group()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workloads", default="all", help="comma-separated subset of " + ",".join(ALL_WORKLOADS))
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--prec", default="3xtf32", choices=["3xtf32", "bf16x3", "bf16", "fp64"])
     ap.add_argument("--train-configs", type=int, default=2000)
@@ -555,15 +972,17 @@ def main():
     ap.add_argument("--thermalize", type=int, default=20)
     ap.add_argument("--bare-sweeps", type=int, default=200)
     ap.add_argument("--eff-thermalize", type=int, default=300)
-    ap.add_argument("--tau-steps", type=int, default=300)
+    ap.add_argument("--large-eff-thermalize", type=int, default=100)
+    ap.add_argument("--tau-steps", type=int, default=3000)
     ap.add_argument("--tau-chains", type=int, default=16)
-    ap.add_argument("--n-wrap", default="auto", help="stabilisation interval, or 'auto' for the autotuner")
-    ap.add_argument("--profile-steps", type=int, default=1)
+    ap.add_argument("--critical-steps", type=int, default=300)
+    ap.add_argument("--precision-fields", type=int, default=4)
+    ap.add_argument("--oracle-sample", type=int, default=2)
+    ap.add_argument("--n-wrap", default="auto", help="stabilisation interval of chains16, or 'auto' for the autotuner")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-train", action="store_true",
                     help="use the bare Ising couplings as H_eff (no local-DQMC training; for profiling runs)")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--skip-critical", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

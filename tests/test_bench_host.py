@@ -21,12 +21,14 @@ def _tree(tmp_path, src_text):
 def test_traffic_record_follows_its_sources(tmp_path, monkeypatch):
     csrc = _tree(tmp_path, "kernel v1\n")
     sha = hashlib.sha256(b"kernel v1\n").hexdigest()[:16]
-    rec = {"gemm_tc": {"sources": ["k.cu"], "sha": sha, "launches": 3, "bytes_per_launch": 1.5e6}}
+    rec = {"chains16": {"gemm_tc": {"sources": ["k.cu"], "sha": sha, "launches": 3, "bytes_per_launch": 1.5e6}}}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     got = bench.traffic_record("gemm_tc")
     assert got is not None and got["bytes_per_launch"] == 1.5e6
     assert bench.traffic_record("gemm_oz") is None
+    # a record holds for the workload it was captured on only
+    assert bench.traffic_record("gemm_tc", "large") is None
     (csrc / "k.cu").write_text("kernel v2\n")
     assert bench.traffic_record("gemm_tc") is None
     os.remove(csrc / "k.cu")
@@ -73,3 +75,45 @@ def test_clock_summary_flags_throttle_reasons():
 def test_weak_scaling_value_counts_all_ranks():
     assert bench.weak_scaling_value(256, 4, 2.0) == 512.0
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_roofline_entry_uses_the_operand_type_peak():
+    """The dominant class's fraction is taken against the peak of its own operand type;
+    the issue efficiency (peak over the MMAs of one product) is a separate field."""
+    pk = {"bf16_tflops": 1700.0, "tf32_tflops": 1700.0 * 1100 / 2250, "fp64_tflops": 1700.0 * 1.25 / 2250,
+          "source": "measured (sustained)"}
+    prof = {"gemm_tc": {"launches": 10, "ms": 100.0, "flops": 8.31e12},
+            "gemm_oz": {"launches": 5, "ms": 50.0, "flops": 1e11},
+            "panel_f64": {"launches": 5, "ms": 10.0, "flops": 1e9}}
+    r = bench.roofline_entry(prof, "3xtf32", pk, "nowhere")
+    assert r["kernel"] == "gemm_tc" and r["bound"] == "tensor" and r["dtype"] == "tf32"
+    assert abs(r["achieved"] - 83.1) < 1e-9
+    assert abs(r["frac"] - 83.1 / pk["tf32_tflops"]) < 1e-12
+    assert abs(r["issue_efficiency"] - 5 * r["frac"]) < 1e-12
+    assert r["traffic"] is None
+    prof["gemm_oz"]["ms"] = 500.0
+    r = bench.roofline_entry(prof, "bf16x3", pk, "nowhere")
+    assert r["kernel"] == "gemm_oz" and r["dtype"] == "bf16"
+    assert abs(r["frac"] - (1e11 / 0.5 / 1e12) / 1700.0) < 1e-12
+    assert abs(r["issue_efficiency"] - 36 * r["frac"]) < 1e-12
+
+
+def test_uneven_buckets_and_fill_fraction():
+    b = bench.uneven_buckets()
+    assert sum(b.values()) == 64 and len(b) == 10
+    assert b[(12, 4.0)] == 7 and b[(32, 8.0)] == 6
+    assert bench.fill_fraction(10.0, 2.0, 20.0, 2.0) == 0.5
+
+
+def test_closed_forms_and_extrapolation():
+    import numpy as np
+    # G of the uniform field is the Fermi function in momentum space: its trace is the filling
+    L, beta, mu = 6, 3.0, -0.7
+    g = bench.closed_form_green_row(L, beta, 1.0, mu)
+    k = 2 * np.pi * np.arange(L) / L
+    eps = -2 * (np.cos(k)[None, :] + np.cos(k)[:, None]) - mu
+    assert abs(g[0, 0] * L * L - np.sum(1.0 / (1.0 + np.exp(-beta * eps)))) < 1e-12
+    ld = bench.closed_form_logdet(L, beta, 1.0, mu)
+    assert abs(ld - np.sum(np.log1p(np.exp(-beta * eps)))) < 1e-12
+    r = bench.extrapolate_oracle(1.0, dict(L=32, beta=20.0, dtau=0.1))
+    assert abs(r - (256 / 1024) ** 3 * (100 / 200)) < 1e-15
