@@ -36,7 +36,10 @@ Beside it, in the same JSON line:
      precision : 32x32, beta=10, dtau=0.05 (M=200), n_wrap in {5,10,20},
                  FP64 / split-TF32 / split-BF16 / BF16 products;
      local4    : plain FP64 DQMC on 4x4 (weight, then local sweeps);
-     critical  : decorrelation at the paper's critical point (beta=1).
+     critical  : decorrelation at the paper's critical point (beta=1);
+     effmodel16: the paper's 16-coupling effective model, its 1 - R^2 range
+                 scans and tau_int of local against cumulative updates for
+                 L = 8, 12, 16, 24.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workloads large,chains16,uneven,precision,local4,critical]
@@ -67,7 +70,8 @@ UNIT = "weight evals/s"
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}  # TFLOP/s, dense, per GPU
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 MMAS = {"3xtf32": 5, "bf16x3": 6, "bf16": 1}
-ALL_WORKLOADS = ("large", "chains16", "uneven", "precision", "local4", "critical")
+SMS, SM_MAX_MHZ = 152, 2070.0
+ALL_WORKLOADS = ("large", "chains16", "uneven", "precision", "local4", "critical", "effmodel16")
 # oracle sample for the CPU baseline and the reference arm: single-flavour
 # weights at 16x16 with the headline's beta, dtau and n_wrap
 CPU_SAMPLE = dict(L=16, beta=10.0, dtau=0.1, n_wrap=10)
@@ -115,6 +119,9 @@ def peaks():
             pass
     vals["fp64_tflops"] = vals["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
     vals["tf32_tflops"] = vals["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
+    # FP32 CUDA-core peak from the unit counts and the maximum SM clock:
+    # 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2070 MHz
+    vals["fp32_tflops"] = SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
     vals["source"] = src
     return vals
 
@@ -212,6 +219,15 @@ def roofline_entry(prof, prec, pk, workload):
         bound, peak, per = "tensor", base, MMAS.get(prec, 1)
         note = (f"{prec} slice products: algorithmic 2N^3 per product against the {dtype.upper()} peak; "
                 f"issue_efficiency against {dtype.upper()} peak / {per} MMAs per product")
+    elif dom == "sep":
+        if prec == "fp64":
+            bound, peak, per, dtype = "alu", pk["fp64_tflops"], 1, "fp64"
+            note = "separable exp(-dtau K) convolutions in FP64 against the FP64 pipe"
+        else:
+            bound, peak, per, dtype = "alu", pk["fp32_tflops"], 3, "fp32"
+            note = ("separable exp(-dtau K) convolutions in split FP32: algorithmic flops (2 N^2 (Lx+Ly) per slice) "
+                    "against the FP32 CUDA-core peak (152 SMs x 128 lanes x 2 x 2070 MHz); issue_efficiency "
+                    "against that peak / 3 FMAs per multiply-add")
     elif dom == "gemm_oz":
         bound, peak, per, dtype = "tensor", pk["bf16_tflops"], 36, "bf16"
         note = ("FP64-accurate digit-split products (Gram, Cholesky-QR updates and panels, R2R1, V update, "
@@ -522,6 +538,9 @@ def run_large(env):
     Te = env.rank_max(time.perf_counter() - t0)
     e2e = {"value": 2 * B * Ke * env.world / Te, "unit": UNIT, "steps": Ke,
            "h2d_bytes_per_step": B * M * N + 8 * B, "d2h_bytes_per_step": B * M * N + 8 * B + 4 * B}
+    sep = separable_arm(env, ctx, d_s, d_lw, d_acc, seed, u, mu_eff, cf) if not args.skip_separable else None
+    if sep:
+        sep["dense_slice_products_ms_per_step"] = prof["gemm_tc"]["ms"] + prof["gemm_f64"]["ms"]
     ctx.close()
     del d_s, u
 
@@ -569,11 +588,42 @@ def run_large(env):
                       "setup_s": round(t_setup, 2)},
            "ms_per_weight": 1e3 * Tmax / (2 * B * args.steps),
            "ms_per_accept_step": 1e3 * Tmax / args.steps,
-           "accept_rate": accept_rate, "fp64": fp64, "precision": precision,
+           "accept_rate": accept_rate, "fp64": fp64, "precision": precision, "separable": sep,
            "decorrelated_samples_per_s": None,
            "decorrelation_note": ("tau_int needs a series of many cumulative steps (seconds each at 100x100); "
                                   "it is measured on the chains16 workload (workloads.chains16)"),
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
+    return out
+
+
+def separable_arm(env, ctx, d_s, d_lw, d_acc, seed, u=None, mu_eff=None, cf=None, prec=None):
+    """The same chains with exp(-dtau K) in its exact separable form (two
+    circular convolutions per slice instead of a dense product): weight
+    evaluations/s, the closed-form error and the slice-product time of a
+    profiled step against the dense one."""
+    torch, args = env.torch, env.args
+    B = d_s.shape[0]
+    ctx.set_kinetic_form("separable")
+    ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 3 * 10 ** 6, 1, d_acc)
+    ctx.sync()
+    K = max(2, args.steps // 2)
+    env.barrier_sync()
+    T = env.rank_max(steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, 3 * 10 ** 6 + 1, K))
+    ctx.profile(True)
+    ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 4 * 10 ** 6, 1, d_acc)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    out = {"value": 2 * B * K * env.world / T, "unit": UNIT, "steps": K, "ms_per_step": 1e3 * T / K,
+           "slice_products_ms_per_step": prof["sep"]["ms"],
+           "roofline": roofline_entry(prof, prec or args.prec, peaks(), "none"),
+           "note": "exp(-dtau K) = e^{dtau mu} E1x (x) E1y applied as two circular convolutions per row of the "
+                   "running product, rows resident in shared memory for a whole block"}
+    if u is not None:
+        ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.weight_batch_dev(u, -1, ld)
+        ctx.sync()
+        out["closed_form_rel_err"] = abs(float(ld.item()) - cf) / abs(cf)
+    ctx.set_kinetic_form("dense")
     return out
 
 
@@ -686,8 +736,21 @@ def run_chains16(env):
         env.barrier_sync()
         T64 = env.rank_max(steps_timed(torch, c64, d_s64, d_lw64, d_acc, seed, 1, K64))
         fp64 = {"value": 2 * B * K64 * env.world / T64, "unit": UNIT, "steps": K64, "ms_per_step": 1e3 * T64 / K64}
+        if not args.skip_separable:
+            c64.profile(True)
+            c64.cumulative_batch_dev(d_s64, d_lw64, 1, seed, 5 * 10 ** 6, 1, d_acc)
+            p_dense = c64.profile_read()
+            c64.profile(False)
+            sp = separable_arm(env, c64, d_s64, d_lw64, d_acc, seed, prec="fp64")
+            # in the FP64 mode the stabilisation also runs on the FP64 GEMM: the dense
+            # slice products are what the separable step no longer spends there
+            sp["dense_slice_products_ms_per_step"] = p_dense["gemm_f64"]["ms"] - sp["roofline"]["breakdown_ms"]["gemm_f64"]
+            fp64["separable"] = sp
         c64.close()
 
+    sep = separable_arm(env, ctx, d_s, d_lw, d_acc, seed) if not args.skip_separable else None
+    if sep:
+        sep["dense_slice_products_ms_per_step"] = prof["gemm_tc"]["ms"] + prof["gemm_f64"]["ms"]
     V = ctx.V
     h_s = torch.empty((B, ctx.M, ctx.N), dtype=torch.int8).pin_memory()
     h_s.copy_(d_s.cpu())
@@ -722,7 +785,7 @@ def run_chains16(env):
             "chains": B * env.world, "steps": K, "ms_per_step": 1e3 * Tmax / K, "precision": args.prec,
             "n_wrap": nwrap, "n_wrap_tuning": tune_log or None, "accept_rate": accept_rate,
             "fit": {"lattice": "8x8", "configs": ncfg, "J": [float(x) for x in J], "E0": E0, "r2": r2},
-            "setup_s": round(t_setup, 2), "fp64": fp64, "errors_vs_oracle": errors,
+            "setup_s": round(t_setup, 2), "fp64": fp64, "separable": sep, "errors_vs_oracle": errors,
             "decorrelated_samples_per_s": samples_per_s, "tau_int": tau, "tau_window": window,
             "tau_observable": "|sum s| per chain",
             "tau_series": {"chains": min(args.tau_chains, B), "steps": args.tau_steps, "note": tau_note},
@@ -922,6 +985,97 @@ def run_critical(env):
                      f"{B} chains, effective model fitted on 8x8 (R^2={r2:.6f})", "steps": steps, "n_eff_scan": scan}
 
 
+# ------------------------- the paper's 16-coupling model and its range scans
+def run_effmodel16(env):
+    """"Results" of the paper at its critical point (beta=1, dtau=0.05, M=20,
+    h=2.774): the 1 - R^2 curves of the temporal range (space fixed at
+    nearest neighbours) and of the spatial range (time fixed at 10), the fit
+    of the 16-coupling model on 8x8 local-DQMC configurations, and tau_int of
+    |sum s| for local DQMC sweeps against cumulative updates with that model
+    transferred to L = 8, 12, 16, 24."""
+    import numpy as np
+    from paper_1612_03804_gb300 import effmodel as EM
+    from paper_1612_03804_gb300.analysis import tau_int
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    torch, sldqmc, args = env.torch, env.sldqmc, env.args
+    wl = dict(CH16, beta=1.0)
+    Bt = args.train_chains
+    t0 = time.perf_counter()
+    c8 = make_ctx(sldqmc, wl, "fp64", Bt, 20, bare_couplings(wl))
+    s = torch.from_numpy(batch_uniform(8300 + env.rank, Bt, c8.M, c8.N)).cuda()
+    for k in range(args.bare_sweeps):
+        c8.eff_sweeps_batch_dev(s, 1, 84, k, -1)
+    c8.local_sweep_batch_dev(s, 84, 0, args.thermalize, want_stats=False)
+    cfgs, sw = [], args.thermalize
+    while len(cfgs) * Bt < args.train_configs:
+        c8.local_sweep_batch_dev(s, 84, sw, 1, want_stats=False)
+        sw += 1
+        cfgs.append(s.cpu().numpy().copy())
+    cfgs = np.concatenate(cfgs)[: args.train_configs]
+    d_c = torch.from_numpy(cfgs).cuda()
+    lw = torch.zeros(len(cfgs), dtype=torch.float64, device="cuda")
+    for k in range(0, len(cfgs), Bt):
+        c8.log_weight_batch_dev(d_c[k:k + Bt], lw[k:k + Bt])
+    c8.sync()
+    logw = lw.cpu().numpy()
+
+    def fit(classes):
+        c8.set_effective_model(classes, np.zeros(len(classes)))
+        return c8.fit_effective_action(cfgs, logw)
+
+    temporal = [{"range": k, "one_minus_r2": 1.0 - fit(cls)[2]} for k, cls in EM.temporal_range_scan(10)]
+    spatial = [{"shells": sh, "one_minus_r2": 1.0 - fit(cls)[2]} for sh, cls in EM.spatial_range_scan(5)]
+    cls16 = EM.paper_classes()
+    J16, E016, r2_16 = fit(cls16)
+    c8.close()
+    t_fit = time.perf_counter() - t0
+
+    taus = []
+    B = args.tau_chains
+    for L in args.effmodel_sizes:
+        wlL = dict(wl, L=L)
+        row = {"L": L}
+        # local DQMC sweeps
+        cl = make_ctx(sldqmc, wlL, "fp64", B, 20)
+        sl = torch.from_numpy(batch_uniform(8400 + L, B, cl.M, cl.N)).cuda()
+        cl.set_effective_model(cls16, J16, E016)
+        for k in range(100):
+            cl.eff_sweeps_batch_dev(sl, 1, 85, k, -1)
+        cl.local_sweep_batch_dev(sl, 85, 0, 5, want_stats=False)
+        S = args.effmodel_steps
+        out = torch.zeros((S, B), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        for k in range(S):
+            cl.local_sweep_batch_dev(sl, 85, 5 + k, 1, want_stats=False)
+            out[k] = sl.float().sum(dim=(1, 2)).abs()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - ta
+        tau, win = tau_int(out.cpu().numpy().astype(np.float64))
+        row["local"] = {"tau_int_sweeps": tau, "window": win, "sweeps_per_s": S / dt,
+                        "note": "window reached" if win < S - 1 else "window not reached: lower bound"}
+        # cumulative updates with the 16-coupling model fitted on 8x8
+        d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
+        cl.log_weight_batch_dev(sl, d_lw)
+        d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        ser = magnetisation_series(torch, cl, sl, d_lw, d_acc, 86, 0, S, args.effmodel_neff).astype(np.float64)
+        dt = time.perf_counter() - ta
+        tau, win = tau_int(ser)
+        row["cumulative"] = {"n_eff": args.effmodel_neff, "tau_int_steps": tau, "window": win,
+                             "steps_per_s": S / dt, "accept_rate": float(d_acc.sum().item()) / (B * S),
+                             "note": "window reached" if win < S - 1 else "window not reached: lower bound"}
+        cl.close()
+        taus.append(row)
+    return {"point": "beta=1, dtau=0.05 (M=20), h=2.774, mu=-0.5, xi=1 (the paper's critical point); fits on "
+                     f"{len(cfgs)} local-DQMC configurations of 8x8",
+            "temporal_range_scan": temporal, "spatial_range_scan": spatial,
+            "model16": {"classes": EM.class_names(), "J": [float(x) for x in J16], "E0": E016, "r2": r2_16,
+                        "one_minus_r2": 1.0 - r2_16},
+            "fit_s": round(t_fit, 2), "tau_vs_L": taus, "chains": B, "series": args.effmodel_steps}
+
+
 def run_ours(args):
     env = Env(args)
     chosen = ALL_WORKLOADS if args.workloads == "all" else tuple(w for w in args.workloads.split(",") if w)
@@ -942,6 +1096,8 @@ def run_ours(args):
         wls["local4"] = run_local4(env)
     if "critical" in chosen and not args.no_train:
         wls["critical"] = run_critical(env)
+    if "effmodel16" in chosen:
+        wls["effmodel16"] = run_effmodel16(env)
     if env.rank == 0:
         if head is None:
             # a partial run (no headline workload): the first workload's numbers head the line
@@ -973,13 +1129,17 @@ def main():
     ap.add_argument("--bare-sweeps", type=int, default=200)
     ap.add_argument("--eff-thermalize", type=int, default=300)
     ap.add_argument("--large-eff-thermalize", type=int, default=100)
-    ap.add_argument("--tau-steps", type=int, default=3000)
+    ap.add_argument("--tau-steps", type=int, default=1000)
     ap.add_argument("--tau-chains", type=int, default=16)
     ap.add_argument("--critical-steps", type=int, default=300)
     ap.add_argument("--precision-fields", type=int, default=4)
     ap.add_argument("--oracle-sample", type=int, default=2)
+    ap.add_argument("--effmodel-sizes", type=lambda v: [int(x) for x in v.split(",")], default=[8, 12, 16, 24])
+    ap.add_argument("--effmodel-steps", type=int, default=300)
+    ap.add_argument("--effmodel-neff", type=int, default=10)
     ap.add_argument("--n-wrap", default="auto", help="stabilisation interval of chains16, or 'auto' for the autotuner")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-separable", action="store_true")
     ap.add_argument("--no-train", action="store_true",
                     help="use the bare Ising couplings as H_eff (no local-DQMC training; for profiling runs)")
     ap.add_argument("--skip-cpu", action="store_true")

@@ -231,6 +231,30 @@ void sldqmc_graph_destroy(sldqmc_graph *g);
  * buffers (the exact weight a cumulative update needs). */
 int sldqmc_log_weight_batch_dev(sldqmc_ctx *ctx, const int8_t *d_s, int B, double *d_logw);
 
+/* Form in which the kinetic propagator exp(-dtau K) enters the slice
+ * products of every weight and Green's-function evaluation of the context
+ * (weight, green, log weight, fresh Green's functions of the local sweep,
+ * cumulative updates).  The paper's cost of a cumulative update assumes a B
+ * matrix applied in O(N^2) per slice and column rather than a dense product
+ * ("Formalism of SLDQMC", the complexity paragraph).
+ *   SLDQMC_KINETIC_DENSE (default): dense N x N products (the slice GEMMs of
+ *     sldqmc_prec).
+ *   SLDQMC_KINETIC_SEPARABLE: the exact factorisation of the periodic
+ *     lattice, exp(-dtau K) = e^{dtau mu} E1x (x) E1y with E1 the ring
+ *     propagator of each direction, applied as two circular convolutions of
+ *     every row of the running product: 2 N^2 (Lx + Ly) flops per slice and
+ *     configuration instead of 2 N^3.  It is not a Trotter splitting of K: the
+ *     result equals the dense form up to rounding.  Arithmetic: FP64 in the
+ *     FP64 mode; split FP32 (each value a pair of floats, 48 significant bits,
+ *     FP32 accumulation) in the mixed modes.  The stabilisation and everything
+ *     after it are unchanged.  Requires N <= about 14500 (a row of the
+ *     product in shared memory); SLDQMC_ERR_UNSUPPORTED otherwise.
+ * The wrapping of the Green's function between slices in local sweeps keeps
+ * the dense products. */
+#define SLDQMC_KINETIC_DENSE 0
+#define SLDQMC_KINETIC_SEPARABLE 1
+int sldqmc_set_kinetic_form(sldqmc_ctx *ctx, int form);
+
 /* Number of this library's kernels launched on the context since create. */
 long long sldqmc_kernel_launches(const sldqmc_ctx *ctx);
 
@@ -286,7 +310,8 @@ int sldqmc_wait_selftest(sldqmc_ctx *ctx, int max_polls);
 #define SLDQMC_KC_LOCAL 4      /* local-update flips */
 #define SLDQMC_KC_OTHER 5      /* everything else */
 #define SLDQMC_KC_GEMM_OZ 6    /* FP64-accurate digit-split products on the BF16 tensor cores (mixed modes): Gram matrices, Cholesky-QR updates and panels, R2 R1, V update, LU updates */
-#define SLDQMC_KC_COUNT 7
+#define SLDQMC_KC_SEP 7        /* slice products with the separable exp(-dtau K) (sldqmc_set_kinetic_form) */
+#define SLDQMC_KC_COUNT 8
 
 /* Timing hooks (off by default): when on, every launch on the context's
  * stream is bracketed by CUDA events and tagged with its class and its

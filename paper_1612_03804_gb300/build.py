@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsldqmc.so")
-SOURCES = ["gemm_f64.cu", "stab.cu", "mc.cu", "tc_gemm.cu", "oz_gram.cu", "sldqmc.cu", "noalloc.cu"]
+SOURCES = ["gemm_f64.cu", "stab.cu", "mc.cu", "tc_gemm.cu", "oz_gram.cu", "sldqmc.cu", "noalloc.cu", "sep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -89,6 +89,13 @@ void oz_keep_bounds(sldqmc_ctx *c, int B);
 void oz_update_V(sldqmc_ctx *c, const double *R, double *V, double *Ts, int B);
 void oz_r2r1(sldqmc_ctx *c, const double *R2, const double *R1, double *R, int B);
 
+// Slice products with the separable exp(-dtau K) (sep.cu): X^T_out =
+// U^T D_t0 E D_t0+1 E ... for nb slices, one row per CTA in shared memory.
+bool sep_supported(int Lx, int Ly);
+void sep_set_limits();
+void sep_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, double cu, double cd, int t0,
+                     int nb, const double *ring, double *Xt_out);
+
 // Event-bracketed timing of launches (sldqmc_profile_*).
 struct ProfRec {
     cudaEvent_t a, b;
@@ -156,4 +163,5 @@ struct sldqmc_ctx {
     sldqmc_ctx *twin;          // second workspace + stream: the other flavour's weight runs concurrently
     cudaEvent_t ev_fork, ev_join;
     int no_twin;               // set on a twin itself, or when the twin could not be created
+    int kinetic;               // SLDQMC_KINETIC_*: form in which exp(-dtau K) enters the slice products
 };

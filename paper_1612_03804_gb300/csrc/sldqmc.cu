@@ -196,7 +196,10 @@ int weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, int tau0, doubl
     for (int m = 0; m < M; m += c->p.n_wrap) {
         const int nb = std::min(c->p.n_wrap, M - m);
         double *Xt;
-        if (c->p.prec == SLDQMC_FP64) {
+        if (c->kinetic == SLDQMC_KINETIC_SEPARABLE) {
+            sep_chain_block(c, Ut, d_s, B, cu, cd, (tau0 + m) % M, nb, c->d_Einv + nn, X1);
+            Xt = X1;
+        } else if (c->p.prec == SLDQMC_FP64) {
             const double *cur = Ut;
             double *outs[2] = {X1, X2};
             int o = 0;
@@ -265,6 +268,7 @@ sldqmc_ctx *get_twin(sldqmc_ctx *c)
         return nullptr;
     }
     t->no_twin = 1;
+    t->kinetic = c->kinetic;
     c->twin = t;
     return t;
 }
@@ -584,6 +588,7 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     }
     if (p->prec != SLDQMC_FP64) tc_convert_E(c);
     set_eff_smem_limits();
+    sep_set_limits();
     {
         int Npad = 1;
         while (Npad < N) Npad <<= 1;
@@ -1240,6 +1245,15 @@ int sldqmc_wait_selftest(sldqmc_ctx *c, int max_polls)
     if (!c || max_polls < 1 || max_polls > (1 << 24)) return SLDQMC_ERR_ARG;
     launch_wait_selftest(c, max_polls);
     return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
+}
+
+int sldqmc_set_kinetic_form(sldqmc_ctx *c, int form)
+{
+    if (!c || (form != SLDQMC_KINETIC_DENSE && form != SLDQMC_KINETIC_SEPARABLE)) return SLDQMC_ERR_ARG;
+    if (form == SLDQMC_KINETIC_SEPARABLE && !sep_supported(c->p.Lx, c->p.Ly)) return SLDQMC_ERR_UNSUPPORTED;
+    c->kinetic = form;
+    if (c->twin) c->twin->kinetic = form;
+    return SLDQMC_OK;
 }
 
 int sldqmc_profile_enable(sldqmc_ctx *c, int on)

@@ -96,6 +96,7 @@ def load(path=None):
         "sldqmc_wait_selftest": ([vp, i], i),
         "sldqmc_gram_batch_dev": ([vp, vp, i, vp], i),
         "sldqmc_profile_read": ([vp, vp, vp, vp], i),
+        "sldqmc_set_kinetic_form": ([vp, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -291,7 +292,13 @@ class Context:
                                             ctypes.c_uint64(seed), ctypes.c_uint32(step0), int(n_steps),
                                             _p(accepts)), "cumulative_batch")
 
-    KERNEL_CLASSES = ("gemm_f64", "gemm_tc", "panel_f64", "eff_sweep", "local_flips", "other", "gemm_oz")
+    KERNEL_CLASSES = ("gemm_f64", "gemm_tc", "panel_f64", "eff_sweep", "local_flips", "other", "gemm_oz", "sep")
+    KINETIC = {"dense": 0, "separable": 1}
+
+    def set_kinetic_form(self, form):
+        """'dense' (default) or 'separable' exp(-dtau K) in the slice products."""
+        _chk(load().sldqmc_set_kinetic_form(self.h, self.KINETIC[form] if isinstance(form, str) else int(form)),
+             "set_kinetic_form")
 
     def profile(self, on):
         _chk(load().sldqmc_profile_enable(self.h, int(bool(on))), "profile_enable")
