@@ -48,8 +48,16 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "3xtf32"])
-@pytest.mark.parametrize("Lx,Ly,mu,beta,dtau,nw,kind", CASES)
+MIXED_CASES = [
+    # the mixed modes need N >= 128 (their dense products use 128-row tensor-core tiles)
+    (12, 12, -0.5, 2.0, 0.05, 20, "uniform"),
+    (13, 11, 0.4, 1.5, 0.1, 5, "domains"),   # N = 143, Lx != Ly, both odd, ragged last block
+    (16, 9, -0.5, 1.0, 0.1, 3, "uniform"),
+]
+
+
+@pytest.mark.parametrize("prec,Lx,Ly,mu,beta,dtau,nw,kind",
+                         [("fp64",) + c for c in CASES] + [(p,) + c for p in ("3xtf32", "bf16x3") for c in MIXED_CASES])
 def test_separable_weight_matches_oracle(prec, Lx, Ly, mu, beta, dtau, nw, kind):
     m = O.Model(Lx, Ly, mu=mu, xi=1.0, beta=beta, dtau=dtau, n_wrap=1)
     if kind == "uniform":
@@ -65,9 +73,9 @@ def test_separable_weight_matches_oracle(prec, Lx, Ly, mu, beta, dtau, nw, kind)
                 assert abs(ld[k] - ref) <= BOUND[prec] * max(1.0, abs(ref)), (prec, k, eta, ld[k], ref)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x3"])
-def test_separable_green_matches_oracle(prec):
-    m = O.Model(6, 5, mu=-0.3, xi=1.0, beta=2.0, dtau=0.1, n_wrap=1)
+@pytest.mark.parametrize("prec,Lx,Ly", [("fp64", 6, 5), ("3xtf32", 12, 11), ("bf16x3", 12, 11)])
+def test_separable_green_matches_oracle(prec, Lx, Ly):
+    m = O.Model(Lx, Ly, mu=-0.3, xi=1.0, beta=2.0, dtau=0.1, n_wrap=1)
     s = uniform_field(41, m.M, m.N)
     with _ctx(m, 10, prec, 1) as ctx:
         for tau in (0, 7):
