@@ -39,7 +39,9 @@ Beside it, in the same JSON line:
      critical  : decorrelation at the paper's critical point (beta=1);
      effmodel16: the paper's 16-coupling effective model, its 1 - R^2 range
                  scans and tau_int of local against cumulative updates for
-                 L = 8, 12, 16, 24.
+                 L = 8, 12, 16, 24;
+     local_delayed: local sweeps with immediate rank-1 against delayed
+                 rank-32 Green's-function updates.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workloads large,chains16,uneven,precision,local4,critical]
@@ -71,7 +73,7 @@ NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}  # TFLOP/s, dense, per 
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 MMAS = {"3xtf32": 5, "bf16x3": 6, "bf16": 1}
 SMS, SM_MAX_MHZ = 152, 2070.0
-ALL_WORKLOADS = ("large", "chains16", "uneven", "precision", "local4", "critical", "effmodel16")
+ALL_WORKLOADS = ("large", "chains16", "uneven", "precision", "local4", "critical", "effmodel16", "local_delayed")
 # oracle sample for the CPU baseline and the reference arm: single-flavour
 # weights at 16x16 with the headline's beta, dtau and n_wrap
 CPU_SAMPLE = dict(L=16, beta=10.0, dtau=0.1, n_wrap=10)
@@ -250,6 +252,29 @@ def roofline_entry(prof, prec, pk, workload):
             "breakdown_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
             "breakdown_tflops": {k: (v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 and v["flops"] > 0
                                      else None) for k, v in prof.items()}}
+
+
+def profile_step(ctx, run):
+    """One profiled pass (CUDA events around every launch, flavours
+    serialised): returns (per-class record, per-site record)."""
+    ctx.profile(True)
+    run()
+    sites = ctx.profile_read_sites()
+    ctx.profile(False)
+    prof = {k: {"launches": 0, "ms": 0.0, "flops": 0.0} for k in ctx.KERNEL_CLASSES}
+    for v in sites.values():
+        p = prof[v["cls"]]
+        p["launches"] += v["launches"]
+        p["ms"] += v["ms"]
+        p["flops"] += v["flops"]
+    return prof, sites
+
+
+def site_table(sites, top=16):
+    rows = sorted(sites.items(), key=lambda kv: -kv[1]["ms"])[:top]
+    return {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 and v["flops"] > 0 else None)}
+            for k, v in rows}
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -486,13 +511,11 @@ def run_large(env):
     accept_rate = float(d_acc.sum().item()) / (B * args.steps)
 
     # roofline: one profiled step (CUDA events around every launch; flavours serialised)
-    ctx.profile(True)
-    ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, 1, d_acc)
-    prof = ctx.profile_read()
-    ctx.profile(False)
+    prof, sites = profile_step(ctx, lambda: ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, 1, d_acc))
     pk = peaks()
     roof = roofline_entry(prof, args.prec, pk, "large")
     roof["serialised_step_ms"] = sum(v["ms"] for v in prof.values())
+    roof["sites"] = site_table(sites)
 
     # error of the benched mode: the uniform field has a closed form (the
     # oracle's dense FP64 at N = 10^4, ~10^14 flops per weight, is beyond the
@@ -609,10 +632,7 @@ def separable_arm(env, ctx, d_s, d_lw, d_acc, seed, u=None, mu_eff=None, cf=None
     K = max(2, args.steps // 2)
     env.barrier_sync()
     T = env.rank_max(steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, 3 * 10 ** 6 + 1, K))
-    ctx.profile(True)
-    ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 4 * 10 ** 6, 1, d_acc)
-    prof = ctx.profile_read()
-    ctx.profile(False)
+    prof, sites = profile_step(ctx, lambda: ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 4 * 10 ** 6, 1, d_acc))
     out = {"value": 2 * B * K * env.world / T, "unit": UNIT, "steps": K, "ms_per_step": 1e3 * T / K,
            "slice_products_ms_per_step": prof["sep"]["ms"],
            "roofline": roofline_entry(prof, prec or args.prec, peaks(), "none"),
@@ -712,11 +732,9 @@ def run_chains16(env):
                     "window not reached: tau_int is a lower bound, samples/s an upper bound")
         samples_per_s = (B * env.world * K / Tmax) / tau
 
-    ctx.profile(True)
-    ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, 1, d_acc)
-    prof = ctx.profile_read()
-    ctx.profile(False)
+    prof, sites = profile_step(ctx, lambda: ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, 1, d_acc))
     roof = roofline_entry(prof, args.prec, peaks(), "chains16")
+    roof["sites"] = site_table(sites)
 
     errors = None
     if env.rank == 0 and args.oracle_sample > 0:
@@ -737,10 +755,8 @@ def run_chains16(env):
         T64 = env.rank_max(steps_timed(torch, c64, d_s64, d_lw64, d_acc, seed, 1, K64))
         fp64 = {"value": 2 * B * K64 * env.world / T64, "unit": UNIT, "steps": K64, "ms_per_step": 1e3 * T64 / K64}
         if not args.skip_separable:
-            c64.profile(True)
-            c64.cumulative_batch_dev(d_s64, d_lw64, 1, seed, 5 * 10 ** 6, 1, d_acc)
-            p_dense = c64.profile_read()
-            c64.profile(False)
+            p_dense, _ = profile_step(c64, lambda: c64.cumulative_batch_dev(d_s64, d_lw64, 1, seed, 5 * 10 ** 6, 1,
+                                                                            d_acc))
             sp = separable_arm(env, c64, d_s64, d_lw64, d_acc, seed, prec="fp64")
             # in the FP64 mode the stabilisation also runs on the FP64 GEMM: the dense
             # slice products are what the separable step no longer spends there
@@ -1037,6 +1053,8 @@ def run_effmodel16(env):
         row = {"L": L}
         # local DQMC sweeps
         cl = make_ctx(sldqmc, wlL, "fp64", B, 20)
+        if L >= 16:
+            cl.set_local_update_rank(32)
         sl = torch.from_numpy(batch_uniform(8400 + L, B, cl.M, cl.N)).cuda()
         cl.set_effective_model(cls16, J16, E016)
         for k in range(100):
@@ -1076,6 +1094,40 @@ def run_effmodel16(env):
             "fit_s": round(t_fit, 2), "tau_vs_L": taus, "chains": B, "series": args.effmodel_steps}
 
 
+# ------------------------------------------- delayed (rank-k) local updates
+def run_local_delayed(env):
+    """Local DQMC sweeps (the step-i training path) with immediate rank-1
+    Sherman-Morrison updates against delayed rank-32 updates, 16 chains at the
+    paper's critical point (beta=1, dtau=0.05, M=20) on 16x16 and 24x24."""
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    torch, sldqmc, args = env.torch, env.sldqmc, env.args
+    rows = []
+    B = args.tau_chains
+    for L in (16, 24):
+        wl = dict(CH16, L=L, beta=1.0)
+        row = {"L": L, "chains": B}
+        for k in (1, 32):
+            ctx = make_ctx(sldqmc, wl, "fp64", B, 20)
+            ctx.set_local_update_rank(k)
+            d_s = torch.from_numpy(batch_uniform(8500 + L, B, ctx.M, ctx.N)).cuda()
+            ctx.local_sweep_batch_dev(d_s, 87, 0, 1, want_stats=False)
+            torch.cuda.synchronize()
+            n_sw = 3
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ctx.local_sweep_batch_dev(d_s, 87, 1, n_sw, want_stats=False)
+            e1.record(st)
+            e1.synchronize()
+            dt = e0.elapsed_time(e1) / 1e3
+            row[f"rank{k}_sweeps_per_s"] = n_sw / dt
+            ctx.close()
+        row["speedup"] = row["rank32_sweeps_per_s"] / row["rank1_sweeps_per_s"]
+        rows.append(row)
+    return {"workload": "local DQMC sweeps, beta=1, dtau=0.05 (M=20), n_wrap=20, mu=-0.5, xi=1, FP64",
+            "rows": rows}
+
+
 def run_ours(args):
     env = Env(args)
     chosen = ALL_WORKLOADS if args.workloads == "all" else tuple(w for w in args.workloads.split(",") if w)
@@ -1098,6 +1150,8 @@ def run_ours(args):
         wls["critical"] = run_critical(env)
     if "effmodel16" in chosen:
         wls["effmodel16"] = run_effmodel16(env)
+    if "local_delayed" in chosen:
+        wls["local_delayed"] = run_local_delayed(env)
     if env.rank == 0:
         if head is None:
             # a partial run (no headline workload): the first workload's numbers head the line

@@ -149,6 +149,18 @@ int sldqmc_local_sweep(sldqmc_ctx *ctx, int8_t *s, uint64_t seed, uint64_t sweep
 int sldqmc_local_sweep_batch_dev(sldqmc_ctx *ctx, int8_t *d_s, int B, uint64_t seed,
                                  uint64_t sweep0, int n_sweeps, sldqmc_stats *stats);
 
+/* Delayed local updates ("Basics of DQMC": the O(N^2) Sherman-Morrison
+ * update per accepted flip).  k = 1 (default): every accepted flip updates
+ * both Green's functions at once (rank 1).  2 <= k <= 32: the sites of a
+ * slice are taken in blocks of k; inside a block the Green's function is
+ * kept as G0 - U V with one column/row pair per accepted flip (each site's
+ * diagonal element and each new pair cost O(N k) instead of O(N^2)), and
+ * after the block the rank-k correction is applied to every chain by one
+ * batched GEMM per flavour.  The flips, decisions and random numbers are
+ * those of k = 1; only the rounding of the Green's function differs (the
+ * decisions agree outside the 1e-8 margin). */
+int sldqmc_set_local_update_rank(sldqmc_ctx *ctx, int k);
+
 /* Effective model (Eq. 2): H_eff = E0 + sum_c J_c f_c(C),
  * f_c(C) = sum_x sum_{o in class c} s_x s_{x+o}.  Class c has n_off[c]
  * offsets (dx, dy, dtau), stored consecutively as int triples in offsets
@@ -320,6 +332,10 @@ int sldqmc_wait_selftest(sldqmc_ctx *ctx, int max_polls);
  * (ms) and the summed algorithmic flops, then clears the record. */
 int sldqmc_profile_enable(sldqmc_ctx *ctx, int on);
 int sldqmc_profile_read(sldqmc_ctx *ctx, long long *launches, double *ms, double *flops);
+/* Same record by launch site instead of by class: one text line per site,
+ * "site class launches ms flops", into buf (len bytes, NUL-terminated;
+ * lines that do not fit are dropped), then clears the record. */
+int sldqmc_profile_read_sites(sldqmc_ctx *ctx, char *buf, int len);
 
 #ifdef __cplusplus
 }

@@ -101,6 +101,7 @@ struct ProfRec {
     cudaEvent_t a, b;
     int cls;
     double flops;
+    const char *site;  // the launch site (a static string)
 };
 struct Prof {
     bool on = false;
@@ -110,7 +111,7 @@ struct Prof {
     int open_cls = -1;
     double open_flops = 0.0;
 };
-void prof_begin(sldqmc_ctx *c, int cls, double flops);
+void prof_begin(sldqmc_ctx *c, int cls, double flops, const char *site = nullptr);
 void prof_end(sldqmc_ctx *c);
 // Launch an FP64 GEMM on the context's stream (counted and, when on, timed).
 void gemm_ctx(sldqmc_ctx *c, const GemmF64 &g, bool TA, bool TB);
@@ -136,12 +137,15 @@ struct sldqmc_ctx {
     double *buf[9];    // Ut, V, X1, X2, W(2*nn), Y, R1, R2, Vg
     double *d_D, *d_Dp, *d_logacc;
     int *d_perm, *d_sgn, *d_piv;
+    int *d_tslu;       // row nominations of the tournament-pivoting LU panels (24 * 32 per item)
     void *tc_ws;       // tensor-core operand workspace (split copies)
     void *oz_ws;       // digit planes of the tensor-core Gram and Cholesky-QR (mixed modes, N >= 128)
     // Monte Carlo state
     int8_t *d_s_tmp;   // cap * M * N proposal buffer
     int8_t *d_s_one;   // staging for host calls
     double *d_G[2];    // Gt for the local sweep: cap items per flavour
+    double *d_U, *d_V; // pending pairs of the delayed local update: 2 flavours x cap x 32 N each
+    int local_rank;    // sites per delayed-update block (1: immediate rank-1 updates)
     double *d_ld_tmp, *d_ld_tmp2;
     int *d_sg_tmp;
     long long *d_stats; // cap * 4 (accepted, proposed, margin, drift bits)

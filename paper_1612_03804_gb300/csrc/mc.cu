@@ -168,12 +168,15 @@ __global__ void __launch_bounds__(512) k_local_flips(LocalArgs a)
                 row[e] = (k == i ? 1.0 : 0.0) - G[f][(long long)i * N + k];
             }
             __syncthreads();
-            const long long tot = 2 * (long long)N * N;
-            for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
-                const int f = (int)(e / ((long long)N * N));
-                const long long r = e % ((long long)N * N);
-                const int rr = (int)(r / N), k = (int)(r % N);
-                G[f][r] -= (coef[f] * col[f * N + rr]) * row[f * N + k];
+            // warp w takes rows w, w + nwarps, ...; its lanes walk the row's
+            // columns (coalesced, no index division)
+            const int nwarps = blockDim.x >> 5, wl = threadIdx.x & 31;
+            for (int fr = threadIdx.x >> 5; fr < 2 * N; fr += nwarps) {
+                const int f = fr >= N, rr = fr - f * N;
+                const double cf = coef[f] * col[f * N + rr];
+                double *g = G[f] + (long long)rr * N;
+                const double *rw = row + f * N;
+                for (int k = wl; k < N; k += 32) g[k] -= cf * rw[k];
             }
             __syncthreads();
         }
@@ -183,6 +186,140 @@ __global__ void __launch_bounds__(512) k_local_flips(LocalArgs a)
         a.stats[b * 4 + 1] += N;
         a.stats[b * 4 + 2] += n_mg;
     }
+}
+
+// ------------------------------------------------- delayed (rank-k) update
+// The same sequence of flips, decisions and Green's functions with the
+// Sherman-Morrison updates delayed: within a block of k <= 32 sites of slice
+// tau the current Green's function of flavour f is
+//   Gt_f = G0_f - U_f V_f,   U_f = [u_0 .. u_{n-1}] (N x n),  V_f = [v_0; ..; v_{n-1}] (n x N),
+// one column/row pair per accepted flip so far.  A site needs only
+// Gt_f[i][i] = G0_f[i][i] - U_f[i,:] V_f[:,i] (n terms); an accepted flip
+// at i appends u_n = (Delta_f / R_f) Gt_f[:, i] and v_n = e_i^T - Gt_f[i, :],
+// each formed from G0 and the n earlier pairs (2 N n multiply-adds instead
+// of the N^2 of an immediate update).  After the block the pending rank-k
+// correction G0 -= U V is applied by one batched GEMM over every chain
+// (unused pairs are zero), so the N^2 work per accepted flip runs as a GEMM
+// on all SMs instead of as rank-1 passes on one SM per chain.
+// U: per chain N x 32 (row stride 32), V: per chain 32 x N; flavour f of
+// chain b at U + (f * cap + b) * 32 N.
+struct DelayArgs {
+    LocalArgs l;
+    double *U, *V;
+    int cap;
+    int i0, ns;   // sites i0 .. i0 + ns - 1 of slice tau (ns <= 32)
+};
+
+__global__ void __launch_bounds__(512) k_local_flips_delayed(DelayArgs d)
+{
+    const LocalArgs &a = d.l;
+    const int b = blockIdx.x;
+    const int N = a.Lx * a.Ly;
+    const double *G[2] = {a.Gp + (long long)b * a.nn, a.Gm + (long long)b * a.nn};
+    double *U[2], *V[2];
+    for (int f = 0; f < 2; ++f) {
+        U[f] = d.U + ((long long)f * d.cap + b) * 32 * N;
+        V[f] = d.V + ((long long)f * d.cap + b) * 32 * N;
+    }
+    int8_t *s = a.s + (long long)b * a.M * N;
+    __shared__ double ui[2][32], vi[2][32];  // U[i, :n] and V[:n, i] of the current site
+    __shared__ double coef[2];
+    __shared__ int accept;
+    const uint64_t seed = a.seed + ((uint64_t)b << 32);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    long long n_acc = 0, n_mg = 0;
+    const int tau = a.tau;
+    int n = 0;  // pending pairs
+    for (int q = 0; q < d.ns; ++q) {
+        const int i = d.i0 + q;
+        if (wid == 0) {
+            // U[i, j] and V[j, i] for j < n, and the current diagonals
+            double dg[2];
+            for (int f = 0; f < 2; ++f) {
+                const double uu = lane < n ? U[f][(long long)i * 32 + lane] : 0.0;
+                const double vv = lane < n ? V[f][(long long)lane * N + i] : 0.0;
+                ui[f][lane] = uu;
+                vi[f][lane] = vv;
+                double p = uu * vv;
+                for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+                dg[f] = G[f][(long long)i * N + i] - p;
+            }
+            if (lane == 0) {
+                const int sold = s[tau * N + i];
+                const int x = i % a.Lx, y = i / a.Lx;
+                int nsp = 0;
+                if (a.Lx > 1) nsp += s[tau * N + wrapi(x + 1, a.Lx) + a.Lx * y] + s[tau * N + wrapi(x - 1, a.Lx) + a.Lx * y];
+                if (a.Ly > 1) nsp += s[tau * N + x + a.Lx * wrapi(y + 1, a.Ly)] + s[tau * N + x + a.Lx * wrapi(y - 1, a.Ly)];
+                const int ntm = s[wrapi(tau + 1, a.M) * N + i] + s[wrapi(tau - 1, a.M) * N + i];
+                double logr = __dmul_rn(-2.0 * (double)sold,
+                                        __dadd_rn(__dmul_rn(a.dtauJ, (double)nsp), __dmul_rn(a.Kt, (double)ntm)));
+                double R[2], Dl[2];
+                for (int f = 0; f < 2; ++f) {
+                    const double eta = f == 0 ? 1.0 : -1.0;
+                    Dl[f] = exp(-2.0 * eta * a.dtxi * (double)sold) - 1.0;
+                    R[f] = __dadd_rn(1.0, __dmul_rn(Dl[f], __dadd_rn(1.0, -dg[f])));
+                    logr = __dadd_rn(logr, __dmul_rn(2.0, log(fabs(R[f]))));
+                }
+                const double u = philox_uniform(seed, (uint32_t)i, (uint32_t)tau, a.sweep, PURPOSE_LOCAL);
+                const double lu = log(u);
+                if (fabs(logr - lu) <= MARGIN) n_mg++;
+                const int acc = lu < logr;
+                accept = acc;
+                if (acc) {
+                    coef[0] = Dl[0] / R[0];
+                    coef[1] = Dl[1] / R[1];
+                    s[tau * N + i] = (int8_t)(-sold);
+                    n_acc++;
+                }
+            }
+        }
+        __syncthreads();
+        if (accept) {
+            // u_n = coef (G0[:, i] - U[:, :n] V[:n, i]),  v_n = e_i - (G0[i, :] - U[i, :n] V[:n, :])
+            for (int e = tid; e < 2 * N; e += blockDim.x) {
+                const int f = e >= N, r = e - f * N;
+                double c = G[f][(long long)r * N + i];
+                const double *ur = U[f] + (long long)r * 32;
+                double w = G[f][(long long)i * N + r];
+                for (int j = 0; j < n; ++j) {
+                    c -= ur[j] * vi[f][j];
+                    w -= ui[f][j] * V[f][(long long)j * N + r];
+                }
+                U[f][(long long)r * 32 + n] = coef[f] * c;
+                V[f][(long long)n * N + r] = (r == i ? 1.0 : 0.0) - w;
+            }
+            ++n;
+        }
+        __syncthreads();
+    }
+    // unused pairs are zero for the batched correction
+    for (int f = 0; f < 2; ++f) {
+        for (long long e = tid; e < (long long)N * (32 - n); e += blockDim.x) {
+            const int r = (int)(e / (32 - n)), j = n + (int)(e % (32 - n));
+            U[f][(long long)r * 32 + j] = 0.0;
+        }
+        for (long long e = tid; e < (long long)(32 - n) * N; e += blockDim.x) V[f][(long long)n * N + e] = 0.0;
+    }
+    if (tid == 0) {
+        a.stats[b * 4 + 0] += n_acc;
+        a.stats[b * 4 + 1] += d.ns;
+        a.stats[b * 4 + 2] += n_mg;
+    }
+}
+
+void launch_local_flips_delayed(sldqmc_ctx *c, double *Gp, double *Gm, double *U, double *V, int8_t *d_s, int B,
+                                int tau, int i0, int ns, uint32_t sweep, uint64_t seed, long long *stats)
+{
+    DelayArgs d;
+    LocalArgs &a = d.l;
+    a.Gp = Gp; a.Gm = Gm; a.nn = c->nn; a.s = d_s;
+    a.Lx = c->p.Lx; a.Ly = c->p.Ly; a.M = c->M; a.tau = tau; a.sweep = sweep; a.seed = seed;
+    a.dtxi = c->p.dtau * c->p.xi; a.dtauJ = c->dtauJ; a.Kt = c->Ktau; a.stats = stats;
+    d.U = U; d.V = V; d.cap = c->cap; d.i0 = i0; d.ns = ns;
+    prof_begin(c, SLDQMC_KC_LOCAL, 0.0, "local_flips_delayed");
+    k_local_flips_delayed<<<B, 512, 0, c->st>>>(d);
+    prof_end(c);
+    c->launches++;
 }
 
 // Gt <- D_tau Gt D_tau^{-1} applied after the two wrap GEMMs is fused into
@@ -398,7 +535,7 @@ void launch_local_flips(sldqmc_ctx *c, double *Gp, double *Gm, int8_t *d_s, int 
     a.dtxi = c->p.dtau * c->p.xi; a.dtauJ = c->dtauJ; a.Kt = c->Ktau; a.stats = stats;
     size_t sh = sizeof(double) * 4 * (size_t)c->N;
     int nt = c->N * c->N >= 512 ? 512 : 256;
-    prof_begin(c, SLDQMC_KC_LOCAL, 0.0);
+    prof_begin(c, SLDQMC_KC_LOCAL, 0.0, "local_flips");
     k_local_flips<<<B, nt, sh, c->st>>>(a);
     prof_end(c);
     c->launches++;
@@ -417,7 +554,7 @@ void launch_eff_sweeps(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t
     const long long V = (long long)c->N * c->M;
     const int nt = 1024;
     const EffModel em = eff_model_of(c);
-    prof_begin(c, SLDQMC_KC_EFF, 0.0);
+    prof_begin(c, SLDQMC_KC_EFF, 0.0, "eff_sweeps");
     if (V <= 200 * 1024) {
         k_eff_sweeps<true><<<B, nt, (size_t)V, c->st>>>(d_s, c->p.Lx, c->p.Ly, c->M, c->p.beta,
                                                         em, c->d_col_start, c->d_col_sites,

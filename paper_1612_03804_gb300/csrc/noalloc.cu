@@ -91,6 +91,7 @@ size_t layout(sldqmc_ctx *c, uintptr_t base, double **ring)
     c->d_perm = k.take<int>(N * B);
     c->d_piv = k.take<int>(N * B);
     c->d_sgn = k.take<int>(2 * B);
+    c->d_tslu = k.take<int>(24 * 32 * B);
     return k.off;
 }
 

@@ -467,8 +467,23 @@ struct OzArgs {
     long long sEB;
     long long splane_stride;  // SLICE: plane stride, leading dimension, plane rows per item,
     int sldp, srows, skoff;   // and the K position of n = 0
+    int a_tri, b_tri;         // A upper triangular (A[m][k] = 0 for k < m) / B^T upper triangular
+                              // (B[n][k] = 0 for k > n): a tile's K-blocks start at m0 / 32 / end
+                              // after the one holding n0 + 31 (kA0 = kB0 = 0)
     int *flag;
 };
+
+// K-blocks [k_lo, k_hi) that can hold nonzero products for the tile at (m0, n0).
+__device__ __forceinline__ void oz_krange(const OzArgs &a, int m0, int n0, int &k_lo, int &k_hi)
+{
+    k_lo = a.a_tri ? m0 / OKE : 0;
+    k_hi = a.nk;
+    if (a.b_tri) {
+        const int e = (n0 + OBN + OKE - 1) / OKE;
+        if (e < k_hi) k_hi = e;
+    }
+    if (k_hi < k_lo) k_hi = k_lo;
+}
 
 // Tile t of the persistent walk -> (item, first row, first column).  UPPER:
 // the 128 x 32 tiles on or above the diagonal; otherwise every tile, columns
@@ -575,7 +590,9 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                 oz_locate<UPPER>(a, t, tiles0, part, b, m0, n0);
                 const CUtensorMap *mA = part ? &tA1 : &tA0;
                 const int arow0 = part ? a.pt[1].arow0 : a.pt[0].arow0;
-                for (int kb = 0; kb < a.nk; ++kb, ++it) {
+                int k_lo, k_hi;
+                oz_krange(a, m0, n0, k_lo, k_hi);
+                for (int kb = k_lo; kb < k_hi; ++kb, ++it) {
                     const int s = it % OSTAGES;
                     if (it >= OSTAGES && !mbar_wait(&empty[s], ((it / OSTAGES) - 1) & 1, a.flag)) { ok = false; break; }
                     mbar_expect_tx(&full[s], OSTAGE);
@@ -594,14 +611,17 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             int it = 0, cc = 0;  // K-block and chunk counters of this CTA
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-                for (int kc0 = 0; kc0 < a.nk && ok; kc0 += OZ_KCHUNK, ++cc) {
+                int part, b, m0, n0, k_lo, k_hi;
+                oz_locate<UPPER>(a, t, tiles0, part, b, m0, n0);
+                oz_krange(a, m0, n0, k_lo, k_hi);
+                for (int kc0 = k_lo; kc0 < k_hi && ok; kc0 += OZ_KCHUNK, ++cc) {
                     const int u = cc & 1;
                     // the epilogue must have drained this buffer (used two chunks ago)
                     if (cc >= 2 && !mbar_wait(&tmem_free[u], ((cc >> 1) - 1) & 1, a.flag)) { ok = false; break; }
                     fence_after();
                     const uint32_t acc0 = tmem + (uint32_t)(u * OZ_G * OBN);
                     uint32_t started = 0;
-                    const int kc1 = kc0 + OZ_KCHUNK < a.nk ? kc0 + OZ_KCHUNK : a.nk;
+                    const int kc1 = kc0 + OZ_KCHUNK < k_hi ? kc0 + OZ_KCHUNK : k_hi;
                     for (int kb = kc0; kb < kc1; ++kb, ++it) {
                         const int s = it % OSTAGES;
                         if (!mbar_wait(&full[s], (it / OSTAGES) & 1, a.flag)) { ok = false; break; }
@@ -663,7 +683,9 @@ __global__ void __launch_bounds__(OTHREADS, 1)
             double w[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) w[j] = 0.0;
-            for (int kc0 = 0; kc0 < a.nk; kc0 += OZ_KCHUNK, ++cc) {
+            int k_lo, k_hi;
+            oz_krange(a, m0, n0, k_lo, k_hi);
+            for (int kc0 = k_lo; kc0 < k_hi; kc0 += OZ_KCHUNK, ++cc) {
                 const int u = cc & 1;
                 ok = mbar_wait(&tmem_full[u], (cc >> 1) & 1, a.flag);
                 fence_after();
@@ -691,7 +713,7 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                         }
                     }
                     // the chunk's value (one rounding); the first chunk needs no addition
-                    if (kc0 == 0) {
+                    if (kc0 == k_lo) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) w[half * 8 + j] = fma((double)l[j], 0x1p-28, (double)h[j]);
                     } else {
@@ -898,8 +920,10 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_oz_slice");
     k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(X, sX, N, N, N, N, w->ldp, w->plane_stride, w->planes,
                                                          w->E);
+    prof_end(c);
     OzArgs a{};
     a.pt[0] = oz_part(N, 0, w->E, N, W, sW, ldw);
     a.nparts = 1;
@@ -909,7 +933,7 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
     a.EB = w->E;
     a.sEB = N;
     a.flag = c->d_flag;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B);
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B, "oz_gram");
     k_oz_gemm<true, false><<<oz_grid<true>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapA, w->mapB, a);
     prof_end(c);
     c->launches += 2;
@@ -930,7 +954,9 @@ void oz_chol_begin(sldqmc_ctx *c, const double *W, long long sW, int B)
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_oz_col_exponents");
     k_oz_col_exponents<<<dim3((N + 255) / 256, B), 256, 0, c->st>>>(W, sW, N, N, w->ER);
+    prof_end(c);
     c->launches++;
 }
 
@@ -949,7 +975,7 @@ void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, doub
     a.EB = w->ER + k0;
     a.sEB = N;
     a.flag = c->d_flag;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * (2 * N - k0) * kb * k0 * B);
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * (2 * N - k0) * kb * k0 * B, "oz_chol_update");
     k_oz_gemm<false, true, true>
         <<<oz_grid<false>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRA, w->mapRB, a);
     prof_end(c);
@@ -982,9 +1008,11 @@ void oz_chol_panel(sldqmc_ctx *c, int k0, int kb, const double *W, long long sW,
     sl.j0[1] = j0;
     sl.planes[1] = w->rplanes;
     sl.E[1] = w->EPW;
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_oz_slice_panel");
     k_oz_slice_panel<<<dim3(sl.nb0 + (nW + 31) / 32, B), 256, 0, c->st>>>(sl, N, N, kb, k0, w->plane_stride,
                                                                            w->ldp, c->d_flag);
-    prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * 2.0 * kb * kb * kb / 3.0);
+    prof_end(c);
+    prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * 2.0 * kb * kb * kb / 3.0, "oz_chol_factor");
     k_oz_chol_factor<<<B, 128, 0, c->st>>>(W, sW, N, R, c->nn, N, k0, kb, w->tplanes, w->tplane_stride, w->ET,
                                            c->d_flag);
     prof_end(c);
@@ -1013,7 +1041,7 @@ void oz_chol_panel(sldqmc_ctx *c, int k0, int kb, const double *W, long long sW,
     a.srows = N;
     a.skoff = k0;
     a.flag = c->d_flag;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * (N + nW) * kb * kb * B);
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * (N + nW) * kb * kb * B, "oz_chol_panel");
     k_oz_gemm<false, false, true, true>
         <<<oz_grid<false>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRA, w->mapT, a);
     prof_end(c);
@@ -1030,8 +1058,10 @@ void oz_lu_update(sldqmc_ctx *c, double *A, long long sA, int lda, int k0, int k
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
     const int j0 = k0 + kb, M = N - j0;
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_oz_slice");
     k_oz_slice<<<dim3((M + 7) / 8, B), 256, 0, c->st>>>(A + (long long)j0 * lda + k0, sA, M, kb, lda, N, w->ldp,
                                                          w->plane_stride, w->planes, w->E);
+    prof_end(c);
     OzPanelSlice sl{};
     sl.src[0] = A + (long long)k0 * lda;
     sl.sS[0] = sA;
@@ -1039,7 +1069,9 @@ void oz_lu_update(sldqmc_ctx *c, double *A, long long sA, int lda, int k0, int k
     sl.planes[0] = w->rplanes;
     sl.E[0] = w->EPW;
     sl.nb0 = (M + 31) / 32;
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_oz_slice_panel");
     k_oz_slice_panel<<<dim3(sl.nb0, B), 256, 0, c->st>>>(sl, N, lda, kb, 0, w->plane_stride, w->ldp, c->d_flag);
+    prof_end(c);
     OzArgs a{};
     a.pt[0] = oz_part(M, 0, w->E, N, A + (long long)j0 * lda + j0, sA, lda);
     a.nparts = 1;
@@ -1050,7 +1082,7 @@ void oz_lu_update(sldqmc_ctx *c, double *A, long long sA, int lda, int k0, int k
     a.EB = w->EPW + j0;
     a.sEB = N;
     a.flag = c->d_flag;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * M * M * kb * B);
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * M * M * kb * B, "oz_lu_update");
     k_oz_gemm<false, true, false, false>
         <<<oz_grid<false>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapA, w->mapRB, a);
     prof_end(c);
@@ -1065,10 +1097,14 @@ void oz_update_V(sldqmc_ctx *c, const double *R, double *V, double *Ts, int B)
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_oz_make_T");
     k_oz_make_T<<<dim3((N + 255) / 256, N, B), 256, 0, c->st>>>(R, c->nn, N, c->d_D, c->d_Dp, Ts);
+    prof_end(c);
     k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(Ts, c->nn, N, N, N, N, w->ldp, w->plane_stride, w->planes,
                                                          w->E);
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_oz_col_max_exponents");
     k_oz_col_max_exponents<<<dim3((N + 31) / 32, B), 256, 0, c->st>>>(V, c->nn, N, N, w->ER1);
+    prof_end(c);
     k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
         V, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag, c->d_perm, N);
     OzArgs a{};
@@ -1079,8 +1115,9 @@ void oz_update_V(sldqmc_ctx *c, const double *R, double *V, double *Ts, int B)
     a.nk = w->ldp / OKE;
     a.EB = w->ER1;
     a.sEB = N;
+    a.a_tri = 1;  // T is upper triangular: tile rows m0.. need K >= m0 only
     a.flag = c->d_flag;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B);
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * (N + 1) * B, "oz_update_V");
     k_oz_gemm<false, false><<<oz_grid<false>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapA, w->mapRB, a);
     prof_end(c);
     c->launches += 5;
@@ -1102,8 +1139,10 @@ void oz_r2r1(sldqmc_ctx *c, const double *R2, const double *R1, double *R, int B
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_oz_slice");
     k_oz_slice<<<dim3((N + 7) / 8, B), 256, 0, c->st>>>(R2, c->nn, N, N, N, N, w->ldp, w->plane_stride, w->planes,
                                                          w->E);
+    prof_end(c);
     k_oz_slice_fixed<<<dim3((N + 31) / 32, B, (N + 31) / 32), 256, 0, c->st>>>(
         R1, c->nn, N, 0, N, N, 0, w->plane_stride, N, w->ldp, w->rplanes, w->ER1, N, c->d_flag);
     OzArgs a{};
@@ -1114,8 +1153,10 @@ void oz_r2r1(sldqmc_ctx *c, const double *R2, const double *R1, double *R, int B
     a.nk = w->ldp / OKE;
     a.EB = w->ER1;
     a.sEB = N;
+    a.a_tri = 1;  // R2[m][l] = 0 for l < m and R1[l][n] = 0 for l > n
+    a.b_tri = 1;
     a.flag = c->d_flag;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * N / 3.0 * B);
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, (double)N * N * N / 3.0 * B, "oz_r2r1");
     k_oz_gemm<true, false><<<oz_grid<true>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapA, w->mapRB, a);
     prof_end(c);
     c->launches += 3;

@@ -37,6 +37,7 @@ namespace sldqmc {
 namespace {
 
 constexpr int SEP_THREADS = 512;
+constexpr int XB = 8;  // outputs per thread along a line (register blocking)
 
 struct SepArgs {
     const double *Ut;     // B items of N x N (row stride N, item stride nn)
@@ -50,65 +51,30 @@ struct SepArgs {
     const double *ex;     // ring propagators E1x (Lx), E1y (Ly)
     const double *ey;
     double emu;           // e^{dtau mu}
+    int R;                // rows of X^T held by a CTA at a time
+    int P;                // line stride of a row image in shared memory (odd, >= Lx)
 };
 
-__device__ __forceinline__ double field_scale(const SepArgs &a, const int8_t *sl, int i)
-{
-    return sl[i] > 0 ? a.cu : a.cd;
-}
-
-// FP64: one row per CTA iteration, persistent over the B*N rows.
-__global__ void __launch_bounds__(SEP_THREADS) k_sep_block_f64(SepArgs a)
-{
-    extern __shared__ double sm[];
-    double *v = sm, *z = sm + a.N, *ex = z + a.N, *ey = ex + a.Lx;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < a.Lx; i += SEP_THREADS) ex[i] = a.ex[i];
-    for (int i = tid; i < a.Ly; i += SEP_THREADS) ey[i] = a.emu * a.ey[i];
-    const long long rows = (long long)a.B * a.N;
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int b = (int)(row / a.N);
-        const double *src = a.Ut + b * a.nn + (row - (long long)b * a.N) * a.N;
-        const int8_t *fs = a.s + b * a.sS;
-        const int8_t *sl0 = fs + (long long)(a.t0 % a.M) * a.N;
-        __syncthreads();  // the previous row is stored, ex/ey are loaded
-        for (int i = tid; i < a.N; i += SEP_THREADS) v[i] = src[i] * field_scale(a, sl0, i);
-        __syncthreads();
-        for (int j = 0; j < a.nb; ++j) {
-            // along x: z[y][xo] = sum_d E1x(d) v[y][(xo + d) mod Lx]
-            for (int o = tid; o < a.N; o += SEP_THREADS) {
-                const int y = o / a.Lx, xo = o - y * a.Lx;
-                const double *vr = v + y * a.Lx;
-                double acc = 0.0;
-                int x = xo;
-                for (int d = 0; d < a.Lx; ++d) {
-                    acc = fma(vr[x], ex[d], acc);
-                    if (++x == a.Lx) x = 0;
-                }
-                z[o] = acc;
-            }
-            __syncthreads();
-            // along y, with e^{dtau mu} and the next slice's field scale:
-            // v[yo][x] = d_next * sum_d e^{dtau mu} E1y(d) z[(yo + d) mod Ly][x]
-            const int8_t *sln = j + 1 < a.nb ? fs + (long long)((a.t0 + j + 1) % a.M) * a.N : nullptr;
-            for (int o = tid; o < a.N; o += SEP_THREADS) {
-                const int yo = o / a.Lx, x = o - yo * a.Lx;
-                double acc = 0.0;
-                int y = yo;
-                for (int d = 0; d < a.Ly; ++d) {
-                    acc = fma(z[y * a.Lx + x], ey[d], acc);
-                    if (++y == a.Ly) y = 0;
-                }
-                v[o] = sln ? acc * field_scale(a, sln, o) : acc;
-            }
-            __syncthreads();
+// Value types: FP64, or an unevaluated pair hi + lo of floats.
+struct F64 {
+    using T = double;
+    struct Acc {
+        double a[XB];
+        __device__ __forceinline__ void zero()
+        {
+#pragma unroll
+            for (int k = 0; k < XB; ++k) a[k] = 0.0;
         }
-        double *dst = a.Xt + b * a.nn + (row - (long long)b * a.N) * a.N;
-        for (int i = tid; i < a.N; i += SEP_THREADS) dst[i] = v[i];
-    }
-}
+        __device__ __forceinline__ void mac(int k, int, double w, double e) { a[k] = fma(w, e, a[k]); }
+        __device__ __forceinline__ double get(int k) const { return a[k]; }
+    };
+    static __device__ __forceinline__ double from(double x) { return x; }
+    static __device__ __forceinline__ double to(double v) { return v; }
+    static __device__ __forceinline__ double scale(double v, double d) { return v * d; }
+    static __device__ __forceinline__ double zero() { return 0.0; }
+};
 
-// (hi, lo) <- hi + lo renormalised so that |lo| <= ulp(hi)/2 (Fast2Sum; |hi| >= |lo|).
+// (hi, lo) <- hi + lo renormalised (Fast2Sum; |hi| >= |lo|).
 __device__ __forceinline__ float2 renorm(float hi, float lo)
 {
     const float s = hi + lo;
@@ -123,107 +89,194 @@ __device__ __forceinline__ float2 two_sum(float a, float b)
     return make_float2(s, (a - (s - bp)) + (b - bp));
 }
 
-__device__ __forceinline__ float2 split_pair(double x)
-{
-    const float h = (float)x;
-    return make_float2(h, (float)(x - (double)h));
-}
-
-// pair * pair (scale by a field factor): hi*hi exactly (FMA residual) plus the cross terms.
-__device__ __forceinline__ float2 mul_pair(float2 v, float2 d)
-{
-    const float p = v.x * d.x;
-    const float e = fmaf(v.x, d.x, -p);
-    return renorm(p, fmaf(v.x, d.y, fmaf(v.y, d.x, e)));
-}
-
-// One circular convolution of length L of pair data: acc over d of
-// w[(o0 + d) mod L] * e[d], w at stride `stride`; leading terms on two
-// accumulators, cross terms on a third, combined without FP64.
-__device__ __forceinline__ float2 conv_pair(const float2 *w, int stride, int o0, int L, const float2 *e)
-{
-    float a0 = 0.0f, a1 = 0.0f, c = 0.0f;
-    int k = o0;
-    int d = 0;
-    for (; d + 1 < L; d += 2) {
-        const float2 w0 = w[k * stride];
-        const float2 e0 = e[d];
-        if (++k == L) k = 0;
-        const float2 w1 = w[k * stride];
-        const float2 e1 = e[d + 1];
-        if (++k == L) k = 0;
-        a0 = fmaf(w0.x, e0.x, a0);
-        c = fmaf(w0.x, e0.y, c);
-        c = fmaf(w0.y, e0.x, c);
-        a1 = fmaf(w1.x, e1.x, a1);
-        c = fmaf(w1.x, e1.y, c);
-        c = fmaf(w1.y, e1.x, c);
+struct F32x2 {
+    using T = float2;
+    // per output: leading products on two accumulators (even and odd d), the
+    // cross terms hi*e_lo + lo*e_hi on a third
+    struct Acc {
+        float a0[XB], a1[XB], c[XB];
+        __device__ __forceinline__ void zero()
+        {
+#pragma unroll
+            for (int k = 0; k < XB; ++k) a0[k] = a1[k] = c[k] = 0.0f;
+        }
+        __device__ __forceinline__ void mac(int k, int par, float2 w, float2 e)
+        {
+            if (par) a1[k] = fmaf(w.x, e.x, a1[k]);
+            else a0[k] = fmaf(w.x, e.x, a0[k]);
+            c[k] = fmaf(w.x, e.y, c[k]);
+            c[k] = fmaf(w.y, e.x, c[k]);
+        }
+        __device__ __forceinline__ float2 get(int k) const
+        {
+            const float2 s = two_sum(a0[k], a1[k]);
+            return renorm(s.x, s.y + c[k]);
+        }
+    };
+    static __device__ __forceinline__ float2 from(double x)
+    {
+        const float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
     }
-    if (d < L) {
-        const float2 w0 = w[k * stride];
-        const float2 e0 = e[d];
-        a0 = fmaf(w0.x, e0.x, a0);
-        c = fmaf(w0.x, e0.y, c);
-        c = fmaf(w0.y, e0.x, c);
+    static __device__ __forceinline__ double to(float2 v) { return (double)v.x + (double)v.y; }
+    // pair * pair: hi*hi exactly (FMA residual) plus the cross terms
+    static __device__ __forceinline__ float2 scale(float2 v, float2 d)
+    {
+        const float p = v.x * d.x;
+        const float e = fmaf(v.x, d.x, -p);
+        return renorm(p, fmaf(v.x, d.y, fmaf(v.y, d.x, e)));
     }
-    const float2 s = two_sum(a0, a1);
-    return renorm(s.x, s.y + c);
+    static __device__ __forceinline__ float2 zero() { return make_float2(0.0f, 0.0f); }
+};
+
+// XB outputs of one line: out[k] = sum_d e[d] w[(o0 + k + d) mod L], the line's
+// values at stride `st` from w; e zero-padded to a multiple of XB.  The
+// window of 2 XB - 1 values of a d-block sits in registers, so a value read
+// from shared memory serves XB products.
+template <class V>
+__device__ __forceinline__ void conv_line(const typename V::T *w, int st, int L, int o0, const typename V::T *e,
+                                          int Lpad, typename V::Acc &acc)
+{
+    using T = typename V::T;
+    acc.zero();
+    T win[2 * XB - 1];
+    int li = o0;  // index of the next value to load, kept in [0, L)
+#pragma unroll
+    for (int j = 0; j < XB - 1; ++j) {
+        win[XB + j] = w[li * st];
+        if (++li == L) li = 0;
+    }
+    for (int d0 = 0; d0 < Lpad; d0 += XB) {
+#pragma unroll
+        for (int j = 0; j < XB - 1; ++j) win[j] = win[XB + j];
+#pragma unroll
+        for (int j = XB - 1; j < 2 * XB - 1; ++j) {
+            win[j] = w[li * st];
+            if (++li == L) li = 0;
+        }
+#pragma unroll
+        for (int t = 0; t < XB; ++t) {
+            const T et = e[d0 + t];
+#pragma unroll
+            for (int k = 0; k < XB; ++k) acc.mac(k, t & 1, win[k + t], et);
+        }
+    }
 }
 
-__global__ void __launch_bounds__(SEP_THREADS) k_sep_block_f32x2(SepArgs a)
+// Each CTA holds R rows of X^T as Ly x Lx images (line stride P, odd, so
+// that lanes reading consecutive lines of the x pass hit different banks),
+// persistent over the B*N rows.  Per slice: the x pass (lines = image rows,
+// work item = line x output block, consecutive lanes on consecutive lines),
+// then the y pass (lines = image columns, consecutive lanes on consecutive
+// columns) with e^{dtau mu} and the next slice's field scale.
+template <class V>
+__global__ void __launch_bounds__(SEP_THREADS) k_sep_block(SepArgs a)
 {
-    extern __shared__ float2 sm2[];
-    float2 *v = sm2, *z = sm2 + a.N, *ex = z + a.N, *ey = ex + a.Lx;
+    using T = typename V::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int Lx = a.Lx, Ly = a.Ly, N = a.N, P = a.P, R = a.R;
+    const int img = Ly * P;
+    const int Lxp = (Lx + XB - 1) / XB * XB, Lyp = (Ly + XB - 1) / XB * XB;
+    T *v = reinterpret_cast<T *>(smraw);
+    T *z = v + (size_t)R * img;
+    T *ex = z + (size_t)R * img;
+    T *ey = ex + Lxp;
     const int tid = threadIdx.x;
-    for (int i = tid; i < a.Lx; i += SEP_THREADS) ex[i] = split_pair(a.ex[i]);
-    for (int i = tid; i < a.Ly; i += SEP_THREADS) ey[i] = split_pair(a.emu * a.ey[i]);
-    const float2 du = split_pair(a.cu), dd = split_pair(a.cd);
-    const long long rows = (long long)a.B * a.N;
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int b = (int)(row / a.N);
-        const double *src = a.Ut + b * a.nn + (row - (long long)b * a.N) * a.N;
-        const int8_t *fs = a.s + b * a.sS;
-        const int8_t *sl0 = fs + (long long)(a.t0 % a.M) * a.N;
-        __syncthreads();
-        for (int i = tid; i < a.N; i += SEP_THREADS) v[i] = split_pair(src[i] * field_scale(a, sl0, i));
+    for (int i = tid; i < Lxp; i += SEP_THREADS) ex[i] = i < Lx ? V::from(a.ex[i]) : V::zero();
+    for (int i = tid; i < Lyp; i += SEP_THREADS) ey[i] = i < Ly ? V::from(a.emu * a.ey[i]) : V::zero();
+    const T du = V::from(a.cu), dd = V::from(a.cd);
+    const long long rows = (long long)a.B * N;
+    const int nbx = Lxp / XB, nby = Lyp / XB;
+    for (long long row0 = (long long)blockIdx.x * R; row0 < rows; row0 += (long long)gridDim.x * R) {
+        const int nr = rows - row0 < R ? (int)(rows - row0) : R;
+        __syncthreads();  // the previous rows are stored; ex, ey are loaded
+        for (int e = tid; e < nr * N; e += SEP_THREADS) {
+            const int r = e / N, i = e - r * N;
+            const long long row = row0 + r;
+            const int b = (int)(row / N);
+            const int8_t *sl0 = a.s + b * a.sS + (long long)(a.t0 % a.M) * N;
+            const double x = a.Ut[b * a.nn + (row - (long long)b * N) * N + i];
+            const int y = i / Lx;
+            v[r * img + y * P + (i - y * Lx)] = V::from(x * (sl0[i] > 0 ? a.cu : a.cd));
+        }
         __syncthreads();
         for (int j = 0; j < a.nb; ++j) {
-            for (int o = tid; o < a.N; o += SEP_THREADS) {
-                const int y = o / a.Lx, xo = o - y * a.Lx;
-                z[o] = conv_pair(v + y * a.Lx, 1, xo, a.Lx, ex);
+            // along x: z[r][y][xo] = sum_d E1x(d) v[r][y][(xo + d) mod Lx]
+            const int lx = nr * Ly;
+            for (int w = tid; w < lx * nbx; w += SEP_THREADS) {
+                const int line = w % lx, o0 = (w / lx) * XB;
+                const int r = line / Ly, y = line - r * Ly;
+                typename V::Acc acc;
+                conv_line<V>(v + r * img + y * P, 1, Lx, o0, ex, Lxp, acc);
+                T *zo = z + r * img + y * P;
+#pragma unroll
+                for (int k = 0; k < XB; ++k)
+                    if (o0 + k < Lx) zo[o0 + k] = acc.get(k);
             }
             __syncthreads();
-            const int8_t *sln = j + 1 < a.nb ? fs + (long long)((a.t0 + j + 1) % a.M) * a.N : nullptr;
-            for (int o = tid; o < a.N; o += SEP_THREADS) {
-                const int yo = o / a.Lx, x = o - yo * a.Lx;
-                const float2 r = conv_pair(z + x, a.Lx, yo, a.Ly, ey);
-                v[o] = sln ? mul_pair(r, sln[o] > 0 ? du : dd) : r;
+            // along y, times e^{dtau mu} (in ey) and the next slice's field scale
+            const bool more = j + 1 < a.nb;
+            const int ly = nr * Lx;
+            for (int w = tid; w < ly * nby; w += SEP_THREADS) {
+                const int line = w % ly, o0 = (w / ly) * XB;
+                const int r = line / Lx, x = line - r * Lx;
+                typename V::Acc acc;
+                conv_line<V>(z + r * img + x, P, Ly, o0, ey, Lyp, acc);
+                const long long row = row0 + r;
+                const int b = (int)(row / N);
+                const int8_t *sln = more ? a.s + b * a.sS + (long long)((a.t0 + j + 1) % a.M) * N : nullptr;
+                T *vo = v + r * img + x;
+#pragma unroll
+                for (int k = 0; k < XB; ++k) {
+                    const int y = o0 + k;
+                    if (y < Ly) {
+                        const T val = acc.get(k);
+                        vo[y * P] = more ? V::scale(val, sln[y * Lx + x] > 0 ? du : dd) : val;
+                    }
+                }
             }
             __syncthreads();
         }
-        double *dst = a.Xt + b * a.nn + (row - (long long)b * a.N) * a.N;
-        for (int i = tid; i < a.N; i += SEP_THREADS) dst[i] = (double)v[i].x + (double)v[i].y;
+        for (int e = tid; e < nr * N; e += SEP_THREADS) {
+            const int r = e / N, i = e - r * N;
+            const long long row = row0 + r;
+            const int b = (int)(row / N);
+            const int y = i / Lx;
+            a.Xt[b * a.nn + (row - (long long)b * N) * N + i] = V::to(v[r * img + y * P + (i - y * Lx)]);
+        }
     }
 }
 
-size_t sep_smem_bytes(int N, int Lx, int Ly)
+int odd_stride(int Lx) { return Lx | 1; }
+
+size_t sep_smem_bytes(int Lx, int Ly, int R)
 {
-    return sizeof(double) * (2 * (size_t)N + Lx + Ly);
+    const int Lxp = (Lx + XB - 1) / XB * XB, Lyp = (Ly + XB - 1) / XB * XB;
+    return 8 * (2 * (size_t)R * Ly * odd_stride(Lx) + Lxp + Lyp);
+}
+
+// Rows per CTA: enough that a CTA's passes have several thousand outputs
+// between barriers, within the shared memory of one CTA.
+int sep_rows_per_cta(int N, int Lx, int Ly)
+{
+    int R = 1;
+    while (R < 32 && (long long)(2 * R) * N <= 4096 && sep_smem_bytes(Lx, Ly, 2 * R) <= 200 * 1024) R *= 2;
+    return R;
 }
 
 }  // namespace
 
-// Largest lattice the shared-memory row kernel takes (two rows of 8-byte
-// values and the ring propagators within 227 KB).
+// Largest lattice the shared-memory row kernel takes (two images of one
+// row of 8-byte values and the ring propagators within 227 KB).
 bool sep_supported(int Lx, int Ly)
 {
-    return sep_smem_bytes(Lx * Ly, Lx, Ly) <= 227 * 1024;
+    return sep_smem_bytes(Lx, Ly, 1) <= 227 * 1024;
 }
 
 void sep_set_limits()
 {
-    cudaFuncSetAttribute(k_sep_block_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_sep_block_f32x2, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_sep_block<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_sep_block<F32x2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 // X^T_out = U^T D_{t0} E D_{t0+1} E ... D_{t0+nb-1} E for B items, E applied
@@ -250,21 +303,23 @@ void sep_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, 
     a.ex = ring;
     a.ey = ring + c->p.Lx;
     a.emu = exp(c->p.dtau * c->p.mu);
-    const size_t sh = sep_smem_bytes(c->N, c->p.Lx, c->p.Ly);
+    a.R = sep_rows_per_cta(c->N, a.Lx, a.Ly);
+    a.P = odd_stride(a.Lx);
+    const size_t sh = sep_smem_bytes(a.Lx, a.Ly, a.R);
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool f64 = c->p.prec == SLDQMC_FP64;
-    if (f64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_block_f64, SEP_THREADS, sh);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_block_f32x2, SEP_THREADS, sh);
+    if (f64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_block<F64>, SEP_THREADS, sh);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_block<F32x2>, SEP_THREADS, sh);
     if (per_sm < 1) per_sm = 1;
-    const long long rows = (long long)B * c->N;
+    const long long groups = ((long long)B * c->N + a.R - 1) / a.R;
     const long long cap = (long long)sms * per_sm;
-    const int grid = (int)(rows < cap ? rows : cap);
+    const int grid = (int)(groups < cap ? groups : cap);
     const double flops = 2.0 * (double)c->N * c->N * (c->p.Lx + c->p.Ly) * nb * B;
-    prof_begin(c, SLDQMC_KC_SEP, flops);
-    if (f64) k_sep_block_f64<<<grid, SEP_THREADS, sh, c->st>>>(a);
-    else k_sep_block_f32x2<<<grid, SEP_THREADS, sh, c->st>>>(a);
+    prof_begin(c, SLDQMC_KC_SEP, flops, "sep_block");
+    if (f64) k_sep_block<F64><<<grid, SEP_THREADS, sh, c->st>>>(a);
+    else k_sep_block<F32x2><<<grid, SEP_THREADS, sh, c->st>>>(a);
     prof_end(c);
     c->launches++;
 }

@@ -5,6 +5,7 @@
 // launches and copies inputs and results.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -25,6 +26,8 @@ void launch_log_bare(sldqmc_ctx *c, const int8_t *d_s, int B, double *out, int a
 void launch_local_flips(sldqmc_ctx *c, double *Gp, double *Gm, int8_t *d_s, int B, int tau,
                         uint32_t sweep, uint64_t seed, long long *stats);
 void launch_drift(sldqmc_ctx *c, const double *Gw, const double *Gf, int B2x, int B, long long *stats);
+void launch_local_flips_delayed(sldqmc_ctx *c, double *Gp, double *Gm, double *U, double *V, int8_t *d_s, int B,
+                                int tau, int i0, int ns, uint32_t sweep, uint64_t seed, long long *stats);
 void launch_eff_sweeps(sldqmc_ctx *c, int8_t *d_s, int B, int n_sweeps, uint64_t seed, uint32_t step,
                        int dir, long long *n_accept, long long *n_margin);
 void launch_features(sldqmc_ctx *c, const int8_t *d_s, int B, long long *out);
@@ -48,7 +51,7 @@ using namespace sldqmc;
 
 namespace sldqmc {
 
-void prof_begin(sldqmc_ctx *c, int cls, double flops)
+void prof_begin(sldqmc_ctx *c, int cls, double flops, const char *site)
 {
     Prof *p = c->prof;
     if (!p || !p->on) return;
@@ -60,7 +63,7 @@ void prof_begin(sldqmc_ctx *c, int cls, double flops)
     cudaEvent_t a = p->pool[p->used], b = p->pool[p->used + 1];
     p->used += 2;
     cudaEventRecord(a, c->st);
-    p->recs.push_back(ProfRec{a, b, cls, flops});
+    p->recs.push_back(ProfRec{a, b, cls, flops, site});
     p->open_cls = cls;
 }
 
@@ -75,7 +78,7 @@ void prof_end(sldqmc_ctx *c)
 void gemm_ctx(sldqmc_ctx *c, const GemmF64 &g, bool TA, bool TB)
 {
     const bool timed = c->prof && c->prof->on;
-    if (timed) prof_begin(c, SLDQMC_KC_GEMM_F64, gemm_flops(g));
+    if (timed) prof_begin(c, SLDQMC_KC_GEMM_F64, gemm_flops(g), "gemm_f64");
     gemm_f64(g, TA, TB, c->st);
     if (timed) prof_end(c);
     c->launches++;
@@ -304,10 +307,38 @@ int ensure_local_buffers(sldqmc_ctx *c)
 {
     if (c->d_G[0]) return SLDQMC_OK;
     const size_t n = (size_t)c->cap * c->nn;
-    int rc = dalloc(&c->d_G[0], 6 * n);
+    const size_t uv = 2 * (size_t)c->cap * 32 * c->N;
+    int rc = dalloc(&c->d_G[0], 6 * n + 2 * uv);
     if (rc) return rc;
     c->d_G[1] = c->d_G[0] + n;
+    c->d_U = c->d_G[0] + 6 * n;
+    c->d_V = c->d_U + uv;
     return SLDQMC_OK;
+}
+
+// The flips of slice tau: one launch of immediate rank-1 updates, or blocks
+// of local_rank sites whose pending corrections G -= U V are applied by one
+// batched GEMM per flavour after each block.
+static void local_flips_slice(sldqmc_ctx *c, double *Gp, double *Gm, int8_t *d_s, int B, int tau, uint32_t sweep,
+                              uint64_t seed)
+{
+    const int N = c->N;
+    if (c->local_rank <= 1) {
+        launch_local_flips(c, Gp, Gm, d_s, B, tau, sweep, seed, c->d_stats);
+        return;
+    }
+    double *G[2] = {Gp, Gm};
+    for (int i0 = 0; i0 < N; i0 += c->local_rank) {
+        const int ns = std::min(c->local_rank, N - i0);
+        launch_local_flips_delayed(c, Gp, Gm, c->d_U, c->d_V, d_s, B, tau, i0, ns, sweep, seed, c->d_stats);
+        for (int f = 0; f < 2; ++f) {
+            const long long so = (long long)f * c->cap * 32 * N;
+            GemmF64 g = gemm_desc(N, N, 32, c->d_U + so, 32, 32LL * N, c->d_V + so, N, 32LL * N, G[f], N, c->nn, B);
+            g.alpha = -1.0;
+            g.beta = 1.0;
+            gemm_ctx(c, g, false, false);
+        }
+    }
 }
 
 // Greedy colouring of the effective model's interaction graph: sites
@@ -541,6 +572,7 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     c->dtauJ = p->dtau * p->J_ising;
     c->Ktau = -0.5 * log(tanh(p->dtau * p->h));
     c->prof = new Prof();
+    c->local_rank = 1;
     int rc = SLDQMC_OK;
     const size_t nn = (size_t)c->nn, cap = (size_t)c->cap;
     if ((rc = dalloc(&c->d_flag, 1))) goto fail;
@@ -562,10 +594,11 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     c->d_Dp = c->d_D + N * cap;
     c->d_logacc = c->d_Dp + N * cap;
     c->d_ld_tmp = nullptr;
-    if ((rc = dalloc(&c->d_perm, 2 * N * cap + 2 * cap + 2 * cap))) goto fail;
+    if ((rc = dalloc(&c->d_perm, 2 * N * cap + 2 * cap + 2 * cap + 24 * 32 * cap))) goto fail;
     c->d_piv = c->d_perm + N * cap;
     c->d_sgn = c->d_piv + N * cap;
     c->d_sg_tmp = c->d_sgn + 2 * cap;
+    c->d_tslu = c->d_sg_tmp + 2 * cap;
     if ((rc = dalloc(&c->d_s_tmp, 2 * (size_t)M * N * cap))) goto fail;
     c->d_s_one = c->d_s_tmp + (size_t)M * N * cap;
     if ((rc = dalloc(&c->d_ld_tmp, 4 * cap))) goto fail;
@@ -810,7 +843,7 @@ int sldqmc_local_sweep_batch_dev(sldqmc_ctx *c, int8_t *d_s, int B, uint64_t see
                 std::swap(Gp, Wp);
                 std::swap(Gm, Wm);
             }
-            launch_local_flips(c, Gp, Gm, d_s, B, tau, sweep_id, seed, c->d_stats);
+            local_flips_slice(c, Gp, Gm, d_s, B, tau, sweep_id, seed);
         }
     }
     if (stats) {
@@ -1247,6 +1280,13 @@ int sldqmc_wait_selftest(sldqmc_ctx *c, int max_polls)
     return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
 }
 
+int sldqmc_set_local_update_rank(sldqmc_ctx *c, int k)
+{
+    if (!c || k < 1 || k > 32) return SLDQMC_ERR_ARG;
+    c->local_rank = k;
+    return SLDQMC_OK;
+}
+
 int sldqmc_set_kinetic_form(sldqmc_ctx *c, int form)
 {
     if (!c || (form != SLDQMC_KINETIC_DENSE && form != SLDQMC_KINETIC_SEPARABLE)) return SLDQMC_ERR_ARG;
@@ -1260,6 +1300,36 @@ int sldqmc_profile_enable(sldqmc_ctx *c, int on)
 {
     if (!c || !c->prof) return SLDQMC_ERR_ARG;
     c->prof->on = on != 0;
+    return SLDQMC_OK;
+}
+
+int sldqmc_profile_read_sites(sldqmc_ctx *c, char *buf, int len)
+{
+    if (!c || !c->prof || !buf || len < 1) return SLDQMC_ERR_ARG;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return SLDQMC_ERR_CUDA;
+    struct Agg { const char *site; int cls; long long n; double ms, flops; };
+    std::vector<Agg> agg;
+    for (const ProfRec &r : c->prof->recs) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return SLDQMC_ERR_CUDA;
+        const char *site = r.site ? r.site : "unnamed";
+        size_t k = 0;
+        while (k < agg.size() && (strcmp(agg[k].site, site) != 0 || agg[k].cls != r.cls)) ++k;
+        if (k == agg.size()) agg.push_back(Agg{site, r.cls, 0, 0.0, 0.0});
+        agg[k].n += 1;
+        agg[k].ms += t;
+        agg[k].flops += r.flops;
+    }
+    c->prof->recs.clear();
+    c->prof->used = 0;
+    int off = 0;
+    buf[0] = 0;
+    for (const Agg &a : agg) {
+        const int w = snprintf(buf + off, (size_t)(len - off), "%s %d %lld %.6f %.6e\n", a.site, a.cls, a.n, a.ms,
+                               a.flops);
+        if (w < 0 || w >= len - off) break;
+        off += w;
+    }
     return SLDQMC_OK;
 }
 

@@ -435,118 +435,250 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_panel_smem(double *A, long lo
     lu_panel_close(piv + (long long)b * N + k0, R, kb, org, pvv, pr, logacc, lusgn, b, N, k0);
 }
 
-// The same panel factorisation on global memory, for panels of more than
-// LU_SMEM_MAX_ROWS rows: same pivot choice and arithmetic, the swaps inside
-// the panel's columns only.  Thread 0 composes the interchanges on the list
-// of changed rows (at most 2 kb) afterwards.
-__global__ void __launch_bounds__(1024) k_lu_panel(double *A, long long sA, int lda, int N, int k0, int kb,
-                                                   int *piv, double *logacc, int *lusgn, int *flag)
+// ---------------------------------------------------------------------------
+// Panels taller than LU_SMEM_MAX_ROWS: tournament pivoting.  The panel's rows
+// are cut into up to TSLU_BLOCKS balanced row blocks; each block (one CTA)
+// runs partial pivoting on its own rows in shared memory and nominates the
+// kb rows it pivoted on; one CTA then runs partial pivoting on the
+// nominated rows (at most TSLU_BLOCKS * 32 of them), whose pivot rows, in
+// order, become the panel's block row: their factors are the panel's L11
+// and U11.  The block row's former rows move into the rows the pivots left,
+// giving the same interchange record as one partial-pivoting pass (the
+// source of each new row j < kb, then the changed rows below), and every
+// other row gets its multipliers from L21 = A21 U11^{-1}.  Any pivot choice
+// with bounded growth gives the same determinant and solve; this one keeps
+// a panel's serial pivot chain inside shared memory and spreads the row
+// work over many CTAs, where a single CTA would stream a tall panel from
+// global memory 32 times.
+constexpr int TSLU_BLOCKS = 24;   // nominated rows 24 * 32 <= LU_SMEM_MAX_ROWS
+constexpr int TSLU_MIN_ROWS = 256;
+
+// Partial pivoting on R rows of kb columns in shared memory (row stride 33),
+// org[] permuted with the rows: afterwards rows 0..min(kb, R)-1 hold the
+// pivot rows in order with their L multipliers and U entries.
+__device__ void lu_gepp_rows(double *P, int *org, int R, int kb, double *pvv, int *pr, int *flag,
+                             unsigned long long *wk, int *wi, double *s_vinv)
 {
-    const int b = blockIdx.x;
-    double *Ab = A + (long long)b * sA + (long long)k0 * lda + k0;  // panel origin
-    const int R = N - k0;
-    __shared__ unsigned long long wk[32];
-    __shared__ int wi[32];
-    __shared__ double pvv[32];
-    __shared__ int pr[32];
-    __shared__ double s_vinv;
-    __shared__ int lpos[64], lorg[64], s_n;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    for (int j = 0; j < kb; ++j) {
-        unsigned long long bk = 0;
-        int bi = R;
-        for (int i = j + tid; i < R; i += blockDim.x) {
-            const unsigned long long k = lu_key(Ab[(long long)i * lda + j]);
-            if (lu_key_better(k, i, bk, bi)) { bk = k; bi = i; }
-        }
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int steps = kb < R ? kb : R;
+    unsigned long long bk = 0;
+    int bi = R;
+    for (int r = tid; r < R; r += LU_THREADS) {
+        const unsigned long long k = lu_key(P[r * 33]);
+        if (lu_key_better(k, r, bk, bi)) { bk = k; bi = r; }
+    }
+    for (int j = 0; j < steps; ++j) {
         lu_warp_argmax(bk, bi);
         if (lane == 0) { wk[wid] = bk; wi[wid] = bi; }
         __syncthreads();
         if (wid == 0) {
-            unsigned long long k = lane < nw ? wk[lane] : 0ull;
-            int i = lane < nw ? wi[lane] : R;
+            unsigned long long k = lane < LU_THREADS / 32 ? wk[lane] : 0ull;
+            int i = lane < LU_THREADS / 32 ? wi[lane] : R;
             lu_warp_argmax(k, i);
-            i = __shfl_sync(0xffffffffu, i, 0);
-            const int p = i < R ? i : j;
-            if (p != j && lane < kb) {
-                const double t = Ab[(long long)j * lda + lane];
-                Ab[(long long)j * lda + lane] = Ab[(long long)p * lda + lane];
-                Ab[(long long)p * lda + lane] = t;
+            const int p = __shfl_sync(0xffffffffu, i, 0) < R ? __shfl_sync(0xffffffffu, i, 0) : j;
+            if (p != j) {
+                const double t = P[j * 33 + lane];
+                P[j * 33 + lane] = P[p * 33 + lane];
+                P[p * 33 + lane] = t;
+                if (lane == 0) {
+                    const int o = org[j];
+                    org[j] = org[p];
+                    org[p] = o;
+                }
             }
             __syncwarp();
             if (lane == 0) {
-                double v = Ab[(long long)j * lda + j];
+                double v = P[j * 33 + j];
                 if (v == 0.0 || !isfinite(v)) {
                     atomicOr(flag, FLAG_NUMERICAL);
                     v = 1.0;
-                    Ab[(long long)j * lda + j] = 1.0;
+                    P[j * 33 + j] = 1.0;
                 }
                 pvv[j] = v;
                 pr[j] = p;
-                s_vinv = 1.0 / v;
+                *s_vinv = 1.0 / v;
             }
         }
         __syncthreads();
-        const double vinv = s_vinv;
-        for (int i = j + 1 + tid; i < R; i += blockDim.x) {
-            double *row = Ab + (long long)i * lda;
+        const double vinv = *s_vinv;
+        bk = 0;
+        bi = R;
+        for (int r = j + 1 + tid; r < R; r += LU_THREADS) {
+            double *row = P + r * 33;
             const double m = row[j] * vinv;
             row[j] = m;
-            for (int l = j + 1; l < kb; ++l) row[l] -= m * Ab[(long long)j * lda + l];
-        }
-        __syncthreads();
-    }
-    // compose the swaps on the changed rows: lpos[t] now holds original row lorg[t]
-    if (tid == 0) {
-        int n = 0;
-        for (int j = 0; j < kb; ++j) {
-            const int p = pr[j];
-            if (p == j) continue;
-            int a = -1, c = -1;
-            for (int t = 0; t < n; ++t) {
-                if (lpos[t] == j) a = t;
-                if (lpos[t] == p) c = t;
+#pragma unroll 4
+            for (int l = j + 1; l < kb; ++l) row[l] -= m * P[j * 33 + l];
+            if (j + 1 < kb) {
+                const unsigned long long k = lu_key(row[j + 1]);
+                if (lu_key_better(k, r, bk, bi)) { bk = k; bi = r; }
             }
-            if (a < 0) { a = n++; lpos[a] = j; lorg[a] = j; }
-            if (c < 0) { c = n++; lpos[c] = p; lorg[c] = p; }
-            const int o = lorg[a];
-            lorg[a] = lorg[c];
-            lorg[c] = o;
         }
-        s_n = n;
     }
     __syncthreads();
-    if (wid == 0) {
-        int *out = piv + (long long)b * N + k0;
-        if (lane < kb) {
-            int s = lane;
-            for (int t = 0; t < s_n; ++t)
-                if (lpos[t] == lane) s = lorg[t];
-            out[lane] = s;
-        }
-        // changed rows >= kb in ascending order (selection over the short list)
-        if (lane == 0) {
-            int e = 0, last = kb - 1;
-            for (;;) {
-                int nxt = R, o = 0;
-                for (int t = 0; t < s_n; ++t)
-                    if (lpos[t] > last && lpos[t] < nxt && lorg[t] != lpos[t]) { nxt = lpos[t]; o = lorg[t]; }
-                if (nxt == R) break;
-                out[kb + e++] = nxt * 64 + o;
-                last = nxt;
-            }
-            if (k0 + kb + e < N) out[kb + e] = -1;
-            double acc = logacc[b];
-            int sg = 1;
-            for (int j = 0; j < kb; ++j) {
-                acc += log(fabs(pvv[j]));
-                if (pr[j] != j) sg = -sg;
-                if (pvv[j] < 0.0) sg = -sg;
-            }
-            logacc[b] = acc;
-            lusgn[b] *= sg;
-        }
+}
+
+// Round 1: row block g of the panel of item b nominates its pivot rows
+// (panel-relative row numbers) into cand[(b * nblk + g) * 32 + j].
+__global__ void __launch_bounds__(LU_THREADS) k_lu_tslu_local(const double *A, long long sA, int lda, int N, int k0,
+                                                              int kb, int nblk, int *cand, int *flag)
+{
+    extern __shared__ double P[];
+    __shared__ unsigned long long wk[LU_THREADS / 32];
+    __shared__ int wi[LU_THREADS / 32];
+    __shared__ double pvv[32], s_vinv;
+    __shared__ int pr[32];
+    const int b = blockIdx.y, g = blockIdx.x;
+    const int R = N - k0;
+    const int r0 = (int)((long long)g * R / nblk), r1 = (int)((long long)(g + 1) * R / nblk), nr = r1 - r0;
+    int *org = reinterpret_cast<int *>(P + (size_t)nr * 33);
+    const double *Ab = A + (long long)b * sA + (long long)(k0 + r0) * lda + k0;
+    for (int e = threadIdx.x; e < nr * 32; e += LU_THREADS) {
+        const int r = e >> 5, l = e & 31;
+        P[r * 33 + l] = l < kb ? Ab[(long long)r * lda + l] : 0.0;
     }
+    for (int r = threadIdx.x; r < nr; r += LU_THREADS) org[r] = r0 + r;
+    __syncthreads();
+    lu_gepp_rows(P, org, nr, kb, pvv, pr, flag, wk, wi, &s_vinv);
+    if (threadIdx.x < kb) cand[((long long)b * nblk + g) * 32 + threadIdx.x] = threadIdx.x < nr ? org[threadIdx.x] : -1;
+}
+
+// Round 2: partial pivoting on the nominated rows; the pivot rows become
+// the block row (factored), the block row's former rows move into the rows
+// the pivots left (original values), and the interchange record, the log
+// of the pivots and the sign are written as by the one-pass panel kernels.
+__global__ void __launch_bounds__(LU_THREADS) k_lu_tslu_final(double *A, long long sA, int lda, int N, int k0,
+                                                              int kb, int nblk, const int *cand, int *piv,
+                                                              double *logacc, int *lusgn, int *flag)
+{
+    extern __shared__ double P[];
+    __shared__ double top[32 * 33];
+    __shared__ unsigned long long wk[LU_THREADS / 32];
+    __shared__ int wi[LU_THREADS / 32];
+    __shared__ double pvv[32], s_vinv;
+    __shared__ int pr[32], dst_q[32], src_t[32], s_nq;
+    const int b = blockIdx.x;
+    double *Ab = A + (long long)b * sA + (long long)k0 * lda + k0;
+    const int *cb = cand + (long long)b * nblk * 32;
+    // nominated rows, in block order (blocks with fewer than kb rows leave -1)
+    int nc = 0;
+    for (int g = 0; g < nblk; ++g)
+        for (int j = 0; j < kb; ++j) nc += cb[g * 32 + j] >= 0;
+    int *org = reinterpret_cast<int *>(P + (size_t)nc * 33);
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int g = 0; g < nblk; ++g)
+            for (int j = 0; j < kb; ++j)
+                if (cb[g * 32 + j] >= 0) org[c++] = cb[g * 32 + j];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * 32; e += LU_THREADS) {
+        const int r = e >> 5, l = e & 31;
+        P[r * 33 + l] = l < kb ? Ab[(long long)org[r] * lda + l] : 0.0;
+    }
+    for (int e = threadIdx.x; e < kb * 32; e += LU_THREADS) {
+        const int r = e >> 5, l = e & 31;
+        top[r * 33 + l] = l < kb ? Ab[(long long)r * lda + l] : 0.0;
+    }
+    __syncthreads();
+    lu_gepp_rows(P, org, nc, kb, pvv, pr, flag, wk, wi, &s_vinv);
+    if (threadIdx.x == 0) {
+        // pivots p_j = org[j]; block-row rows not chosen move, in ascending
+        // order, into the chosen rows below the block row, in ascending order
+        unsigned chosen_top = 0u;
+        int nq = 0;
+        for (int j = 0; j < kb; ++j) {
+            const int p = org[j];
+            if (p < kb) chosen_top |= 1u << p;
+            else dst_q[nq++] = p;
+        }
+        for (int x = 1; x < nq; ++x)  // insertion sort of at most 32 rows
+            for (int y = x; y > 0 && dst_q[y - 1] > dst_q[y]; --y) {
+                const int t = dst_q[y];
+                dst_q[y] = dst_q[y - 1];
+                dst_q[y - 1] = t;
+            }
+        int nd = 0;
+        for (int t = 0; t < kb; ++t)
+            if (!(chosen_top & (1u << t))) src_t[nd++] = t;
+        s_nq = nq;
+        int *out = piv + (long long)b * N + k0;
+        for (int j = 0; j < kb; ++j) out[j] = org[j];
+        for (int m = 0; m < nq; ++m) out[kb + m] = dst_q[m] * 64 + src_t[m];
+        if (k0 + kb + nq < N) out[kb + nq] = -1;
+        // parity of the permutation: position j < kb receives row p_j, position
+        // dst_q[m] receives row src_t[m]; count the cycles over the moved positions
+        int pos[64], img[64], n = 0;
+        for (int j = 0; j < kb; ++j) { pos[n] = j; img[n] = org[j]; ++n; }
+        for (int m = 0; m < nq; ++m) { pos[n] = dst_q[m]; img[n] = src_t[m]; ++n; }
+        unsigned long long seen = 0ull;
+        int cycles = 0;
+        for (int s0 = 0; s0 < n; ++s0) {
+            if (seen & (1ull << s0)) continue;
+            ++cycles;
+            int cur = s0;
+            while (!(seen & (1ull << cur))) {
+                seen |= 1ull << cur;
+                int nxt = -1;
+                for (int u = 0; u < n; ++u)
+                    if (pos[u] == img[cur]) { nxt = u; break; }
+                if (nxt < 0) break;
+                cur = nxt;
+            }
+        }
+        double acc = logacc[b];
+        int sg = ((n - cycles) & 1) ? -1 : 1;
+        for (int j = 0; j < kb; ++j) {
+            acc += log(fabs(pvv[j]));
+            if (pvv[j] < 0.0) sg = -sg;
+        }
+        logacc[b] = acc;
+        lusgn[b] *= sg;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kb * 32; e += LU_THREADS) {
+        const int r = e >> 5, l = e & 31;
+        if (l < kb) Ab[(long long)r * lda + l] = P[r * 33 + l];
+    }
+    const int nq = s_nq;
+    for (int e = threadIdx.x; e < nq * 32; e += LU_THREADS) {
+        const int m = e >> 5, l = e & 31;
+        if (l < kb) Ab[(long long)dst_q[m] * lda + l] = top[src_t[m] * 33 + l];
+    }
+}
+
+// Round 3: multipliers of the rows below the block row, L21 = A21 U11^{-1},
+// one thread per row.
+__global__ void __launch_bounds__(128) k_lu_tslu_l21(double *A, long long sA, int lda, int N, int k0, int kb)
+{
+    __shared__ double U[32][33];
+    __shared__ double uinv[32];
+    const int b = blockIdx.y;
+    double *Ab = A + (long long)b * sA + (long long)k0 * lda + k0;
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int r = e >> 5, c = e & 31;
+        U[r][c] = (r < kb && c < kb && c >= r) ? Ab[(long long)r * lda + c] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) uinv[threadIdx.x] = threadIdx.x < kb ? 1.0 / U[threadIdx.x][threadIdx.x] : 0.0;
+    __syncthreads();
+    const int R = N - k0;
+    const int i = kb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
+    double *row = Ab + (long long)i * lda;
+    double x[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) x[l] = l < kb ? row[l] : 0.0;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+        double acc = x[l];
+#pragma unroll
+        for (int m = 0; m < l; ++m) acc -= x[m] * U[m][l];
+        x[l] = acc * uinv[l];
+    }
+#pragma unroll
+    for (int l = 0; l < 32; ++l)
+        if (l < kb) row[l] = x[l];
 }
 
 // U12 = L11^{-1} A12 for the block row k0..k0+kb (L11 unit lower), with the
@@ -700,8 +832,10 @@ void stab_set_limits(int Npad)
         if (dev >= 0) sort_max[dev] = sh;
     }
     if (dev < 0 || !lu_set[dev]) {
-        cudaFuncSetAttribute(k_lu_panel_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((sizeof(double) * 33 + sizeof(int)) * LU_SMEM_MAX_ROWS));
+        const int lu_sh = (int)((sizeof(double) * 33 + sizeof(int)) * LU_SMEM_MAX_ROWS);
+        cudaFuncSetAttribute(k_lu_panel_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, lu_sh);
+        cudaFuncSetAttribute(k_lu_tslu_local, cudaFuncAttributeMaxDynamicSharedMemorySize, lu_sh);
+        cudaFuncSetAttribute(k_lu_tslu_final, cudaFuncAttributeMaxDynamicSharedMemorySize, lu_sh);
         if (dev >= 0) lu_set[dev] = true;
     }
 }
@@ -709,7 +843,9 @@ void stab_set_limits(int Npad)
 void launch_init_udv(sldqmc_ctx *c, double *Ut, double *V, int B)
 {
     dim3 grid(cdiv(c->nn, 256) < 64 ? cdiv(c->nn, 256) : 64, B);
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_init_udv");
     k_init_udv<<<grid, 256, 0, c->st>>>(Ut, V, c->nn, c->N, c->d_D, c->d_sgn, c->d_logacc, c->cap);
+    prof_end(c);
     c->launches++;
 }
 
@@ -738,7 +874,7 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
         } else {
             dim3 grid(cdiv(nW + N, CHOL_THREADS * CHOL_CPT), B);
             // algorithmic flops: factor of the kb x kb block, triangular solves of nW + N columns
-            prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * ((double)kb * kb * kb / 3.0 + (double)(nW + N) * kb * kb));
+            prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * ((double)kb * kb * kb / 3.0 + (double)(nW + N) * kb * kb), "chol_panel_f64");
             k_chol_panel<32, CHOL_CPT><<<grid, CHOL_THREADS, 0, c->st>>>(W, sW, N, Y, nn, R, nn, N, k0, kb, c->d_flag);
             prof_end(c);
             c->launches++;
@@ -781,11 +917,13 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B, int pass
     int Npad = 1;
     while (Npad < N) Npad <<= 1;
     size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
-    prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0);
+    prof_begin(c, SLDQMC_KC_PANEL_F64, 0.0, "sort_pivot");
     k_sort_pivot<<<B, 1024, sh, c->st>>>(W, 2 * nn, N, c->d_D, N, Npad, c->d_perm, c->d_Dp, c->d_sgn);
     prof_end(c);
     dim3 gg(cdiv(N, 256), N, B);
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_gather_pivot");
     k_gather_pivot<<<gg, 256, 0, c->st>>>(W, 2 * nn, Xt, Wc, Y, nn, N, N, c->d_perm);
+    prof_end(c);
     c->launches += 2;
     chol_pass(c, Wc, nn, Y, R1, B);
     const double *R = R1;
@@ -811,14 +949,18 @@ void stabilize(sldqmc_ctx *c, double *Xt, double *Wc, double *Y, int B, int pass
         R = Xt;
     }
     dim3 gd(cdiv(N, 256), B);
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_new_D");
     k_new_D<<<gd, 256, 0, c->st>>>(R, nn, N, c->d_Dp, c->d_D, c->d_flag);
+    prof_end(c);
     c->launches++;
     if (c->oz_ws) {
         // mixed-precision modes: V = (D^{-1} R D_p) P^T V, FP64-accurate on the tensor cores
         oz_update_V(c, R, V, Vg, B);
         return;
     }
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_gather_V");
     k_gather_V<<<gg, 256, 0, c->st>>>(V, Vg, nn, N, c->d_perm, c->d_Dp);
+    prof_end(c);
     // V = D^{-1} R Vg
     GemmF64 g4 = gemm_desc(N, N, N, R, N, nn, Vg, N, nn, V, N, nn, B);
     g4.a_upper = 1;
@@ -838,26 +980,39 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
     const int ncols = lda;
     double *A = c->buf[4];  // 2*nn per item
     dim3 gm(cdiv(N, 256), N, B);
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_mmid");
     k_mmid<<<gm, 256, 0, c->st>>>(Ut, c->buf[1], c->d_D, A, nn, N, lda, rhs);
+    prof_end(c);
     c->launches++;
     // note: k_mmid writes item b at offset b*N*lda; with lda = N the items
     // are packed at stride nn, with lda = 2N at stride 2nn.
     const long long sItem = (long long)N * lda;
     for (int k0 = 0; k0 < N; k0 += 32) {
         int kb = N - k0 < 32 ? N - k0 : 32;
-        prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * (N - k0) * kb * kb);
-        if (N - k0 <= LU_SMEM_MAX_ROWS)
+        prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * (N - k0) * kb * kb, N - k0 <= LU_SMEM_MAX_ROWS ? "lu_panel_smem" : "lu_panel_tournament");
+        if (N - k0 <= LU_SMEM_MAX_ROWS) {
             k_lu_panel_smem<<<B, LU_THREADS, (sizeof(double) * 33 + sizeof(int)) * (N - k0), c->st>>>(
                 A, sItem, lda, N, k0, kb, c->d_piv, c->d_logacc, c->d_sgn + c->cap, c->d_flag);
-        else
-            k_lu_panel<<<B, 1024, 0, c->st>>>(A, sItem, lda, N, k0, kb, c->d_piv, c->d_logacc,
-                                              c->d_sgn + c->cap, c->d_flag);
+            c->launches++;
+        } else {
+            // tournament pivoting: nominations by row blocks, the final choice, the multipliers
+            const int R = N - k0;
+            int nblk = R / TSLU_MIN_ROWS;
+            if (nblk > TSLU_BLOCKS) nblk = TSLU_BLOCKS;
+            const int rmax = (R + nblk - 1) / nblk;
+            int *cand = c->d_tslu;  // TSLU_BLOCKS * 32 nominations per item
+            k_lu_tslu_local<<<dim3(nblk, B), LU_THREADS, (sizeof(double) * 33 + sizeof(int)) * rmax, c->st>>>(
+                A, sItem, lda, N, k0, kb, nblk, cand, c->d_flag);
+            k_lu_tslu_final<<<B, LU_THREADS, (sizeof(double) * 33 + sizeof(int)) * nblk * 32, c->st>>>(
+                A, sItem, lda, N, k0, kb, nblk, cand, c->d_piv, c->d_logacc, c->d_sgn + c->cap, c->d_flag);
+            k_lu_tslu_l21<<<dim3(cdiv(R - kb, 128), B), 128, 0, c->st>>>(A, sItem, lda, N, k0, kb);
+            c->launches += 3;
+        }
         prof_end(c);
-        c->launches++;
         int rest = ncols - (k0 + kb);
         if (rest > 0) {
             dim3 gt(cdiv(rest, 128), B);
-            prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * rest * kb * kb);
+            prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * rest * kb * kb, "lu_trsm_row");
             k_lu_trsm_row<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, N, ncols, k0, kb, c->d_piv);
             prof_end(c);
             c->launches++;
@@ -879,7 +1034,7 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
             int k0 = kbi * 32;
             int kb = N - k0 < 32 ? N - k0 : 32;
             dim3 gt(cdiv(N, 128), B);
-            prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * N * kb * kb);
+            prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * N * kb * kb, "trsm_upper_rhs");
             k_trsm_upper_rhs<32><<<gt, 128, 0, c->st>>>(A, sItem, lda, N, k0, kb);
             prof_end(c);
             c->launches++;
@@ -891,11 +1046,15 @@ void finalize(sldqmc_ctx *c, const double *Ut, int B, double *d_ld, int *d_sign,
             }
         }
         dim3 gc(cdiv(N, 256), N, B);
+        prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_copy_rhs");
         k_copy_rhs<<<gc, 256, 0, c->st>>>(A, sItem, lda, N, d_G);
+        prof_end(c);
         c->launches++;
     }
+    prof_begin(c, SLDQMC_KC_OTHER, 0.0, "k_finalize");
     k_finalize<<<B, 256, 0, c->st>>>(c->d_D, N, c->d_logacc, c->d_sgn, c->cap, d_ld, d_sign, scale,
                                      accumulate);
+    prof_end(c);
     c->launches++;
 }
 

@@ -575,11 +575,13 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
     const long long sS = (long long)M * N;
     const long long s_out = (long long)N * w->ldp;
     {
+        prof_begin(c, SLDQMC_KC_OTHER, 0.0, "tc_split");
         void *o[3] = {w->op[0][0], w->op[0][1], w->op[0][2]};
         const int8_t *sk = d_s + (long long)slices[0] * N;
         if (w->mode == 0) launch_split<0>(c, w, Ut, c->nn, B, sk, sS, cu, cd, o, s_out, 2);
         else if (w->mode == 1) launch_split<1>(c, w, Ut, c->nn, B, sk, sS, cu, cd, o, s_out, 1);
         else launch_split<2>(c, w, Ut, c->nn, B, sk, sS, cu, cd, o, s_out, 3);
+        prof_end(c);
     }
     const int tiles = ((N + BN - 1) / BN) * ((N + BM - 1) / BM) * B;
     const int grid = tiles < w->num_sms ? tiles : w->num_sms;
@@ -604,7 +606,7 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
             a.cd_l = (float)(cd - (double)a.cd_h);
             for (int p = 0; p < 3; ++p) a.out[p] = w->op[dst][p];
         }
-        prof_begin(c, SLDQMC_KC_GEMM_TC, 2.0 * (double)N * N * N * B);
+        prof_begin(c, SLDQMC_KC_GEMM_TC, 2.0 * (double)N * N * N * B, "tc_gemm");
         if (w->mode == 0) launch_gemm<0>(c, w, src, grid, a);
         else if (w->mode == 1) launch_gemm<1>(c, w, src, grid, a);
         else launch_gemm<2>(c, w, src, grid, a);

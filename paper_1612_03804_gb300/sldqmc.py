@@ -97,6 +97,8 @@ def load(path=None):
         "sldqmc_gram_batch_dev": ([vp, vp, i, vp], i),
         "sldqmc_profile_read": ([vp, vp, vp, vp], i),
         "sldqmc_set_kinetic_form": ([vp, i], i),
+        "sldqmc_set_local_update_rank": ([vp, i], i),
+        "sldqmc_profile_read_sites": ([vp, ctypes.c_char_p, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -295,6 +297,10 @@ class Context:
     KERNEL_CLASSES = ("gemm_f64", "gemm_tc", "panel_f64", "eff_sweep", "local_flips", "other", "gemm_oz", "sep")
     KINETIC = {"dense": 0, "separable": 1}
 
+    def set_local_update_rank(self, k):
+        """1: immediate rank-1 local updates; 2..32: delayed updates in blocks of k sites."""
+        _chk(load().sldqmc_set_local_update_rank(self.h, int(k)), "set_local_update_rank")
+
     def set_kinetic_form(self, form):
         """'dense' (default) or 'separable' exp(-dtau K) in the slice products."""
         _chk(load().sldqmc_set_kinetic_form(self.h, self.KINETIC[form] if isinstance(form, str) else int(form)),
@@ -311,6 +317,16 @@ class Context:
         _chk(load().sldqmc_profile_read(self.h, _p(la), _p(ms), _p(fl)), "profile_read")
         return {k: dict(launches=int(la[i]), ms=float(ms[i]), flops=float(fl[i]))
                 for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def profile_read_sites(self):
+        """Per launch site: {site: dict(cls, launches, ms, flops)} (clears the record)."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        _chk(load().sldqmc_profile_read_sites(self.h, buf, len(buf)), "profile_read_sites")
+        out = {}
+        for line in buf.value.decode().splitlines():
+            site, cls, n, ms, fl = line.split()
+            out[site] = dict(cls=self.KERNEL_CLASSES[int(cls)], launches=int(n), ms=float(ms), flops=float(fl))
+        return out
 
     def gram_batch_dev(self, d_X, d_W):
         """W_b = X_b X_b^T (upper triangle) for (B, N, N) float64 device tensors."""

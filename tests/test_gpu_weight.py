@@ -1,6 +1,8 @@
 """GPU parity of the exact fermion weight and Green's function (Eq. 1) against
 the FP64 CPU oracle, through the C ABI.  Bar (FP64 mode): log|det| to 1e-9
 relative, identical sign, G to 1e-9 absolute."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -192,3 +194,33 @@ def test_device_field_validation():
         ctx.weight_batch_dev(s, 1, ld)
         ctx.sync()
         assert abs(float(ld[0]) - O.weight(m, s[0].cpu().numpy(), 1)[0]) < 1e-9 * abs(float(ld[0]))
+
+
+def _tall_case():
+    m = O.Model(36, 36, mu=-0.3, xi=1.0, beta=0.5, dtau=0.1, n_wrap=5)
+    return m, domain_field(7, m.M, 36, 36, corr=3)
+
+
+@functools.lru_cache(maxsize=1)
+def _tall_ref():
+    m, s = _tall_case()
+    return O.weight(m, s, 1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32"])
+def test_lu_tournament_pivoting_tall_panels(prec):
+    """36x36 (N = 1296): the first 16 LU panels are taller than 800 rows and take the
+    tournament-pivoting path (row blocks nominate pivots, one CTA chooses), the rest
+    the shared-memory panel.  Weight (LU without a right-hand side; in split-TF32 with
+    digit-split trailing updates) and, in FP64, G (LU with one) against the oracle."""
+    m, s = _tall_case()
+    bound = LD_RTOL if prec == "fp64" else 1e-6
+    with _ctx(m, 5, max_batch=1, prec=prec) as ctx:
+        ref_p, sp = _tall_ref()
+        ld, sg = ctx.weight(s, 1)
+        assert sg == sp and abs(ld - ref_p) <= bound * abs(ref_p), (ld, ref_p)
+        if prec == "fp64":
+            ref_m, sm, Gref = O.weight(m, s, -1, tau0=3, want_G=True)
+            G, ldg, sgg = ctx.green(s, -1, 3)
+            assert sgg == sm and abs(ldg - ref_m) <= LD_RTOL * abs(ref_m)
+            np.testing.assert_allclose(G, Gref, rtol=0, atol=G_ATOL)
