@@ -475,7 +475,7 @@ def run_large(env):
     import numpy as np
     from paper_1612_03804_gb300.inputs import uniform_field
     torch, sldqmc, args = env.torch, env.sldqmc, env.args
-    wl = LARGE
+    wl = dict(LARGE, L=args.large_L)
     N, M, nw = wl["L"] ** 2, int(round(wl["beta"] / wl["dtau"])), wl["n_wrap"]
     B = 1
     t_setup = time.perf_counter()
@@ -484,6 +484,8 @@ def run_large(env):
     else:
         J, E0, r2, ncfg = train_effective_model(torch, sldqmc, wl, args, 9000 + env.rank)
     ctx = make_ctx(sldqmc, wl, args.prec, B, nw, J, E0)
+    if args.prec != "fp64":
+        ctx.set_tile_n(args.large_tile)
     seed = 987654321 + (env.rank << 20)
     d_s = torch.from_numpy(uniform_field(5100 + env.rank, M, N)[None]).cuda()
     d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
@@ -605,7 +607,8 @@ def run_large(env):
            "data": "synthetic (seeded random fields; effective model fitted on seeded local-DQMC runs)",
            "config": {"workload": workload_name(wl), "global_batch": B * env.world, "seq_len": M,
                       "lattice": f"{wl['L']}x{wl['L']}", "chains_per_gpu": B, "precision": args.prec,
-                      "n_wrap": nw, "parallelism": f"replicas x{env.world}",
+                      "n_wrap": nw, "tile_n": args.large_tile if args.prec != "fp64" else None,
+                      "parallelism": f"replicas x{env.world}",
                       "l2": "working set > L2 (each N x N FP64 matrix is 800 MB; no flush)",
                       "fit": {"lattice": "8x8", "configs": ncfg, "J": [float(x) for x in J], "E0": E0, "r2": r2},
                       "setup_s": round(t_setup, 2)},
@@ -688,15 +691,17 @@ def run_chains16(env):
     t_setup = time.perf_counter() - t_setup
     B = args.batch
     seed = 123456789 + (env.rank << 20)
-    nwrap, tune_log = {}, {}
+    nwrap, tiles, tune_log = {}, {}, {}
     for prec in {args.prec, "fp64"}:
         if args.n_wrap == "auto":
-            from paper_1612_03804_gb300.tune import autotune_nwrap
-            nwrap[prec], res = autotune_nwrap(wl["L"], wl["beta"], wl["dtau"], wl["mu"], prec, t=wl["t"], xi=wl["xi"])
-            tune_log[prec] = [[r[0], round(r[1], 2), r[2]] for r in res]
+            from paper_1612_03804_gb300.tune import autotune_schedule
+            nwrap[prec], tiles[prec], res = autotune_schedule(wl["L"], wl["beta"], wl["dtau"], wl["mu"], prec,
+                                                              t=wl["t"], xi=wl["xi"])
+            tune_log[prec] = [[r[0], r[1], round(r[2], 2), r[3]] for r in res]
         else:
-            nwrap[prec] = int(args.n_wrap)
+            nwrap[prec], tiles[prec] = int(args.n_wrap), 64
     ctx = make_ctx(sldqmc, wl, args.prec, B, nwrap[args.prec], J, E0)
+    ctx.set_tile_n(tiles[args.prec])
     d_s = torch.from_numpy(batch_uniform(5000 + env.rank, B, ctx.M, ctx.N)).cuda()
     d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
     d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
@@ -799,7 +804,9 @@ def run_chains16(env):
                "sample": f"{cores} single-flavour weights of this workload (n_wrap=10), one per host core, {dt:.1f} s"}
     return {"workload": workload_name(dict(wl, n_wrap=nwrap[args.prec])), "value": value, "unit": UNIT,
             "chains": B * env.world, "steps": K, "ms_per_step": 1e3 * Tmax / K, "precision": args.prec,
-            "n_wrap": nwrap, "n_wrap_tuning": tune_log or None, "accept_rate": accept_rate,
+            "n_wrap": nwrap, "tile_n": tiles, "tuning": tune_log or None,
+            "tuning_columns": ["n_wrap", "tile_n", "ms per batch of 16", "max rel log-det deviation"],
+            "accept_rate": accept_rate,
             "fit": {"lattice": "8x8", "configs": ncfg, "J": [float(x) for x in J], "E0": E0, "r2": r2},
             "setup_s": round(t_setup, 2), "fp64": fp64, "separable": sep, "errors_vs_oracle": errors,
             "decorrelated_samples_per_s": samples_per_s, "tau_int": tau, "tau_window": window,
@@ -832,16 +839,17 @@ def fill_fraction(work_uneven, t_uneven, work_full, t_full):
 def run_uneven(env, full_rate=None):
     import numpy as np
     from paper_1612_03804_gb300.inputs import batch_uniform
-    from paper_1612_03804_gb300.tune import autotune_nwrap
+    from paper_1612_03804_gb300.tune import autotune_schedule
     torch, sldqmc, args = env.torch, env.sldqmc, env.args
     dtau, mu = 0.05, -0.5
     members, tuned, work = [], {}, 0.0
     t_setup = time.perf_counter()
     for k, ((L, beta), B) in enumerate(sorted(uneven_buckets().items())):
-        nw, _ = autotune_nwrap(L, beta, dtau, mu, args.prec, batch=2, reps=1)
-        tuned[f"{L}x{L} beta={beta:g}"] = {"chains": B, "n_wrap": nw}
+        nw, tile, _ = autotune_schedule(L, beta, dtau, mu, args.prec, batch=2, reps=1)
+        tuned[f"{L}x{L} beta={beta:g}"] = {"chains": B, "n_wrap": nw, "tile_n": tile}
         wl = dict(CH16, L=L, beta=beta)
         ctx = make_ctx(sldqmc, wl, args.prec, B, nw, bare_couplings(wl))
+        ctx.set_tile_n(tile)
         s = torch.from_numpy(batch_uniform(900 + k + 100 * env.rank, B, ctx.M, ctx.N)).cuda()
         ctx.eff_sweeps_batch_dev(s, 20, 5, 0, -1)
         lw = torch.zeros(B, dtype=torch.float64, device="cuda")
@@ -1183,6 +1191,10 @@ def main():
     ap.add_argument("--bare-sweeps", type=int, default=200)
     ap.add_argument("--eff-thermalize", type=int, default=300)
     ap.add_argument("--large-eff-thermalize", type=int, default=100)
+    ap.add_argument("--large-tile", type=int, default=64, choices=[64, 128],
+                    help="tensor-core tile width of the headline workload's slice products")
+    ap.add_argument("--large-L", type=int, default=LARGE["L"],
+                    help="lattice of the headline workload (profiling captures use a smaller one)")
     ap.add_argument("--tau-steps", type=int, default=1000)
     ap.add_argument("--tau-chains", type=int, default=16)
     ap.add_argument("--critical-steps", type=int, default=300)

@@ -267,6 +267,14 @@ int sldqmc_log_weight_batch_dev(sldqmc_ctx *ctx, const int8_t *d_s, int B, doubl
 #define SLDQMC_KINETIC_SEPARABLE 1
 int sldqmc_set_kinetic_form(sldqmc_ctx *ctx, int form);
 
+/* Output tile of the tensor-core slice products of the mixed modes:
+ * 128 x 64 (bn = 64, default) with the FP32 accumulation spread over eight
+ * tensor-memory accumulators, or 128 x 128 (bn = 128) with four, which reads
+ * half the shared-memory operand bytes per flop and puts each accumulator
+ * under more MMAs (a larger FP32 accumulation error).  The n_wrap autotuner
+ * chooses per lattice and precision.  FP64 mode: only 64 is accepted. */
+int sldqmc_set_tile_n(sldqmc_ctx *ctx, int bn);
+
 /* Number of this library's kernels launched on the context since create. */
 long long sldqmc_kernel_launches(const sldqmc_ctx *ctx);
 

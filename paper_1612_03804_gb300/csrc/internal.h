@@ -146,6 +146,7 @@ struct sldqmc_ctx {
     double *d_G[2];    // Gt for the local sweep: cap items per flavour
     double *d_U, *d_V; // pending pairs of the delayed local update: 2 flavours x cap x 32 N each
     int local_rank;    // sites per delayed-update block (1: immediate rank-1 updates)
+    int tile_n;        // output tile width of the tensor-core slice products (64 or 128)
     double *d_ld_tmp, *d_ld_tmp2;
     int *d_sg_tmp;
     long long *d_stats; // cap * 4 (accepted, proposed, margin, drift bits)

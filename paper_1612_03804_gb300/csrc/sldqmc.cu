@@ -45,6 +45,7 @@ int tc_prepare(sldqmc_ctx *c);
 void tc_release(sldqmc_ctx *c);
 void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, double cu, double cd,
                     const int *slices, int nb, double *Xt_out, double *scratch_a, double *scratch_b);
+int tc_set_tile_n(sldqmc_ctx *c, int bn);
 }  // namespace sldqmc
 
 using namespace sldqmc;
@@ -272,6 +273,8 @@ sldqmc_ctx *get_twin(sldqmc_ctx *c)
     }
     t->no_twin = 1;
     t->kinetic = c->kinetic;
+    if (c->tile_n == 128) tc_set_tile_n(t, 128);
+    t->tile_n = c->tile_n;
     c->twin = t;
     return t;
 }
@@ -573,6 +576,7 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     c->Ktau = -0.5 * log(tanh(p->dtau * p->h));
     c->prof = new Prof();
     c->local_rank = 1;
+    c->tile_n = 64;
     int rc = SLDQMC_OK;
     const size_t nn = (size_t)c->nn, cap = (size_t)c->cap;
     if ((rc = dalloc(&c->d_flag, 1))) goto fail;
@@ -1278,6 +1282,16 @@ int sldqmc_wait_selftest(sldqmc_ctx *c, int max_polls)
     if (!c || max_polls < 1 || max_polls > (1 << 24)) return SLDQMC_ERR_ARG;
     launch_wait_selftest(c, max_polls);
     return cudaGetLastError() == cudaSuccess ? SLDQMC_OK : SLDQMC_ERR_CUDA;
+}
+
+int sldqmc_set_tile_n(sldqmc_ctx *c, int bn)
+{
+    if (!c) return SLDQMC_ERR_ARG;
+    if (c->p.prec == SLDQMC_FP64) return bn == 64 ? SLDQMC_OK : SLDQMC_ERR_UNSUPPORTED;
+    int rc = tc_set_tile_n(c, bn);
+    if (rc == SLDQMC_OK && c->twin) rc = tc_set_tile_n(c->twin, bn);
+    if (rc == SLDQMC_OK) c->tile_n = bn;
+    return rc;
 }
 
 int sldqmc_set_local_update_rank(sldqmc_ctx *c, int k)

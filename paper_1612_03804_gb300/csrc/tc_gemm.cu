@@ -45,10 +45,17 @@ namespace {
 
 using namespace tcx;
 
-constexpr int BM = 128, BN = 64, NACC = 8;
+// Output tiles are BM x BN with BN = 64 (eight accumulators) or BN = 128
+// (four accumulators: half the shared-memory operand reads per flop, one
+// accumulator for every three leading products instead of every seven).
+// Both fill the 512 tensor-memory columns.
+constexpr int BM = 128, BN = 64;
 constexpr int TILE_A = BM * 128;  // one A part of one stage: 128 rows x 128 bytes
-constexpr int TILE_B = BN * 128;  // one B part of one stage: 64 rows x 128 bytes
-constexpr int TMEM_COLS = BN * NACC;
+constexpr int TMEM_COLS = 512;
+template <int BNT> struct TileCfg {
+    static constexpr int NACC = TMEM_COLS / BNT;  // accumulators
+    static constexpr int TILE_B = BNT * 128;      // one B part of one stage: BNT rows x 128 bytes
+};
 
 struct TcArgs {
     int N, ldp, nk, batch;
@@ -87,10 +94,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 64.
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format)
+// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = BNT.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, int BNT)
 {
-    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(BN >> 3) << 17) |
+    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(BNT >> 3) << 17) |
            ((uint32_t)(BM >> 4) << 24);
 }
 
@@ -120,14 +127,22 @@ __device__ __forceinline__ float to_tf32(float x)
 // 8-wide K-step); 1 = BF16 (one kind::f16 MMA per 16-wide K-step); 2 = split
 // BF16 (A and E in 3 BF16 parts each, six kind::f16 MMAs per 16-wide K-step).
 template <int MODE> struct ModeCfg;
-template <> struct ModeCfg<0> { static constexpr int NPA = 2, NPB = 3, STAGES = 3, KELEM = 32; static constexpr uint32_t FMT = 2; };
-template <> struct ModeCfg<1> { static constexpr int NPA = 1, NPB = 1, STAGES = 5, KELEM = 64; static constexpr uint32_t FMT = 1; };
-template <> struct ModeCfg<2> { static constexpr int NPA = 3, NPB = 3, STAGES = 3, KELEM = 64; static constexpr uint32_t FMT = 1; };
+template <> struct ModeCfg<0> { static constexpr int NPA = 2, NPB = 3, KELEM = 32; static constexpr uint32_t FMT = 2; };
+template <> struct ModeCfg<1> { static constexpr int NPA = 1, NPB = 1, KELEM = 64; static constexpr uint32_t FMT = 1; };
+template <> struct ModeCfg<2> { static constexpr int NPA = 3, NPB = 3, KELEM = 64; static constexpr uint32_t FMT = 1; };
 
-template <int MODE>
-__host__ __device__ constexpr int stages() { return ModeCfg<MODE>::STAGES; }
-template <int MODE>
-__host__ __device__ constexpr int stage_bytes() { return ModeCfg<MODE>::NPA * TILE_A + ModeCfg<MODE>::NPB * TILE_B; }
+template <int MODE, int BNT>
+__host__ __device__ constexpr int stage_bytes() { return ModeCfg<MODE>::NPA * TILE_A + ModeCfg<MODE>::NPB * TileCfg<BNT>::TILE_B; }
+// pipeline stages: 64-wide tiles 3 (split modes) or 5 (BF16), measured best;
+// 128-wide tiles as many as fit in 227 KB, at most five
+template <int MODE, int BNT>
+__host__ __device__ constexpr int stages()
+{
+    return BNT == 64 ? (MODE == 1 ? 5 : 3)
+                     : ((227 * 1024 - 1024 - 256) / stage_bytes<MODE, BNT>() < 5
+                            ? (227 * 1024 - 1024 - 256) / stage_bytes<MODE, BNT>()
+                            : 5);
+}
 
 // Persistent kernel: one CTA per SM loops over the 128 x 64 output tiles of
 // the whole batch (tile t = blockIdx.x, blockIdx.x + gridDim.x, ...).
@@ -138,9 +153,7 @@ __host__ __device__ constexpr int stage_bytes() { return ModeCfg<MODE>::NPA * TI
 // accumulators into registers, hand tensor memory back at once, and then
 // scale, re-split and store while the MMAs of the next tile run.
 constexpr int EPI_WARPS = 8;                     // epilogue warps: EPI_WARPS / 4 per TMEM lane quarter
-constexpr int EPI_COLS = BN * 4 / EPI_WARPS;      // accumulator columns drained by one epilogue warp
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
-static_assert(EPI_COLS % 16 == 0, "epilogue warps drain 16-column chunks");
 
 __device__ __forceinline__ __nv_bfloat16 bf16_rn(float x) { return __float2bfloat16_rn(x); }
 
@@ -178,18 +191,23 @@ __device__ __forceinline__ void store_part(void *base, long long o, const float 
     }
 }
 
-template <int MODE>
+template <int MODE, int BNT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
               const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, TcArgs a)
 {
     using C = ModeCfg<MODE>;
-    constexpr int STAGE_BYTES = stage_bytes<MODE>();
-    constexpr int STAGES = C::STAGES;
+    constexpr int BN = BNT;
+    constexpr int NACC = TileCfg<BNT>::NACC;
+    constexpr int TILE_B = TileCfg<BNT>::TILE_B;
+    constexpr int EPI_COLS = BN * 4 / EPI_WARPS;  // accumulator columns drained by one epilogue warp
+    static_assert(EPI_COLS % 16 == 0 && EPI_COLS <= 64, "epilogue warps drain 16-column chunks");
+    constexpr int STAGE_BYTES = stage_bytes<MODE, BNT>();
+    constexpr int STAGES = stages<MODE, BNT>();
     constexpr int KSTEPS = 4;  // 128-byte row / 32 bytes per MMA K-step (8 TF32 or 16 BF16)
-    constexpr uint32_t IDESC = instr_desc(C::FMT);
-    constexpr bool SPLIT = MODE != 1;  // leading products on accumulators 0..6, corrections on 7
+    constexpr uint32_t IDESC = instr_desc(C::FMT, BNT);
+    constexpr bool SPLIT = MODE != 1;  // leading products on accumulators 0..NACC-2, corrections on the last
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -302,13 +320,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
             const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
             const int n0 = tn * BN, m0 = tm * BM;
-            // Column scale signs of this tile as a 64-bit mask, fetched before
-            // the accumulators are ready.
+            // Column scale signs of this warp's columns as a 64-bit mask,
+            // fetched before the accumulators are ready.
             uint64_t up_mask = 0;
             const int8_t *sn = a.s_n ? a.s_n + (long long)b * a.sSn : nullptr;
             if (sn) {
-                const bool u0 = n0 + lane < a.N && sn[n0 + lane] > 0;
-                const bool u1 = n0 + 32 + lane < a.N && sn[n0 + 32 + lane] > 0;
+                const int c0w = n0 + cb;
+                const bool u0 = lane < EPI_COLS && c0w + lane < a.N && sn[c0w + lane] > 0;
+                const bool u1 = 32 + lane < EPI_COLS && c0w + 32 + lane < a.N && sn[c0w + 32 + lane] > 0;
                 up_mask = (uint64_t)__ballot_sync(0xffffffffu, u0) | ((uint64_t)__ballot_sync(0xffffffffu, u1) << 32);
             }
             const bool ok = mbar_wait(tmem_full, ti & 1, a.flag);
@@ -365,7 +384,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const float x = v[c][j];
                     float yh = x, ye = 0.0f;
                     if (sn) {
-                        const bool up = (up_mask >> (c0 + j)) & 1u;
+                        const bool up = (up_mask >> (c * 16 + j)) & 1u;
                         const float dh = up ? a.cu_h : a.cd_h, dl = up ? a.cu_l : a.cd_l;
                         yh = x * dh;
                         ye = fmaf(x, dh, -yh) + x * dl;
@@ -436,7 +455,9 @@ struct TcWs {
     void *op[2][3];          // [ping-pong buffer][part]
     void *Ep[3];             // E in parts
     CUtensorMap mapA[2][3];  // [buffer][part]
-    CUtensorMap mapB[3];     // [part]
+    CUtensorMap mapB[3];     // [part], 64-row boxes
+    CUtensorMap mapB128[3];  // [part], 128-row boxes
+    int bn;                  // output tile width of the slice products: 64 or 128
     void *mem;
     int num_sms;
 };
@@ -456,11 +477,11 @@ bool encode(CUtensorMap *map, void *ptr, bool bf16, int rank, int ldp, int rows,
     return r == CUDA_SUCCESS;
 }
 
-template <int MODE>
+template <int MODE, int BNT>
 constexpr size_t smem_bytes()
 {
     // stages, alignment, barriers
-    return (size_t)stages<MODE>() * stage_bytes<MODE>() + 1024 + 256;
+    return (size_t)stages<MODE, BNT>() * stage_bytes<MODE, BNT>() + 1024 + 256;
 }
 
 int mode_of(const sldqmc_ctx *c) { return c->p.prec == SLDQMC_3XTF32 ? 0 : (c->p.prec == SLDQMC_BF16 ? 1 : 2); }
@@ -478,8 +499,13 @@ template <int MODE>
 void launch_gemm(sldqmc_ctx *c, const TcWs *w, int src, int grid, const TcArgs &a)
 {
     const CUtensorMap *A = w->mapA[src];
-    k_tc_gemm<MODE><<<grid, NTHREADS, smem_bytes<MODE>(), c->st>>>(A[0], A[1], A[2], w->mapB[0], w->mapB[1], w->mapB[2],
-                                                                   a);
+    if (w->bn == 128) {
+        const CUtensorMap *E = w->mapB128;
+        k_tc_gemm<MODE, 128><<<grid, NTHREADS, smem_bytes<MODE, 128>(), c->st>>>(A[0], A[1], A[2], E[0], E[1], E[2], a);
+    } else {
+        const CUtensorMap *E = w->mapB;
+        k_tc_gemm<MODE, 64><<<grid, NTHREADS, smem_bytes<MODE, 64>(), c->st>>>(A[0], A[1], A[2], E[0], E[1], E[2], a);
+    }
 }
 
 }  // namespace
@@ -492,7 +518,7 @@ void launch_wait_selftest(sldqmc_ctx *c, int limit)
 
 int tc_prepare(sldqmc_ctx *c)
 {
-    if (c->N < BM) return SLDQMC_ERR_UNSUPPORTED;  // tensor-core tiles are 128 x 64
+    if (c->N < BM) return SLDQMC_ERR_UNSUPPORTED;  // tensor-core tiles are 128 rows
     TcWs *w = new TcWs();
     c->tc_ws = w;
     {
@@ -535,15 +561,21 @@ int tc_prepare(sldqmc_ctx *c)
         if (p < w->npb) {
             w->Ep[p] = q;
             q += (size_t)w->esz * N * w->ldp;
-            if (!encode(&w->mapB[p], w->Ep[p], bf, 2, w->ldp, N, 1, BN)) return SLDQMC_ERR_CUDA;
+            if (!encode(&w->mapB[p], w->Ep[p], bf, 2, w->ldp, N, 1, 64)) return SLDQMC_ERR_CUDA;
+            if (!encode(&w->mapB128[p], w->Ep[p], bf, 2, w->ldp, N, 1, 128)) return SLDQMC_ERR_CUDA;
         } else {
             w->Ep[p] = nullptr;
             w->mapB[p] = w->mapB[0];
+            w->mapB128[p] = w->mapB128[0];
         }
     }
-    cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<0>());
-    cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1>());
-    cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2>());
+    w->bn = 64;
+    cudaFuncSetAttribute(k_tc_gemm<0, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<0, 64>());
+    cudaFuncSetAttribute(k_tc_gemm<1, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1, 64>());
+    cudaFuncSetAttribute(k_tc_gemm<2, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2, 64>());
+    cudaFuncSetAttribute(k_tc_gemm<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<0, 128>());
+    cudaFuncSetAttribute(k_tc_gemm<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<1, 128>());
+    cudaFuncSetAttribute(k_tc_gemm<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<2, 128>());
     return SLDQMC_OK;
 }
 
@@ -583,7 +615,7 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
         else launch_split<2>(c, w, Ut, c->nn, B, sk, sS, cu, cd, o, s_out, 3);
         prof_end(c);
     }
-    const int tiles = ((N + BN - 1) / BN) * ((N + BM - 1) / BM) * B;
+    const int tiles = ((N + w->bn - 1) / w->bn) * ((N + BM - 1) / BM) * B;
     const int grid = tiles < w->num_sms ? tiles : w->num_sms;
     for (int j = 0; j < nb; ++j) {
         const int src = j & 1, dst = src ^ 1;
@@ -615,4 +647,15 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
     }
 }
 
+}  // namespace sldqmc
+
+namespace sldqmc {
+int tc_set_tile_n(sldqmc_ctx *c, int bn)
+{
+    TcWs *w = (TcWs *)c->tc_ws;
+    if (!w) return SLDQMC_ERR_UNSUPPORTED;
+    if (bn != 64 && bn != 128) return SLDQMC_ERR_ARG;
+    w->bn = bn;
+    return SLDQMC_OK;
+}
 }  // namespace sldqmc

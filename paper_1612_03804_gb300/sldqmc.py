@@ -98,6 +98,7 @@ def load(path=None):
         "sldqmc_profile_read": ([vp, vp, vp, vp], i),
         "sldqmc_set_kinetic_form": ([vp, i], i),
         "sldqmc_set_local_update_rank": ([vp, i], i),
+        "sldqmc_set_tile_n": ([vp, i], i),
         "sldqmc_profile_read_sites": ([vp, ctypes.c_char_p, i], i),
     }
     for name, (args, res) in sig.items():
@@ -296,6 +297,10 @@ class Context:
 
     KERNEL_CLASSES = ("gemm_f64", "gemm_tc", "panel_f64", "eff_sweep", "local_flips", "other", "gemm_oz", "sep")
     KINETIC = {"dense": 0, "separable": 1}
+
+    def set_tile_n(self, bn):
+        """Tensor-core slice-product tile width: 64 (eight accumulators) or 128 (four)."""
+        _chk(load().sldqmc_set_tile_n(self.h, int(bn)), "set_tile_n")
 
     def set_local_update_rank(self, k):
         """1: immediate rank-1 local updates; 2..32: delayed updates in blocks of k sites."""

@@ -13,8 +13,12 @@ and precision mode by measurement:
   bound (FP64 1e-9, split-TF32 1e-6, BF16 1e-2, all relative);
   speed: the fastest accurate candidate wins (CUDA-event time of one batch).
 
-The tile shapes are fixed by the kernels' design (64x64 FP64 tiles,
-128x64 tensor-core tiles); n_wrap is the tuned parameter.
+autotune_schedule() tunes n_wrap together with the output tile of the
+tensor-core slice products (128 x 64 with eight FP32 accumulators, or
+128 x 128 with four: fewer shared-memory operand reads per flop, more
+accumulation error per accumulator), keeping the fastest (n_wrap, tile)
+pair whose log|det| meets the mode's bound.  The FP64 GEMM picks its own
+tile (64 x 64 or 32 x 32) from the number of tiles a launch has.
 """
 import math
 
@@ -31,7 +35,17 @@ def candidates(M, dtau, t=1.0, xi=1.0, limit=LIMIT):
 
 
 def autotune_nwrap(L, beta, dtau, mu, prec, t=1.0, xi=1.0, batch=16, reps=2, seed=4321, tol=None):
-    """Returns (best n_wrap, [(n_wrap, ms per batch, max relative log-det deviation), ...])."""
+    """Returns (best n_wrap, [(n_wrap, ms per batch, max relative log-det deviation), ...])
+    with the default 128 x 64 tensor-core tile."""
+    nw, _, res = autotune_schedule(L, beta, dtau, mu, prec, t=t, xi=xi, batch=batch, reps=reps, seed=seed,
+                                   tol=tol, tiles=(64,))
+    return nw, [(r[0], r[2], r[3]) for r in res]
+
+
+def autotune_schedule(L, beta, dtau, mu, prec, t=1.0, xi=1.0, batch=16, reps=2, seed=4321, tol=None,
+                      tiles=(64, 128)):
+    """Returns (best n_wrap, best tile width, [(n_wrap, tile, ms per batch, max relative
+    log-det deviation), ...]); FP64 mode and lattices below 128 sites tune n_wrap only."""
     import torch
     from . import sldqmc
     from .inputs import batch_uniform
@@ -45,6 +59,8 @@ def autotune_nwrap(L, beta, dtau, mu, prec, t=1.0, xi=1.0, batch=16, reps=2, see
                         max_batch=batch) as c0:
         c0.weight_batch_dev(s, -1, ref)
         c0.sync()
+    if prec == "fp64" or L * L < 128:
+        tiles = (64,)
     results = []
     for nw in cands:
         try:
@@ -53,20 +69,22 @@ def autotune_nwrap(L, beta, dtau, mu, prec, t=1.0, xi=1.0, batch=16, reps=2, see
         except sldqmc.SldqmcError:
             continue
         with ctx:
-            ld = torch.zeros(batch, dtype=torch.float64, device="cuda")
-            ctx.weight_batch_dev(s, -1, ld)
-            ctx.sync()
-            st = torch.cuda.current_stream()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            for _ in range(reps):
+            for tile in tiles:
+                ctx.set_tile_n(tile)
+                ld = torch.zeros(batch, dtype=torch.float64, device="cuda")
                 ctx.weight_batch_dev(s, -1, ld)
-            e1.record(st)
-            ctx.sync()
-            ms = e0.elapsed_time(e1) / reps
-            err = float(((ld - ref).abs() / ref.abs()).max())
-            results.append((nw, ms, err))
-    ok = [r for r in results if math.isfinite(r[2]) and r[2] <= tol]
-    best = min(ok, key=lambda r: r[1])[0] if ok else cands[0]
-    return best, results
+                ctx.sync()
+                st = torch.cuda.current_stream()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(reps):
+                    ctx.weight_batch_dev(s, -1, ld)
+                e1.record(st)
+                ctx.sync()
+                ms = e0.elapsed_time(e1) / reps
+                err = float(((ld - ref).abs() / ref.abs()).max())
+                results.append((nw, tile, ms, err))
+    ok = [r for r in results if math.isfinite(r[3]) and r[3] <= tol]
+    best = min(ok, key=lambda r: r[2]) if ok else (cands[0], 64)
+    return best[0], best[1], results

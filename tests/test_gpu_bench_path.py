@@ -67,17 +67,24 @@ def _check(ld, sg, ref, rtol, what):
     assert rel.max() <= rtol, (what, rel.max(), int(rel.argmax()))
 
 
-@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
-def test_many_tiles_per_cta_nwrap32(prec):
-    """16x16, beta = 2 (M = 40: one 32-slice block and a ragged 8-slice block),
-    B = 128: 1024 tiles per slice product on 152 CTAs, as in the benchmark."""
+@pytest.fixture(scope="module")
+def many_tiles_case():
     m = O.Model(16, 16, mu=-0.5, xi=1.0, beta=2.0, dtau=0.05, n_wrap=10)
+    fields = batch_uniform(2401, 128, m.M, m.N)
+    return m, fields, O.weight_many(m, fields, -1)
+
+
+@pytest.mark.parametrize("prec,tile", [("3xtf32", 64), ("bf16x3", 64), ("3xtf32", 128), ("bf16x3", 128)])
+def test_many_tiles_per_cta_nwrap32(prec, tile, many_tiles_case):
+    """16x16, beta = 2 (M = 40: one 32-slice block and a ragged 8-slice block),
+    B = 128: 1024 (tile 64) or 512 (tile 128) output tiles per slice product on 152
+    CTAs, as in the benchmark."""
+    m, fields, ref = many_tiles_case
     B = 128
-    fields = batch_uniform(2401, B, m.M, m.N)
-    ref = O.weight_many(m, fields, -1)
     with _ctx(m, 32, prec, B) as ctx:
+        ctx.set_tile_n(tile)
         ld, sg = _gpu_weights(ctx, fields, -1)
-        _check(ld, sg, ref, SPLIT_LD_RTOL, f"{prec} 16x16 M=40 B=128 n_wrap=32")
+        _check(ld, sg, ref, SPLIT_LD_RTOL, f"{prec} tile {tile} 16x16 M=40 B=128 n_wrap=32")
         # G of the first and the last configuration of the batch (both ends of the tile walk)
         import torch
         d_s = torch.from_numpy(fields).cuda()
@@ -91,18 +98,19 @@ def test_many_tiles_per_cta_nwrap32(prec):
             assert err <= SPLIT_G_ATOL
 
 
-@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
-def test_benchmark_workload_size(prec):
+@pytest.mark.parametrize("prec,tile", [("3xtf32", 64), ("bf16x3", 64), ("3xtf32", 128)])
+def test_benchmark_workload_size(prec, tile):
     """The benchmark's lattice and imaginary time: 16x16, beta = 8, dtau = 0.05
     (M = 160), n_wrap = 32 (five blocks), both flavours, random fields."""
     m = O.Model(16, 16, mu=-0.5, xi=1.0, beta=8.0, dtau=0.05, n_wrap=10)
     B = 8
     fields = batch_uniform(2402, B, m.M, m.N)
     with _ctx(m, 32, prec, B) as ctx:
+        ctx.set_tile_n(tile)
         for eta in (1, -1):
             ref = O.weight_many(m, fields, eta)
             ld, sg = _gpu_weights(ctx, fields, eta)
-            _check(ld, sg, ref, SPLIT_LD_RTOL, f"{prec} 16x16 M=160 n_wrap=32 eta={eta}")
+            _check(ld, sg, ref, SPLIT_LD_RTOL, f"{prec} tile {tile} 16x16 M=160 n_wrap=32 eta={eta}")
 
 
 def test_fp64_products_with_64x64_tiles():

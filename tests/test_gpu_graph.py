@@ -52,3 +52,69 @@ def test_graph_replays_equal_sequential_steps(prec_big):
         np.testing.assert_array_equal(gm[3].cpu().numpy(), rm[3].cpu().numpy())
         np.testing.assert_array_equal(gm[2].cpu().numpy(), rm[2].cpu().numpy())
     g.close()
+
+
+def test_uneven_graph_chains_against_oracle():
+    """A small uneven set stepped by one CUDA graph, against the FP64 CPU oracle step by
+    step: 12x12 at beta = 1 and 16x16 at beta = 2 (dtau = 0.05), split-TF32 products,
+    bare-Ising H_eff, two chains each.  Decisions within the margin that the log-det
+    bound allows (twice 1e-6 of the fermion part of log omega) are margin events, where
+    the oracle takes the graph's outcome; every other decision, configuration and kept
+    weight must agree."""
+    import math
+
+    import torch
+    from oracle import oracle as O
+    from paper_1612_03804_gb300 import sldqmc
+    from paper_1612_03804_gb300.inputs import uniform_field
+    bound = 1e-6
+    specs = [(12, 1.0), (16, 2.0)]
+    B, steps, step0 = 2, 4, 5
+    members, models, states, seeds = [], [], [], []
+    for k, (L, beta) in enumerate(specs):
+        m = O.Model(L, L, mu=-0.5, xi=1.0, beta=beta, dtau=0.05, n_wrap=10, J=1.0, h=2.774)
+        kt = -0.5 * math.log(math.tanh(m.dtau * m.h))
+        J = np.array([-m.dtau * m.J / m.beta, 0.0, 0.0, -kt / m.beta])
+        s0 = np.stack([O.eff_sweeps(m, uniform_field(4100 + 10 * k + b, m.M, m.N), CLASSES, J, 30, seed=7,
+                                    step=b, direction=0)[0] for b in range(B)])
+        ctx = sldqmc.Context(L, L, mu=-0.5, xi=1.0, beta=beta, dtau=0.05, n_wrap=10, prec="3xtf32", max_batch=B)
+        ctx.set_effective_model(CLASSES, J)
+        d_s = torch.from_numpy(s0).cuda()
+        d_lw = torch.zeros(B, dtype=torch.float64, device="cuda")
+        ctx.log_weight_batch_dev(d_s, d_lw)
+        d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+        ctx.sync()
+        seed = 5150 + k
+        members.append((ctx, d_s, d_lw, d_acc, seed))
+        models.append((m, J))
+        states.append(([s0[b].copy() for b in range(B)], [O.log_weight_total(m, s0[b]) for b in range(B)]))
+        seeds.append(seed)
+    g = sldqmc.Graph(members, n_eff=1, step0=step0)
+    compared = margin = 0
+    for t in range(steps):
+        before = [mb[3].cpu().numpy().copy() for mb in members]
+        g.launch(1)
+        g.sync()
+        for k, (ctx, d_s, d_lw, d_acc, seed) in enumerate(members):
+            m, J = models[k]
+            so_l, lw_l = states[k]
+            s_g, lw_g = d_s.cpu().numpy(), d_lw.cpu().numpy()
+            acc_g = d_acc.cpu().numpy() - before[k]
+            for b in range(B):
+                fermion = abs(lw_l[b] - O.log_bare_weight(m, so_l[b]))
+                mg = 4.0 * bound * fermion
+                so, lwo, ao, lro, _, _ = O.cumulative_update(m, so_l[b], lw_l[b], CLASSES, J, 1,
+                                                             seed=seed + (b << 32), step=step0 + t)
+                lu = math.log(O.uniform(seed + (b << 32), 0, 0, step0 + t, 4))
+                if abs(lro - lu) <= mg:
+                    margin += 1
+                    so_l[b], lw_l[b] = s_g[b].copy(), O.log_weight_total(m, s_g[b])
+                    continue
+                compared += 1
+                assert acc_g[b] == ao, (k, b, t, lro, lu)
+                np.testing.assert_array_equal(s_g[b], so)
+                assert abs(lw_g[b] - lwo) <= 2.0 * bound * fermion
+                so_l[b], lw_l[b] = so, lwo
+    g.close()
+    print(f"uneven graph vs oracle: {compared} decisions compared, {margin} margin events")
+    assert compared >= len(specs) * B * steps - 2

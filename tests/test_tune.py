@@ -21,3 +21,16 @@ def test_autotune_picks_an_accurate_candidate():
     best, res = autotune_nwrap(12, 4.0, 0.05, -0.5, "3xtf32", batch=4, reps=1)
     assert best in [r[0] for r in res]
     assert dict((r[0], r[2]) for r in res)[best] <= TOL["3xtf32"]
+
+
+@pytest.mark.gpu
+def test_autotune_schedule_tries_both_tiles():
+    import torch
+    from paper_1612_03804_gb300 import build
+    from paper_1612_03804_gb300.tune import TOL, autotune_schedule
+    build.build()
+    torch.cuda.set_device(0)
+    nw, tile, res = autotune_schedule(12, 2.0, 0.05, -0.5, "3xtf32", batch=4, reps=1)
+    assert {r[1] for r in res} == {64, 128}
+    assert (nw, tile) in [(r[0], r[1]) for r in res]
+    assert dict(((r[0], r[1]), r[3]) for r in res)[(nw, tile)] <= TOL["3xtf32"]
