@@ -632,7 +632,7 @@ def separable_arm(env, ctx, d_s, d_lw, d_acc, seed, u=None, mu_eff=None, cf=None
     ctx.set_kinetic_form("separable")
     ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 3 * 10 ** 6, 1, d_acc)
     ctx.sync()
-    K = max(2, args.steps // 2)
+    K = 2
     env.barrier_sync()
     T = env.rank_max(steps_timed(torch, ctx, d_s, d_lw, d_acc, seed, 3 * 10 ** 6 + 1, K))
     prof, sites = profile_step(ctx, lambda: ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 4 * 10 ** 6, 1, d_acc))
