@@ -68,13 +68,14 @@ void oz_release(sldqmc_ctx *c);
 void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long sW, int ldw, int B);
 // Left-looking Cholesky-QR on the tensor cores (mixed modes, same N range):
 // oz_chol_begin fixes the digit exponents of R's columns from diag(W);
-// oz_chol_update subtracts the finished rows' contributions from the panel's
-// rows k0..k0+kb of W and of Y = Q^T (k0 > 0); oz_chol_panel factors the
+// oz_chol_update subtracts the contributions of the finished rows
+// kstart..k0-1 from rows k0..k0+kb of W and of Y = Q^T (kb <= 128, k0 - kstart
+// a multiple of 32 and > 0); oz_chol_panel factors the
 // panel's diagonal block, forms its rows of R and Q^T as products with the
 // block's inverse and splits them for the later panels.  W row stride N,
 // item stride sW; R, Y row stride N, item stride N*N.
 void oz_chol_begin(sldqmc_ctx *c, const double *W, long long sW, int B);
-void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, double *Y, int B);
+void oz_chol_update(sldqmc_ctx *c, int k0, int kb, int kstart, double *W, long long sW, double *Y, int B);
 void oz_chol_panel(sldqmc_ctx *c, int k0, int kb, const double *W, long long sW, double *Y, double *R, int B);
 // Trailing update of the finalisation's blocked LU without a right-hand side
 // (A row stride lda, item stride sA; panel k0..k0+kb with kb = 32), FP64-

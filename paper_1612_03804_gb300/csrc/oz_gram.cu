@@ -940,9 +940,10 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
 }
 
 // Left-looking Cholesky-QR of W = X X^T (row stride N, item stride sW) that
-// forms Q^T = R^-T X^T in Y (row stride N, item stride N*N): before the panel
-// of rows k0..k0+kb the products of all finished rows are subtracted from the
-// panel's rows,
+// forms Q^T = R^-T X^T in Y (row stride N, item stride N*N): before the rows
+// k0..k0+kb the products of the finished rows kstart..k0-1 are subtracted
+// from them (the caller runs it once per block of up to 128 rows with all
+// earlier rows, then per 32-row panel with the block's own finished rows),
 //   Y[k0+r][n]    -= sum_{l<k0} Q^T[l][n] R[l][k0+r],
 //   W[k0+r][k0+n] -= sum_{l<k0} R[l][k0+n] R[l][k0+r],
 // FP64-accurate on the tensor cores in one launch of two parts (the product
@@ -960,7 +961,7 @@ void oz_chol_begin(sldqmc_ctx *c, const double *W, long long sW, int B)
     c->launches++;
 }
 
-void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, double *Y, int B)
+void oz_chol_update(sldqmc_ctx *c, int k0, int kb, int kstart, double *W, long long sW, double *Y, int B)
 {
     OzWs *w = (OzWs *)c->oz_ws;
     const int N = c->N;
@@ -971,11 +972,14 @@ void oz_chol_update(sldqmc_ctx *c, int k0, int kb, double *W, long long sW, doub
     a.Nn = kb;
     a.brow0 = k0;
     a.batch = B;
-    a.nk = k0 / OKE;
+    a.kA0 = kstart;
+    a.kB0 = kstart;
+    a.nk = (k0 - kstart) / OKE;
     a.EB = w->ER + k0;
     a.sEB = N;
     a.flag = c->d_flag;
-    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * (2 * N - k0) * kb * k0 * B, "oz_chol_update");
+    prof_begin(c, SLDQMC_KC_GEMM_OZ, 2.0 * (2 * N - k0) * kb * (k0 - kstart) * B,
+               kstart ? "oz_chol_update_inner" : "oz_chol_update");
     k_oz_gemm<false, true, true>
         <<<oz_grid<false>(w, a), OTHREADS, oz_smem_bytes(), c->st>>>(w->mapA, w->mapRA, w->mapRB, a);
     prof_end(c);

@@ -864,14 +864,27 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
     // product also splits the finished rows for the later panels.  Otherwise
     // right-looking with FP64 triangular solves and trailing updates.
     const bool oz = c->oz_ws != nullptr;
-    if (oz) oz_chol_begin(c, W, sW, B);
+    if (oz) {
+        // blocks of 128 rows: one update of the block's rows with every earlier
+        // row (128 output columns: four times the tiles of a panel's update, a
+        // quarter of the long-K launches), then per 32-row panel an update with
+        // the block's own finished rows (K <= 96) and the panel itself
+        oz_chol_begin(c, W, sW, B);
+        for (int K0 = 0; K0 < N; K0 += 128) {
+            const int KB = N - K0 < 128 ? N - K0 : 128;
+            if (K0 > 0) oz_chol_update(c, K0, KB, 0, W, sW, Y, B);
+            for (int k0 = K0; k0 < K0 + KB; k0 += 32) {
+                const int kb = N - k0 < 32 ? N - k0 : 32;
+                if (k0 > K0) oz_chol_update(c, k0, kb, K0, W, sW, Y, B);
+                oz_chol_panel(c, k0, kb, W, sW, Y, R, B);
+            }
+        }
+        return;
+    }
     for (int k0 = 0; k0 < N; k0 += 32) {
         int kb = N - k0 < 32 ? N - k0 : 32;
         int nW = N - (k0 + kb);
-        if (oz) {
-            if (k0 > 0) oz_chol_update(c, k0, kb, W, sW, Y, B);
-            oz_chol_panel(c, k0, kb, W, sW, Y, R, B);
-        } else {
+        {
             dim3 grid(cdiv(nW + N, CHOL_THREADS * CHOL_CPT), B);
             // algorithmic flops: factor of the kb x kb block, triangular solves of nW + N columns
             prof_begin(c, SLDQMC_KC_PANEL_F64, (double)B * ((double)kb * kb * kb / 3.0 + (double)(nW + N) * kb * kb), "chol_panel_f64");
@@ -879,7 +892,7 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
             prof_end(c);
             c->launches++;
         }
-        if (nW == 0 || oz) continue;
+        if (nW == 0) continue;
         // W[k0+kb:, k0+kb:] -= R_blk^T R_blk   (upper triangle only)
         GemmF64 g = gemm_desc(nW, nW, kb, R + (long long)k0 * N + k0 + kb, N, nn,
                               R + (long long)k0 * N + k0 + kb, N, nn,

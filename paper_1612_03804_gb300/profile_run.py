@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--prec", default="3xtf32")
     ap.add_argument("--kinetic", default="dense", choices=["dense", "separable"])
+    ap.add_argument("--tile", type=int, default=64, choices=[64, 128])
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
     args = ap.parse_args()
@@ -42,6 +43,8 @@ def main():
     ctx = sldqmc.Context(args.L, args.L, mu=args.mu, xi=1.0, beta=args.beta, dtau=args.dtau, n_wrap=args.n_wrap,
                          prec=args.prec, max_batch=args.batch)
     ctx.set_kinetic_form(args.kinetic)
+    if args.prec != "fp64":
+        ctx.set_tile_n(args.tile)
     kt = -0.5 * math.log(math.tanh(args.dtau * 2.774))
     ctx.set_effective_model(CLASSES, np.array([-args.dtau / args.beta, 0.0, 0.0, -kt / args.beta]))
     B = args.batch

@@ -33,4 +33,8 @@ def test_autotune_schedule_tries_both_tiles():
     nw, tile, res = autotune_schedule(12, 2.0, 0.05, -0.5, "3xtf32", batch=4, reps=1)
     assert {r[1] for r in res} == {64, 128}
     assert (nw, tile) in [(r[0], r[1]) for r in res]
-    assert dict(((r[0], r[1]), r[3]) for r in res)[(nw, tile)] <= TOL["3xtf32"]
+    err = dict(((r[0], r[1]), r[3]) for r in res)
+    assert err[(nw, tile)] <= TOL["3xtf32"]
+    # every pair faster than the chosen one misses the bound
+    ms = dict(((r[0], r[1]), r[2]) for r in res)
+    assert all(err[k] > TOL["3xtf32"] for k in ms if ms[k] < ms[(nw, tile)])
