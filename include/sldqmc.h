@@ -270,10 +270,11 @@ int sldqmc_set_kinetic_form(sldqmc_ctx *ctx, int form);
 /* Output tile of the tensor-core slice products of the mixed modes:
  * 128 x 64 (bn = 64, default) with the FP32 accumulation spread over eight
  * tensor-memory accumulators, or 128 x 128 (bn = 128) with four, which reads
- * half the shared-memory operand bytes per flop and puts each accumulator
- * under three times as many MMAs (a larger FP32 accumulation error: 1.4e-6
- * relative in log|det| at 16x16, M = 160, in split-TF32, against 6.7e-7 with
- * bn = 64).  The autotuner keeps bn = 128 only where it meets the mode's
+ * fewer shared-memory operand bytes per flop.  Four accumulators over the
+ * whole K would take three times as many MMAs each (1.4e-6 relative log|det|
+ * error at 16x16, M = 160, in split-TF32, against 6.7e-7 with bn = 64), so a
+ * 128-wide tile drains its accumulators into registers after each third of
+ * K.  The autotuner picks the faster tile whose error meets the mode's
  * bound.  FP64 mode: only 64 is accepted. */
 int sldqmc_set_tile_n(sldqmc_ctx *ctx, int bn);
 

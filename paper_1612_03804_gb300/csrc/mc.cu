@@ -124,11 +124,21 @@ __global__ void __launch_bounds__(512) k_local_flips(LocalArgs a)
     extern __shared__ double sh[];
     double *col = sh;           // 2N
     double *row = sh + 2 * N;   // 2N
-    __shared__ double coef[2];
+    double *lus = sh + 4 * N;   // N: log u of every site of the slice
+    __shared__ double coef[2], dls[2][2];
     __shared__ int accept;
     const uint64_t seed = a.seed + ((uint64_t)b << 32);
     long long n_acc = 0, n_mg = 0;
     const int tau = a.tau;
+    // off the serial chain: the uniforms of all sites, and Delta_f for both field values
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        lus[i] = log(philox_uniform(seed, (uint32_t)i, (uint32_t)tau, a.sweep, PURPOSE_LOCAL));
+    if (threadIdx.x < 4) {
+        const int f = threadIdx.x >> 1, sp = threadIdx.x & 1;
+        const double eta = f == 0 ? 1.0 : -1.0;
+        dls[f][sp] = exp(-2.0 * eta * a.dtxi * (sp ? 1.0 : -1.0)) - 1.0;
+    }
+    __syncthreads();
     for (int i = 0; i < N; ++i) {
         if (threadIdx.x == 0) {
             const int sold = s[tau * N + i];
@@ -141,13 +151,11 @@ __global__ void __launch_bounds__(512) k_local_flips(LocalArgs a)
                                     __dadd_rn(__dmul_rn(a.dtauJ, (double)nsp), __dmul_rn(a.Kt, (double)ntm)));
             double R[2], Dl[2];
             for (int f = 0; f < 2; ++f) {
-                const double eta = f == 0 ? 1.0 : -1.0;
-                Dl[f] = exp(-2.0 * eta * a.dtxi * (double)sold) - 1.0;
+                Dl[f] = dls[f][sold > 0];
                 R[f] = __dadd_rn(1.0, __dmul_rn(Dl[f], __dadd_rn(1.0, -G[f][(long long)i * N + i])));
                 logr = __dadd_rn(logr, __dmul_rn(2.0, log(fabs(R[f]))));
             }
-            const double u = philox_uniform(seed, (uint32_t)i, (uint32_t)tau, a.sweep, PURPOSE_LOCAL);
-            const double lu = log(u);
+            const double lu = lus[i];
             if (fabs(logr - lu) <= MARGIN) n_mg++;
             const int acc = lu < logr;
             accept = acc;
@@ -223,13 +231,22 @@ __global__ void __launch_bounds__(512) k_local_flips_delayed(DelayArgs d)
     }
     int8_t *s = a.s + (long long)b * a.M * N;
     __shared__ double ui[2][32], vi[2][32];  // U[i, :n] and V[:n, i] of the current site
-    __shared__ double coef[2];
+    __shared__ double coef[2], dls[2][2], lus[32];
     __shared__ int accept;
     const uint64_t seed = a.seed + ((uint64_t)b << 32);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     long long n_acc = 0, n_mg = 0;
     const int tau = a.tau;
     int n = 0;  // pending pairs
+    // off the serial chain: the block's uniforms, and Delta_f for both field values
+    if (tid < d.ns)
+        lus[tid] = log(philox_uniform(seed, (uint32_t)(d.i0 + tid), (uint32_t)tau, a.sweep, PURPOSE_LOCAL));
+    if (tid >= 32 && tid < 36) {
+        const int f = (tid - 32) >> 1, sp = tid & 1;
+        const double eta = f == 0 ? 1.0 : -1.0;
+        dls[f][sp] = exp(-2.0 * eta * a.dtxi * (sp ? 1.0 : -1.0)) - 1.0;
+    }
+    __syncthreads();
     for (int q = 0; q < d.ns; ++q) {
         const int i = d.i0 + q;
         if (wid == 0) {
@@ -255,13 +272,11 @@ __global__ void __launch_bounds__(512) k_local_flips_delayed(DelayArgs d)
                                         __dadd_rn(__dmul_rn(a.dtauJ, (double)nsp), __dmul_rn(a.Kt, (double)ntm)));
                 double R[2], Dl[2];
                 for (int f = 0; f < 2; ++f) {
-                    const double eta = f == 0 ? 1.0 : -1.0;
-                    Dl[f] = exp(-2.0 * eta * a.dtxi * (double)sold) - 1.0;
+                    Dl[f] = dls[f][sold > 0];
                     R[f] = __dadd_rn(1.0, __dmul_rn(Dl[f], __dadd_rn(1.0, -dg[f])));
                     logr = __dadd_rn(logr, __dmul_rn(2.0, log(fabs(R[f]))));
                 }
-                const double u = philox_uniform(seed, (uint32_t)i, (uint32_t)tau, a.sweep, PURPOSE_LOCAL);
-                const double lu = log(u);
+                const double lu = lus[q];
                 if (fabs(logr - lu) <= MARGIN) n_mg++;
                 const int acc = lu < logr;
                 accept = acc;
@@ -533,7 +548,7 @@ void launch_local_flips(sldqmc_ctx *c, double *Gp, double *Gm, int8_t *d_s, int 
     a.Gp = Gp; a.Gm = Gm; a.nn = c->nn; a.s = d_s;
     a.Lx = c->p.Lx; a.Ly = c->p.Ly; a.M = c->M; a.tau = tau; a.sweep = sweep; a.seed = seed;
     a.dtxi = c->p.dtau * c->p.xi; a.dtauJ = c->dtauJ; a.Kt = c->Ktau; a.stats = stats;
-    size_t sh = sizeof(double) * 4 * (size_t)c->N;
+    size_t sh = sizeof(double) * 5 * (size_t)c->N;
     int nt = c->N * c->N >= 512 ? 512 : 256;
     prof_begin(c, SLDQMC_KC_LOCAL, 0.0, "local_flips");
     k_local_flips<<<B, nt, sh, c->st>>>(a);

@@ -818,9 +818,11 @@ int sldqmc_local_sweep_batch_dev(sldqmc_ctx *c, int8_t *d_s, int B, uint64_t see
                                  int n_sweeps, sldqmc_stats *stats)
 {
     if (!c || B < 1 || B > c->cap || !d_s || n_sweeps < 0) return SLDQMC_ERR_ARG;
-    // the flip kernel stages a column and a row of both Green's functions
-    // in shared memory: 4N doubles within the 200 KB opt-in limit
-    if (c->N > 6400) return SLDQMC_ERR_UNSUPPORTED;
+    // the rank-1 flip kernel stages a column and a row of both Green's
+    // functions and the slice's log-uniforms in shared memory: 5N doubles
+    // within the 200 KB opt-in limit (the delayed path keeps its pairs in
+    // global memory)
+    if (c->N > 5120 && c->local_rank <= 1) return SLDQMC_ERR_UNSUPPORTED;
     int rc = ensure_local_buffers(c);
     if (rc) return rc;
     const long long V = (long long)c->N * c->M;

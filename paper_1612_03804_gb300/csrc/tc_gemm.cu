@@ -59,6 +59,8 @@ template <int BNT> struct TileCfg {
 
 struct TcArgs {
     int N, ldp, nk, batch;
+    int kseg;      // K-blocks per accumulation segment: the epilogue drains and sums the
+                   // accumulators after each segment (bounds the MMAs per accumulator)
     void *out[3];  // next operand, split in parts (FP32 for split TF32, BF16 otherwise)
     double *out_f64;
     long long s_out, s_f64;
@@ -267,13 +269,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int it = 0, ti = 0;
+            int it = 0, sc = 0;  // K-block and segment counters of this CTA
             bool ok = true;
-            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++ti) {
-                // the epilogue must have drained the previous tile's accumulators
-                if (ti > 0 && !mbar_wait(tmem_free, (ti - 1) & 1, a.flag)) { ok = false; break; }
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+              for (int s0 = 0; s0 < a.nk && ok; s0 += a.kseg, ++sc) {
+                // the epilogue must have drained the previous segment's accumulators
+                if (sc > 0 && !mbar_wait(tmem_free, (sc - 1) & 1, a.flag)) { ok = false; break; }
                 fence_after();
-                for (int kb = 0; kb < a.nk; ++kb, ++it) {
+                const int s1 = s0 + a.kseg < a.nk ? s0 + a.kseg : a.nk;
+                for (int kb = s0; kb < s1; ++kb, ++it) {
                     const int s = it % STAGES;
                     if (!mbar_wait(&full[s], (it / STAGES) & 1, a.flag)) { ok = false; break; }
                     fence_after();
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int k = 0; k < KSTEPS; ++k) {
                         const uint32_t off = k * 32;
-                        const int g = kb * KSTEPS + k;
+                        const int g = (kb - s0) * KSTEPS + k;  // step within the segment
                         if (SPLIT) {
                             // The leading product round-robin over accumulators 0..6; the
                             // small correction products all go to accumulator 7, where their
@@ -309,6 +313,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     mma_commit(&empty[s]);
                 }
                 if (ok) mma_commit(tmem_full);
+              }
             }
         }
     } else {
@@ -316,8 +321,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // [cb, cb + EPI_COLS) of the tile; each thread owns one row.
         const int q4 = warp & 3;
         const int cb = ((warp - 2) >> 2) * EPI_COLS;
-        int ti = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
+        int sc = 0;  // segment counter, in step with the MMA thread's
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
             const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
             const int n0 = tn * BN, m0 = tm * BM;
             // Column scale signs of this warp's columns as a 64-bit mask,
@@ -330,30 +335,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const bool u1 = 32 + lane < EPI_COLS && c0w + 32 + lane < a.N && sn[c0w + 32 + lane] > 0;
                 up_mask = (uint64_t)__ballot_sync(0xffffffffu, u0) | ((uint64_t)__ballot_sync(0xffffffffu, u1) << 32);
             }
-            const bool ok = mbar_wait(tmem_full, ti & 1, a.flag);
-            fence_after();
-            // Drain this warp's accumulator columns into registers (summed over
-            // the accumulators; every accumulator received MMAs since K >= 128),
-            // then hand tensor memory back so that the next tile's MMAs run
-            // while this tile is scaled, split and stored.
+            // Drain this warp's accumulator columns into registers after every
+            // segment (summed over the accumulators; each received MMAs in every
+            // segment), handing tensor memory back each time, so that the next
+            // segment's or tile's MMAs run while this tile is scaled, split and
+            // stored.
             float v[EPI_COLS / 16][16];
 #pragma unroll
-            for (int c = 0; c < EPI_COLS / 16; ++c) {
-                const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cb + c * 16);
+            for (int c = 0; c < EPI_COLS / 16; ++c)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[c][j] = 0.0f;
+            bool ok = true;
+            for (int s0 = 0; s0 < a.nk; s0 += a.kseg, ++sc) {
+                ok = mbar_wait(tmem_full, sc & 1, a.flag);
+                fence_after();
 #pragma unroll
-                for (int q = 0; q < NACC; q += 2) {
-                    uint32_t r0[16], r1[16];
-                    tmem_ld16_nowait(lane_base + (uint32_t)(q * BN), r0);
-                    tmem_ld16_nowait(lane_base + (uint32_t)((q + 1) * BN), r1);
-                    tmem_wait_ld32(r0, r1);
+                for (int c = 0; c < EPI_COLS / 16; ++c) {
+                    const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cb + c * 16);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[c][j] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    for (int q = 0; q < NACC; q += 2) {
+                        uint32_t r0[16], r1[16];
+                        tmem_ld16_nowait(lane_base + (uint32_t)(q * BN), r0);
+                        tmem_ld16_nowait(lane_base + (uint32_t)((q + 1) * BN), r1);
+                        tmem_wait_ld32(r0, r1);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[c][j] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    }
                 }
+                fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_free)) : "memory");
+                if (!ok) break;
             }
-            fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_free)) : "memory");
             if (!ok) break;  // a wait ran out: the flag is raised, stop instead of waiting per tile
             const int mm = m0 + q4 * 32 + lane;
 #pragma unroll
@@ -627,6 +639,10 @@ void tc_chain_block(sldqmc_ctx *c, const double *Ut, const int8_t *d_s, int B, d
         a.s_out = s_out;
         a.s_f64 = c->nn;
         a.flag = c->d_flag;
+        // 128-wide tiles (four accumulators) drain after each third of K, so that
+        // an accumulator takes no more MMAs than in a 64-wide tile (eight
+        // accumulators, one segment)
+        a.kseg = w->bn == 128 ? (a.nk + 2) / 3 : a.nk;
         if (j == nb - 1) {
             a.out_f64 = Xt_out;
         } else {
