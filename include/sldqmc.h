@@ -271,11 +271,12 @@ int sldqmc_set_kinetic_form(sldqmc_ctx *ctx, int form);
  * 128 x 64 (bn = 64, default) with the FP32 accumulation spread over eight
  * tensor-memory accumulators, or 128 x 128 (bn = 128) with four, which reads
  * fewer shared-memory operand bytes per flop.  Four accumulators over the
- * whole K would take three times as many MMAs each (1.4e-6 relative log|det|
- * error at 16x16, M = 160, in split-TF32, against 6.7e-7 with bn = 64), so a
- * 128-wide tile drains its accumulators into registers after each third of
- * K.  The autotuner picks the faster tile whose error meets the mode's
- * bound.  FP64 mode: only 64 is accepted. */
+ * whole K would take three times as many MMAs each, so a 128-wide tile
+ * drains its accumulators into registers after each third of K; its log|det|
+ * error is still larger (split-TF32, 16x16, M = 160: 1.0e-6 against 6.7e-7
+ * with bn = 64; 100x100 uniform field: 8.4e-7 against 4.6e-7).  The
+ * autotuner picks the faster tile whose error meets the mode's bound.  FP64
+ * mode: only 64 is accepted. */
 int sldqmc_set_tile_n(sldqmc_ctx *ctx, int bn);
 
 /* Number of this library's kernels launched on the context since create. */
