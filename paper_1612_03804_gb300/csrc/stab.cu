@@ -826,8 +826,10 @@ void stab_set_limits(int Npad)
         dev = -1;
     }
     std::lock_guard<std::mutex> lk(mu);
+    // always raised from its default: the sort kernel also has static shared
+    // memory, so a dynamic size of exactly 48 KB (Npad = 4096) is already too much
     const size_t sh = (size_t)Npad * (sizeof(double) + sizeof(int));
-    if (dev < 0 || sh > (sort_max[dev] ? sort_max[dev] : (size_t)48 * 1024)) {
+    if (dev < 0 || sh > sort_max[dev]) {
         cudaFuncSetAttribute(k_sort_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
         if (dev >= 0) sort_max[dev] = sh;
     }

@@ -224,3 +224,24 @@ def test_lu_tournament_pivoting_tall_panels(prec):
             G, ldg, sgg = ctx.green(s, -1, 3)
             assert sgg == sm and abs(ldg - ref_m) <= LD_RTOL * abs(ref_m)
             np.testing.assert_allclose(G, Gref, rtol=0, atol=G_ATOL)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32"])
+def test_lattice_between_2048_and_4096_sites(prec):
+    """48x48 (N = 2304): the pivot sort pads to 4096 columns, whose keys take exactly the
+    default 48 KB of dynamic shared memory; the LU has tournament panels.  Uniform fields
+    against the closed form, a random field against the particle-hole identity
+    ld_eta(s; mu) - ld_-eta(s; -mu) = beta N mu + eta dtau xi sum s."""
+    m = O.Model(48, 48, mu=-0.5, xi=1.0, beta=0.5, dtau=0.1)
+    bound = LD_RTOL if prec == "fp64" else 1e-6
+    with _ctx(m, 5, max_batch=1, prec=prec) as ctx:
+        s = np.ones((m.M, m.N), dtype=np.int8)
+        ld, sg = ctx.weight(s, -1)
+        ref = _closed(m, m.mu - 1.0)
+        assert sg == 1 and abs(ld - ref) <= bound * abs(ref), (ld, ref)
+        r = uniform_field(48, m.M, m.N)
+        ld_a, _ = ctx.weight(r, 1)
+    with _ctx(m.replace(mu=0.5), 5, max_batch=1, prec=prec) as ctx:
+        ld_b, _ = ctx.weight(r, -1)
+    rhs = m.beta * m.N * m.mu + m.dtau * m.xi * float(r.astype(np.int64).sum())
+    assert abs((ld_a - ld_b) - rhs) <= 2 * bound * max(abs(ld_a), abs(ld_b)), (ld_a - ld_b, rhs)
