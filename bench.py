@@ -959,10 +959,39 @@ def run_local4(env):
         stats = ctx.local_sweep_batch_dev(s, 17, 5, n_sw)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+    # the same configuration for 128 independent chains (one launch serves them all)
+    from paper_1612_03804_gb300.inputs import batch_uniform
+    Bb = 128
+    with make_ctx(sldqmc, wl, "fp64", Bb, 10) as ctx:
+        sb = torch.from_numpy(batch_uniform(1002, Bb, ctx.M, ctx.N)).cuda()
+        ctx.local_sweep_batch_dev(sb, 18, 0, 2, want_stats=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.local_sweep_batch_dev(sb, 18, 2, 50, want_stats=False)
+        torch.cuda.synchronize()
+        batched = Bb * 50 / (time.perf_counter() - t0)
+    cpu = None
+    if env.rank == 0 and not env.args.skip_cpu:
+        # the FP64 CPU oracle on one host core: one weight and a few local sweeps
+        from oracle import oracle as O
+        m = O.Model(4, 4, t=1.0, mu=0.0, xi=1.0, beta=2.0, dtau=0.1, n_wrap=10)
+        s0 = uniform_field(1001, m.M, m.N)
+        t0 = time.perf_counter()
+        for _ in range(20):
+            O.weight(m, s0, -1)
+        tw = (time.perf_counter() - t0) / 20
+        t0 = time.perf_counter()
+        O.local_sweep(m, s0, 17, 0, 20)
+        ts = (time.perf_counter() - t0) / 20
+        cpu = {"us_per_weight": 1e6 * tw, "us_per_sweep": 1e6 * ts, "cores": 1, "kind": "oracle",
+               "sample": "20 weights and 20 local sweeps of this configuration, one host core"}
     return {"workload": "plain FP64 DQMC, 4x4, mu=0, beta=2, dtau=0.1 (M=20), n_wrap=10, one chain",
             "us_per_weight": us_w, "us_per_sweep": 1e6 * dt / n_sw, "sweeps": n_sw,
             "accept_rate": stats[0]["accepted"] / max(stats[0]["proposed"], 1),
-            "max_drift": stats[0]["max_drift"]}
+            "max_drift": stats[0]["max_drift"], "batched_chains": Bb, "batched_sweeps_per_s": batched,
+            "note": "one chain is launch-latency bound (about ten launches per slice and a stabilised "
+                    "recomputation of G every n_wrap slices); chains batch into the same launches",
+            "cpu_baseline": cpu}
 
 
 # ----------------------------------------- decorrelation at the critical point

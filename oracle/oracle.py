@@ -6,6 +6,11 @@ code with the CUDA path.  Each function cites the part of the paper
 (Xu, Qi, Liu, Fu, Meng, arXiv:1612.03804) it follows; the C source holds the
 arithmetic.
 
+weight_many() and cumulative_chains() only run weight() and
+cumulative_update() for many configurations or chains in spawned processes
+(so that the tests and the benchmark's CPU baseline use every host core); they
+add no arithmetic.
+
 Parity pins: every function here is pinned by tests/test_oracle_pins.py
 against closed forms, library routines, brute force or exact enumeration
 (free-fermion product formula, uniform-field shift, particle-hole identity,
@@ -168,6 +173,36 @@ def weight_many(m, fields, eta, workers=None, tau0=0, want_G=False):
         return [_weight_job(j) for j in jobs]
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_weight_job, jobs))
+
+
+def _chain_job(job):
+    kw, s, logw, classes, J, n_eff, seed, step0, steps = job
+    m = Model(**kw)
+    mags, acc = [], 0
+    for k in range(steps):
+        s, logw, a, _, _, _ = cumulative_update(m, s, logw, classes, J, n_eff, seed, step0 + k)
+        acc += a
+        mags.append(int(np.sum(s.astype(np.int64))))
+    return np.array(mags), acc
+
+
+def cumulative_chains(m, starts, classes, J, n_eff, seeds, step0, steps, workers=None):
+    """Independent cumulative-update chains (one per start configuration, each
+    with its own seed), run as cumulative_update() calls on `workers` spawned
+    processes.  Returns (total magnetisation after every step, shape
+    (steps, chains); accepted steps per chain)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    jobs = [(m.kwargs(), np.ascontiguousarray(st, dtype=np.int8), log_weight_total(m, st), classes,
+             np.ascontiguousarray(J, dtype=np.float64), int(n_eff), int(sd), int(step0), int(steps))
+            for st, sd in zip(starts, seeds)]
+    workers = max(1, min(len(jobs), workers or len(os.sched_getaffinity(0))))
+    if workers == 1:
+        res = [_chain_job(j) for j in jobs]
+    else:
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            res = list(ex.map(_chain_job, jobs))
+    return np.stack([r[0] for r in res], axis=1), np.array([r[1] for r in res])
 
 
 def log_bare_weight(m, s):

@@ -69,8 +69,8 @@ void oz_gram(sldqmc_ctx *c, const double *X, long long sX, double *W, long long 
 // Left-looking Cholesky-QR on the tensor cores (mixed modes, same N range):
 // oz_chol_begin fixes the digit exponents of R's columns from diag(W);
 // oz_chol_update subtracts the contributions of the finished rows
-// kstart..k0-1 from rows k0..k0+kb of W and of Y = Q^T (kb <= 128, k0 - kstart
-// a multiple of 32 and > 0); oz_chol_panel factors the
+// kstart..k0-1 from rows k0..k0+kb of W and of Y = Q^T (k0 - kstart a
+// multiple of 32 and > 0); oz_chol_panel factors the
 // panel's diagonal block, forms its rows of R and Q^T as products with the
 // block's inverse and splits them for the later panels.  W row stride N,
 // item stride sW; R, Y row stride N, item stride N*N.

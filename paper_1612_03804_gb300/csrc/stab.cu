@@ -852,6 +852,7 @@ void launch_init_udv(sldqmc_ctx *c, double *Ut, double *V, int B)
 }
 
 constexpr int CHOL_CPT = 2;      // columns per thread of the panel solves
+constexpr int CHOL_BLOCK = 256;  // rows per block of the left-looking tensor-core Cholesky-QR
 constexpr int CHOL_THREADS = 128; // threads per CTA of the panel kernel
 
 static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double *R, int B)
@@ -867,13 +868,14 @@ static void chol_pass(sldqmc_ctx *c, double *W, long long sW, double *Y, double 
     // right-looking with FP64 triangular solves and trailing updates.
     const bool oz = c->oz_ws != nullptr;
     if (oz) {
-        // blocks of 128 rows: one update of the block's rows with every earlier
-        // row (128 output columns: four times the tiles of a panel's update, a
-        // quarter of the long-K launches), then per 32-row panel an update with
-        // the block's own finished rows (K <= 96) and the panel itself
+        // blocks of CHOL_BLOCK rows: one update of the block's rows with every
+        // earlier row (CHOL_BLOCK output columns: CHOL_BLOCK / 32 times the tiles
+        // of a panel's update, that fraction of the long-K launches), then per
+        // 32-row panel an update with the block's own finished rows (K < CHOL_BLOCK)
+        // and the panel itself
         oz_chol_begin(c, W, sW, B);
-        for (int K0 = 0; K0 < N; K0 += 128) {
-            const int KB = N - K0 < 128 ? N - K0 : 128;
+        for (int K0 = 0; K0 < N; K0 += CHOL_BLOCK) {
+            const int KB = N - K0 < CHOL_BLOCK ? N - K0 : CHOL_BLOCK;
             if (K0 > 0) oz_chol_update(c, K0, KB, 0, W, sW, Y, B);
             for (int k0 = K0; k0 < K0 + KB; k0 += 32) {
                 const int kb = N - k0 < 32 ? N - k0 : 32;
