@@ -199,7 +199,12 @@ def traffic_record(kernel_class, workload="chains16"):
         return None
 
 
-def roofline_entry(prof, prec, pk, workload):
+def dominant_site(sites):
+    """The launch site (one kernel instantiation) with the most event time."""
+    return max(sites, key=lambda k: sites[k]["ms"]) if sites else None
+
+
+def roofline_entry(prof, prec, pk, workload, sites=None):
     """Roofline of the dominant kernel class of a profiled step.
 
     achieved = algorithmic flops of the class (2 N^3 per slice product; the
@@ -211,8 +216,14 @@ def roofline_entry(prof, prec, pk, workload):
     issue_efficiency divides instead by that peak over the MMAs one
     algorithmic product issues (5 split-TF32, 6 split-BF16, 36 digit
     products)."""
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    rec = prof[dom]
+    site = dominant_site(sites) if sites else None
+    if site:
+        # the dominant kernel: one launch site, classed for its peak
+        rec = sites[site]
+        dom = rec["cls"]
+    else:
+        dom = max(prof, key=lambda k: prof[k]["ms"])
+        rec = prof[dom]
     achieved = rec["flops"] / (rec["ms"] * 1e-3) / 1e12 if rec["ms"] > 0 and rec["flops"] > 0 else None
     issue = None
     if dom == "gemm_tc":
@@ -241,7 +252,7 @@ def roofline_entry(prof, prec, pk, workload):
     if achieved and per > 1:
         issue = achieved / (peak / per)
     tr = traffic_record(dom, workload)
-    return {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    return {"kernel": site or dom, "class": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "dtype": dtype,
             "issue_efficiency": issue, "mmas_per_product": per,
             "traffic": tr["bytes_per_launch"] if tr else None,
@@ -249,6 +260,7 @@ def roofline_entry(prof, prec, pk, workload):
             "peak_note": note,
             "launches": rec["launches"], "ms_per_launch": rec["ms"] / max(rec["launches"], 1),
             "share": rec["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-30),
+            "class_share": prof[dom]["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-30),
             "breakdown_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
             "breakdown_tflops": {k: (v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 and v["flops"] > 0
                                      else None) for k, v in prof.items()}}
@@ -515,7 +527,7 @@ def run_large(env):
     # roofline: one profiled step (CUDA events around every launch; flavours serialised)
     prof, sites = profile_step(ctx, lambda: ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, 1, d_acc))
     pk = peaks()
-    roof = roofline_entry(prof, args.prec, pk, "large")
+    roof = roofline_entry(prof, args.prec, pk, "large", sites)
     roof["serialised_step_ms"] = sum(v["ms"] for v in prof.values())
     roof["sites"] = site_table(sites)
 
@@ -638,7 +650,7 @@ def separable_arm(env, ctx, d_s, d_lw, d_acc, seed, u=None, mu_eff=None, cf=None
     prof, sites = profile_step(ctx, lambda: ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 4 * 10 ** 6, 1, d_acc))
     out = {"value": 2 * B * K * env.world / T, "unit": UNIT, "steps": K, "ms_per_step": 1e3 * T / K,
            "slice_products_ms_per_step": prof["sep"]["ms"],
-           "roofline": roofline_entry(prof, prec or args.prec, peaks(), "none"),
+           "roofline": roofline_entry(prof, prec or args.prec, peaks(), "none", sites),
            "note": "exp(-dtau K) = e^{dtau mu} E1x (x) E1y applied as two circular convolutions per row of the "
                    "running product, rows resident in shared memory for a whole block"}
     if u is not None:
@@ -738,7 +750,7 @@ def run_chains16(env):
         samples_per_s = (B * env.world * K / Tmax) / tau
 
     prof, sites = profile_step(ctx, lambda: ctx.cumulative_batch_dev(d_s, d_lw, 1, seed, 10 ** 6, 1, d_acc))
-    roof = roofline_entry(prof, args.prec, peaks(), "chains16")
+    roof = roofline_entry(prof, args.prec, peaks(), "chains16", sites)
     roof["sites"] = site_table(sites)
 
     errors = None

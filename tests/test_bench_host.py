@@ -117,3 +117,20 @@ def test_closed_forms_and_extrapolation():
     assert abs(ld - np.sum(np.log1p(np.exp(-beta * eps)))) < 1e-12
     r = bench.extrapolate_oracle(1.0, dict(L=32, beta=20.0, dtau=0.1))
     assert abs(r - (256 / 1024) ** 3 * (100 / 200)) < 1e-15
+
+
+def test_roofline_reports_the_dominant_launch_site():
+    """The class with the most time can be several kernels; the roofline names the single
+    launch site (one kernel instantiation) with the most time and takes its class's peak."""
+    pk = {"bf16_tflops": 1700.0, "tf32_tflops": 1700.0 * 1100 / 2250, "fp64_tflops": 1700.0 * 1.25 / 2250,
+          "fp32_tflops": 80.0, "source": "measured (sustained)"}
+    sites = {"tc_gemm": {"cls": "gemm_tc", "launches": 10, "ms": 100.0, "flops": 1e13},
+             "oz_gram": {"cls": "gemm_oz", "launches": 2, "ms": 60.0, "flops": 1e12},
+             "oz_update_V": {"cls": "gemm_oz", "launches": 2, "ms": 60.0, "flops": 1e12}}
+    prof = {"gemm_tc": {"launches": 10, "ms": 100.0, "flops": 1e13},
+            "gemm_oz": {"launches": 4, "ms": 120.0, "flops": 2e12}}
+    r = bench.roofline_entry(prof, "3xtf32", pk, "nowhere", sites)
+    assert r["kernel"] == "tc_gemm" and r["class"] == "gemm_tc" and r["dtype"] == "tf32"
+    assert abs(r["achieved"] - 100.0) < 1e-9
+    assert abs(r["share"] - 100.0 / 220.0) < 1e-12 and abs(r["class_share"] - 100.0 / 220.0) < 1e-12
+    assert bench.roofline_entry(prof, "3xtf32", pk, "nowhere")["kernel"] == "gemm_oz"
