@@ -553,3 +553,22 @@ def test_enumeration_cumulative_update_chi2(enum_model):
         assert abs(l - lw[_code(s)]) < 1e-12
     assert 0.05 * n_chain < acc < 0.98 * n_chain
     assert _chi2_p(counts, p) > 0.01
+
+
+# --------------------------------------------------------- parallel helpers
+def test_parallel_helpers_equal_sequential_calls():
+    """weight_many and cumulative_chains only spread weight() and cumulative_update() over
+    processes: same numbers as calling them one by one."""
+    m = O.Model(3, 2, mu=-0.3, xi=1.0, beta=1.0, dtau=0.25, n_wrap=2, J=1.0, h=1.3)
+    fields = [uniform_field(70 + k, m.M, m.N) for k in range(3)]
+    assert O.weight_many(m, fields, 1, workers=2) == [O.weight(m, f, 1) for f in fields]
+    classes = [[(1, 0, 0), (0, 1, 0)], [(0, 0, 1)]]
+    J = np.array([-0.2, -0.5])
+    series, acc = O.cumulative_chains(m, fields[:2], classes, J, 2, [11, 12], 5, 4, workers=2)
+    for c in range(2):
+        s, lw, n_acc = fields[c], O.log_weight_total(m, fields[c]), 0
+        for k in range(4):
+            s, lw, a, _, _, _ = O.cumulative_update(m, s, lw, classes, J, 2, 11 + c, 5 + k)
+            n_acc += a
+            assert series[k, c] == int(s.astype(np.int64).sum())
+        assert acc[c] == n_acc
