@@ -1109,7 +1109,8 @@ def run_effmodel16(env):
         for k in range(100):
             cl.eff_sweeps_batch_dev(sl, 1, 85, k, -1)
         cl.local_sweep_batch_dev(sl, 85, 0, 5, want_stats=False)
-        S = args.effmodel_steps
+        # local sweeps cost O(N^2) per accepted flip: the largest lattice gets a shorter series
+        S = args.effmodel_steps if L <= 16 else max(50, args.effmodel_steps // 3)
         out = torch.zeros((S, B), dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
         ta = time.perf_counter()
@@ -1127,6 +1128,7 @@ def run_effmodel16(env):
         d_acc = torch.zeros(B, dtype=torch.int32, device="cuda")
         torch.cuda.synchronize()
         ta = time.perf_counter()
+        S = args.effmodel_steps
         ser = magnetisation_series(torch, cl, sl, d_lw, d_acc, 86, 0, S, args.effmodel_neff).astype(np.float64)
         dt = time.perf_counter() - ta
         tau, win = tau_int(ser)
