@@ -971,9 +971,9 @@ def run_local4(env):
         stats = ctx.local_sweep_batch_dev(s, 17, 5, n_sw)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-    # the same configuration for 128 independent chains (one launch serves them all)
+    # the same configuration for 1024 independent chains (one launch serves them all)
     from paper_1612_03804_gb300.inputs import batch_uniform
-    Bb = 128
+    Bb = 1024
     with make_ctx(sldqmc, wl, "fp64", Bb, 10) as ctx:
         sb = torch.from_numpy(batch_uniform(1002, Bb, ctx.M, ctx.N)).cuda()
         ctx.local_sweep_batch_dev(sb, 18, 0, 2, want_stats=False)
