@@ -25,7 +25,8 @@
 // (for a Gram matrix only those on or above the diagonal; a launch may carry
 // two parts with their own A rows and outputs): warp 0 streams the 8 + 8
 // digit-plane tiles of a 32-wide K-block by TMA (64-byte swizzle), warp 1
-// issues the 36 MMAs per 16-wide K-step, and eight epilogue warps drain one
+// issues the 36 digit products per 16-wide K-step as eight MMAs (A's plane p
+// against B's planes 0..7-p at once), and eight epilogue warps drain one
 // of two tensor-memory buffers (8 groups x 32 columns each) while the next
 // tile accumulates into the other.  Every mbarrier wait is bounded; a wait
 // that runs out raises the context's timeout flag and the CTA frees its
@@ -73,16 +74,19 @@ __device__ __forceinline__ uint64_t smem_desc64(uint32_t saddr)
     return d;
 }
 
-// kind::f16 with BF16 operands, FP32 accumulator, K-major A and B, M = 128, N = 32.
-constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OBN >> 3) << 17) |
-                              ((uint32_t)(OBM >> 4) << 24);
+// kind::f16 with BF16 operands, FP32 accumulator, K-major A and B, M = 128,
+// N = n (a multiple of 32 up to 256).
+__device__ __forceinline__ constexpr uint32_t oz_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(OBM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc)
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             tmem),
-        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc));
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 // Balanced base-2^7 digits of v = round(|x| 2^(56 - E)) < 2^56 for a double x
@@ -457,42 +461,6 @@ __device__ __forceinline__ double oz_scale2(double x, int e)
     return scalbn(x, e);
 }
 
-// h + l 2^-28 for the two 64-bit integers of a chunk's exact group sums,
-// rounded to nearest even once, built from integer operations: the value is
-// the 128-bit integer h 2^28 + l (|h|, |l| < 2^47, so it is exact), whose
-// leading 53 bits and rounding are found by shifts and the exponent placed
-// directly (the value lies between 2^-28 and 2^47, always a normal double).
-// Equal to fma((double)l, 2^-28, (double)h), without the FP64 pipe, which
-// runs about two instructions per clock per SM on this GPU.
-__device__ __forceinline__ double oz_pair_to_double(long long h, long long l)
-{
-    const __int128 v = ((__int128)h << 28) + (__int128)l;
-    if (v == 0) return 0.0;
-    const bool neg = v < 0;
-    const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-    const unsigned long long uh = (unsigned long long)(u >> 64), ul = (unsigned long long)u;
-    int e = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);
-    unsigned long long mant;
-    if (e <= 52) {
-        mant = ul << (52 - e);  // e <= 52: u fits in the low word
-    } else {
-        const int sh = e - 52;
-        mant = (unsigned long long)(u >> sh);
-        const unsigned __int128 rem = u & ((((unsigned __int128)1) << sh) - 1);
-        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1ull))) {
-            ++mant;
-            if (mant == (1ull << 53)) {
-                mant >>= 1;
-                ++e;
-            }
-        }
-    }
-    const unsigned long long bits = ((unsigned long long)neg << 63) |
-                                    ((unsigned long long)(e - 28 + 1023) << 52) | (mant & ((1ull << 52) - 1));
-    return __longlong_as_double((long long)bits);
-}
-
 struct OzArgs {
     OzPart pt[2];           // pt[1] only with nparts = 2 (its A rows through the second A map)
     int nparts;
@@ -656,7 +624,6 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                     if (cc >= 2 && !mbar_wait(&tmem_free[u], ((cc >> 1) - 1) & 1, a.flag)) { ok = false; break; }
                     fence_after();
                     const uint32_t acc0 = tmem + (uint32_t)(u * OZ_G * OBN);
-                    uint32_t started = 0;
                     const int kc1 = kc0 + OZ_KCHUNK < k_hi ? kc0 + OZ_KCHUNK : k_hi;
                     for (int kb = kc0; kb < kc1; ++kb, ++it) {
                         const int s = it % OSTAGES;
@@ -664,18 +631,20 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                         fence_after();
                         const uint32_t sa = smem_u32(base + s * OSTAGE);
                         const uint32_t sb = sa + OZ_S * OTILE_A;
+                        // The B planes of a stage lie one after another (32 rows each), so
+                        // planes 0..7-p form one K-major operand of 32 (8 - p) rows: a single
+                        // MMA multiplies A's plane p with all of them, and with its output
+                        // starting at column 32 p the product with plane q lands in group
+                        // p + q's accumulator.  Eight MMAs per K-step instead of 36, each
+                        // reading A's plane from shared memory once.  The first MMA of a
+                        // chunk (p = 0) spans every group and initialises all eight.
 #pragma unroll
                         for (int k = 0; k < OKE / 16; ++k) {
 #pragma unroll
                             for (int p = 0; p < OZ_S; ++p) {
-                                const uint64_t da = smem_desc64(sa + p * OTILE_A + k * 32);
-#pragma unroll
-                                for (int q = 0; q < OZ_S - p; ++q) {
-                                    const int g = p + q;
-                                    mma_bf16(acc0 + (uint32_t)(g * OBN), da, smem_desc64(sb + q * OTILE_B + k * 32),
-                                             (started >> g) & 1u);
-                                    started |= 1u << g;
-                                }
+                                mma_bf16(acc0 + (uint32_t)(p * OBN), smem_desc64(sa + p * OTILE_A + k * 32),
+                                         smem_desc64(sb + k * 32), oz_idesc(OBN * (OZ_S - p)),
+                                         (kb != kc0 || k != 0 || p != 0) ? 1u : 0u);
                             }
                         }
                         mma_commit(&empty[s]);
@@ -751,10 +720,10 @@ __global__ void __launch_bounds__(OTHREADS, 1)
                     // the chunk's value (one rounding); the first chunk needs no addition
                     if (kc0 == k_lo) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) w[half * 8 + j] = oz_pair_to_double(h[j], l[j]);
+                        for (int j = 0; j < 8; ++j) w[half * 8 + j] = fma((double)l[j], 0x1p-28, (double)h[j]);
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) w[half * 8 + j] += oz_pair_to_double(h[j], l[j]);
+                        for (int j = 0; j < 8; ++j) w[half * 8 + j] += fma((double)l[j], 0x1p-28, (double)h[j]);
                     }
                 }
                 fence_before();
