@@ -27,8 +27,9 @@
  *   - Matrices are row-major double, N x N.
  *
  * Ownership and threading: a context owns all device memory it allocates
- * (at create time) and one CUDA stream (the caller's, or the legacy default
- * stream when NULL).  Host-pointer calls copy in, run and copy out, and
+ * (at create time, and the exact log weight's second workspace on its first
+ * use, see sldqmc_log_weight_batch_dev) and one CUDA stream (the caller's, or
+ * the legacy default stream when NULL).  Host-pointer calls copy in, run and copy out, and
  * return after the stream has finished (synchronous).  Device-pointer calls
  * (suffix _dev) take caller-owned device memory, are ordered on the
  * context's stream and return before completion; their error flags are
@@ -240,7 +241,15 @@ int sldqmc_graph_sync(sldqmc_graph *g);
 void sldqmc_graph_destroy(sldqmc_graph *g);
 
 /* log omega = log phi + 2 ld(+1) + 2 ld(-1) for B configurations on device
- * buffers (the exact weight a cumulative update needs). */
+ * buffers (the exact weight a cumulative update needs).  The first call
+ * creates a second workspace of twice max_batch with its own stream, if it
+ * takes under a third of the free device memory.  With it, a batch whose
+ * 2B items fit in one wave of CTAs (2B <= the device's SMs) runs both
+ * flavours as one batch [s; -s] at eta = +1 (B_tau(-1) for s is B_tau(+1)
+ * for -s, Eq. 1), so that every launch of the chain serves both; a larger
+ * batch runs the two flavours on the two streams at once.  Without it the
+ * flavours run in sequence on the context.  The results are the same bit
+ * for bit.  B may exceed max_batch (processed in chunks). */
 int sldqmc_log_weight_batch_dev(sldqmc_ctx *ctx, const int8_t *d_s, int B, double *d_logw);
 
 /* Form in which the kinetic propagator exp(-dtau K) enters the slice

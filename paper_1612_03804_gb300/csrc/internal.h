@@ -166,8 +166,9 @@ struct sldqmc_ctx {
     sldqmc::Prof *prof;
     const uint32_t *step_dev;  // when set (graph capture), kernels read the MC step from here
     uint32_t *d_step;          // this context's device step counter
-    sldqmc_ctx *twin;          // second workspace + stream: the other flavour's weight runs concurrently
+    sldqmc_ctx *twin;          // second workspace (twice the capacity) + stream for the exact log weight
     cudaEvent_t ev_fork, ev_join;
     int no_twin;               // set on a twin itself, or when the twin could not be created
+    int num_sms;               // streaming multiprocessors of the context's device
     int kinetic;               // SLDQMC_KINETIC_*: form in which exp(-dtau K) enters the slice products
 };

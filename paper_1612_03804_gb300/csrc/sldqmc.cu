@@ -231,17 +231,19 @@ int weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, int eta, int tau0, doubl
     return SLDQMC_OK;
 }
 
-__global__ void k_add_vec(double *a, const double *b, int B)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < B) a[i] += b[i];
-}
-
-// A second context with the same parameters and its own stream, used to run
-// the eta = -1 weight concurrently with the eta = +1 weight (independent
-// chains of kernels; each fills the other's launch tails).  Created on first
-// use when its workspace takes under a third of the free device memory;
-// otherwise the flavours run in sequence.
+// A second context with the same parameters, twice the batch capacity and
+// its own stream, for the two flavours of the exact log weight.  B_tau(eta =
+// -1) for the field s is B_tau(eta = +1) for the field -s (the flavour only
+// picks which of the two scale constants goes with s = +1), so the items
+// [s_1 .. s_B, -s_1 .. -s_B] at eta = +1 give ld(+1) and ld(-1) of every
+// configuration in one batch, and each latency-bound kernel of the
+// stabilisation (diagonal-block factors, panel products, pivot tournaments)
+// serves both flavours in one launch.  That is the form taken while 2B
+// items fit in one wave of CTAs (2B <= SMs); for larger batches those
+// kernels already fill the GPU, and the flavours run as two batches on the
+// two streams at once, where each fills the other's serial phases.  Created
+// on first use when its workspace takes under a third of the free device
+// memory; otherwise the flavours run in sequence on the context itself.
 sldqmc_ctx *get_twin(sldqmc_ctx *c)
 {
     if (c->no_twin) return nullptr;
@@ -252,7 +254,7 @@ sldqmc_ctx *get_twin(sldqmc_ctx *c)
         c->no_twin = 1;
         return nullptr;
     }
-    const double ws_bytes = 12.0 * (double)c->nn * 8.0 * c->cap + 2.0 * c->M * (double)c->N * c->cap;
+    const double ws_bytes = 2.0 * (12.0 * (double)c->nn * 8.0 * c->cap + 2.0 * c->M * (double)c->N * c->cap);
     if (ws_bytes * 3.0 > (double)free_b) { c->no_twin = 1; return nullptr; }
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -262,6 +264,7 @@ sldqmc_ctx *get_twin(sldqmc_ctx *c)
     }
     sldqmc_ctx *t = nullptr;
     sldqmc_params p = c->p;
+    p.max_batch = 2 * c->cap;
     if (sldqmc_create(&p, (void *)st, &t) != SLDQMC_OK ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -279,10 +282,34 @@ sldqmc_ctx *get_twin(sldqmc_ctx *c)
     return t;
 }
 
+// out = [s; -s] for B configurations of V spins each.
+__global__ void k_pair_fields(const int8_t *__restrict__ s, int8_t *__restrict__ out, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int8_t v = s[i];
+        out[i] = v;
+        out[n + i] = (int8_t)(-v);
+    }
+}
+
+__global__ void k_add_vec(double *a, const double *b, int B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B) a[i] += b[i];
+}
+
+// d_lw[b] = ld[b] + ld[B + b]: the two flavours' 2 log|det| of configuration b.
+__global__ void k_add_halves(double *d_lw, const double *ld, int B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B) d_lw[i] = ld[i] + ld[B + i];
+}
+
 // log omega = log phi + 2 ld(+1) + 2 ld(-1) into d_lw.
 int log_weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, double *d_lw)
 {
     sldqmc_ctx *t = (c->prof && c->prof->on) ? nullptr : get_twin(c);
+    if (t && 2 * B > t->cap) t = nullptr;  // callers chunk by the context's capacity; never more
     if (!t) {
         int rc = weight_run(c, d_s, B, 1, 0, d_lw, nullptr, nullptr, 2.0, 0);
         if (rc) return rc;
@@ -294,13 +321,26 @@ int log_weight_run(sldqmc_ctx *c, const int8_t *d_s, int B, double *d_lw)
     cudaStream_t tst = t->st;
     cudaEventRecord(c->ev_fork, c->st);
     cudaStreamWaitEvent(tst, c->ev_fork, 0);
-    int rc = weight_run(t, d_s, B, -1, 0, t->d_ld_tmp, nullptr, nullptr, 2.0, 0);
-    if (rc) return rc;
-    rc = weight_run(c, d_s, B, 1, 0, d_lw, nullptr, nullptr, 2.0, 0);
-    if (rc) return rc;
-    cudaEventRecord(c->ev_join, tst);
-    cudaStreamWaitEvent(c->st, c->ev_join, 0);
-    k_add_vec<<<cdiv(B, 128), 128, 0, c->st>>>(d_lw, t->d_ld_tmp, B);
+    if (2 * B <= c->num_sms) {
+        // one batch [s; -s] at eta = +1 on the twin
+        const long long n = (long long)B * c->M * c->N;
+        k_pair_fields<<<(int)std::min<long long>(cdiv(n, 256), 4096), 256, 0, tst>>>(d_s, t->d_s_one, n);
+        t->launches++;
+        int rc = weight_run(t, t->d_s_one, 2 * B, 1, 0, t->d_ld_tmp, nullptr, nullptr, 2.0, 0);
+        if (rc) return rc;
+        cudaEventRecord(c->ev_join, tst);
+        cudaStreamWaitEvent(c->st, c->ev_join, 0);
+        k_add_halves<<<cdiv(B, 128), 128, 0, c->st>>>(d_lw, t->d_ld_tmp, B);
+    } else {
+        // eta = -1 on the twin's stream while eta = +1 runs on the context's
+        int rc = weight_run(t, d_s, B, -1, 0, t->d_ld_tmp, nullptr, nullptr, 2.0, 0);
+        if (rc) return rc;
+        rc = weight_run(c, d_s, B, 1, 0, d_lw, nullptr, nullptr, 2.0, 0);
+        if (rc) return rc;
+        cudaEventRecord(c->ev_join, tst);
+        cudaStreamWaitEvent(c->st, c->ev_join, 0);
+        k_add_vec<<<cdiv(B, 128), 128, 0, c->st>>>(d_lw, t->d_ld_tmp, B);
+    }
     c->launches++;
     launch_log_bare(c, d_s, B, d_lw, 1);
     return SLDQMC_OK;
@@ -567,6 +607,14 @@ int sldqmc_create(const sldqmc_params *p, void *stream, sldqmc_ctx **out)
     c->st = (cudaStream_t)stream;
     c->cap = p->max_batch;
     c->nn = N * N;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c->num_sms < 1) {
+            cudaGetLastError();
+            c->num_sms = 148;
+        }
+    }
     for (int e = 0; e < 2; ++e) {
         const double eta = e == 0 ? 1.0 : -1.0;
         c->ex_scale[e][0] = exp(eta * p->dtau * p->xi);

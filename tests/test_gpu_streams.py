@@ -5,10 +5,15 @@
   bit-exact against the FP64 oracle.
 * A tensor-core context created on a non-blocking stream gives the same
   weights, bit for bit, as one on the default stream.
-* The exact log weight runs its two flavours on two streams; the result
-  equals 2 ld(+1) + 2 ld(-1) + log phi from the single-flavour calls bit for
-  bit, equals the sequential evaluation (profiling on), and agrees with the
+* The exact log weight evaluates its two flavours as one batch [s; -s] at
+  eta = +1 on a second context and stream (B = 3), or as two batches on the
+  two streams at once (B = 80: 2B above the SM count); the result equals
+  2 ld(+1) + 2 ld(-1) + log phi from the single-flavour calls bit for bit,
+  equals the sequential evaluation (profiling on), and agrees with the
   oracle within the split-TF32 bound.
+* The identity behind that batch: ld(s, eta = -1) = ld(-s, eta = +1) and the
+  same sign, bit for bit, in every precision mode (B_tau(-1) for s is
+  B_tau(+1) for -s, Eq. 1).
 """
 import numpy as np
 import pytest
@@ -74,10 +79,10 @@ def test_tc_context_on_nonblocking_stream():
     assert np.max(np.abs(out[0] - ref) / np.abs(ref)) < 1e-6
 
 
-def test_log_weight_flavours_on_two_streams():
+@pytest.mark.parametrize("B", [3, 80])
+def test_log_weight_flavours_on_two_streams(B):
     import torch
     m = O.Model(12, 12, beta=1.0, dtau=0.1, mu=-0.5)
-    B = 3
     fields = batch_uniform(78, B, m.M, m.N)
     d_s = torch.from_numpy(fields).cuda()
     with _ctx(m, 5, "3xtf32", B) as ctx:
@@ -99,5 +104,23 @@ def test_log_weight_flavours_on_two_streams():
         ctx.profile(False)
         ctx.sync()
         np.testing.assert_array_equal(lw, lw_seq.cpu().numpy())
-    ref = np.array([O.log_weight_total(m, f) for f in fields])
-    assert np.max(np.abs(lw - ref) / np.abs(ref)) < 1e-6
+    ref = np.array([O.log_weight_total(m, f) for f in fields[:3]])
+    assert np.max(np.abs(lw[:3] - ref) / np.abs(ref)) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x3"])
+def test_flavour_is_the_negated_field(prec):
+    import torch
+    m = O.Model(12, 12, beta=1.0, dtau=0.1, mu=-0.5)
+    B = 3
+    fields = batch_uniform(79, B, m.M, m.N)
+    with _ctx(m, 5, prec, B) as ctx:
+        ld = [torch.zeros(B, dtype=torch.float64, device="cuda") for _ in range(2)]
+        sg = [torch.zeros(B, dtype=torch.int32, device="cuda") for _ in range(2)]
+        ctx.weight_batch_dev(torch.from_numpy(fields).cuda(), -1, ld[0], sg[0])
+        ctx.weight_batch_dev(torch.from_numpy(-fields).cuda(), 1, ld[1], sg[1])
+        ctx.sync()
+        np.testing.assert_array_equal(ld[0].cpu().numpy(), ld[1].cpu().numpy())
+        np.testing.assert_array_equal(sg[0].cpu().numpy(), sg[1].cpu().numpy())
+    ref = [O.weight(m, f, -1)[0] for f in fields]
+    assert np.max(np.abs(ld[0].cpu().numpy() - ref) / np.abs(ref)) < (1e-9 if prec == "fp64" else 1e-6)
