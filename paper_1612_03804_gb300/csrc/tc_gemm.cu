@@ -198,6 +198,30 @@ __device__ __forceinline__ void store_part(void *base, long long o, const float 
     }
 }
 
+// Tile t of the persistent walk -> (item, row strip, column strip).  Within
+// an item the tiles go in groups of TILE_GROUP_M row strips, column-major
+// inside a group: the CTAs of one wave (consecutive t) then share a few
+// 128-row strips of the running product and a few strips of E, rather than
+// one strip of the first and a different strip of E each.  At N = 10^4 the
+// three parts of E (1.2 GB) far exceed L2, and walking columns first
+// streamed E from HBM about once per row strip: at N = 4096 (two items) the
+// grouped walk reads 2.7 instead of 5.8 GB from DRAM per product, in the
+// same time (the kernel is bound by its shared-memory operand traffic).
+constexpr int TILE_GROUP_M = 8;
+
+__device__ __forceinline__ void tc_tile(int t, int tiles_m, int tiles_n, int &b, int &tm, int &tn)
+{
+    const int per_item = tiles_m * tiles_n;
+    b = t / per_item;
+    const int r = t - b * per_item;
+    const int g = r / (TILE_GROUP_M * tiles_n);
+    const int m_first = g * TILE_GROUP_M;
+    const int gm = tiles_m - m_first < TILE_GROUP_M ? tiles_m - m_first : TILE_GROUP_M;
+    const int rr = r - g * TILE_GROUP_M * tiles_n;
+    tm = m_first + rr % gm;
+    tn = rr / gm;
+}
+
 template <int MODE, int BNT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
@@ -256,7 +280,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const CUtensorMap *mA[3] = {&tA0, &tA1, &tA2};
             const CUtensorMap *mB[3] = {&tB0, &tB1, &tB2};
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-                const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
+                int b, tm, tn;
+                tc_tile(t, tiles_m, tiles_n, b, tm, tn);
                 const int n0 = tn * BN, m0 = tm * BM;
                 for (int kb = 0; kb < a.nk; ++kb, ++it) {
                     const int s = it % STAGES;
@@ -351,7 +376,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int cb = ((warp - 2) >> 2) * EPI_COLS;
         int sc = 0;  // segment counter, in step with the MMA thread's
         for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-            const int tn = t % tiles_n, tm = (t / tiles_n) % tiles_m, b = t / (tiles_n * tiles_m);
+            int b, tm, tn;
+            tc_tile(t, tiles_m, tiles_n, b, tm, tn);
             const int n0 = tn * BN, m0 = tm * BM;
             // Column scale signs of this warp's columns as a 64-bit mask,
             // fetched before the accumulators are ready.

@@ -3,8 +3,9 @@
 
 The mixed-precision modes compute W = X X^T for N >= 128 on the BF16 tensor
 cores by error-free digit splitting (exact accumulation in chunks of K <= 384,
-so N = 400 and N = 1024 take two and three chunks); the result must be as
-accurate as FP64 itself.  Inputs are seeded Gaussian rows with power-of-two row scales
+so N = 400 and N = 1024 take two and three chunks; N = 1296 walks two groups
+of row strips, 8 and 3, the last with a partial column of tiles); the result
+must be as accurate as FP64 itself.  Inputs are seeded Gaussian rows with power-of-two row scales
 2^-20 .. 2^20 (the grading of X's columns in the stabilised chain), rows
 whose entries span nine decades, and a zero row.  The error measure is
 |W_ij - W_ij,ref| / sqrt(W_ii W_jj) over the upper triangle."""
@@ -48,12 +49,13 @@ def _err(W, X):
 
 @pytest.mark.parametrize("prec,L1,L2,tensor", [("3xtf32", 12, 12, True), ("bf16x3", 16, 16, True),
                                                ("3xtf32", 16, 24, True), ("3xtf32", 20, 20, True),
-                                               ("bf16x3", 32, 32, True), ("fp64", 16, 16, False)])
+                                               ("bf16x3", 32, 32, True), ("3xtf32", 36, 36, True),
+                                               ("fp64", 16, 16, False)])
 def test_gram_against_extended_precision(prec, L1, L2, tensor):
     import torch
     from paper_1612_03804_gb300 import sldqmc
     N = L1 * L2
-    B = 3 if N <= 400 else 2
+    B = 3 if N <= 400 else (2 if N <= 1024 else 1)
     X = _rows(17 + N, B, N)
     with sldqmc.Context(L1, L2, mu=-0.5, xi=1.0, beta=1.0, dtau=0.1, n_wrap=5, prec=prec, max_batch=B) as ctx:
         dX = torch.from_numpy(X).cuda()
