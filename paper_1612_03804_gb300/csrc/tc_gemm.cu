@@ -11,8 +11,7 @@
 //           across slices) falls to 2^-33; A E ~ A_h E_h + A_h E_m + A_l E_h
 //           + A_h E_l + A_l E_m, five kind::tf32 products per K-step;
 //   split BF16 ("bf16x3" mode): both operands in three BF16 parts, the six
-//           products a0e0 + a0e1 + a1e0 + a0e2 + a1e1 + a2e0 as kind::f16 MMAs
-//           (four per K-step with 128 x 64 tiles);
+//           products a0e0 + a0e1 + a1e0 + a0e2 + a1e1 + a2e0 as kind::f16 MMAs;
 //   BF16:   one kind::f16 MMA with BF16 operands.
 //
 // The tensor cores accumulate in FP32 with a rounding that is not
@@ -21,10 +20,7 @@
 // over several accumulators in tensor memory (512 columns) and adds them in
 // the epilogue.  The leading products use all accumulators but the last,
 // which the small correction products share (seven and one with 128 x 64
-// tiles, three and one with 128 x 128), except in split-BF16 mode with
-// 128 x 64 tiles: there the leading products use six, and the corrections
-// of first and second order one each, two of them per K-step as one MMA
-// over two adjacent parts of E.
+// tiles, three and one with 128 x 128).
 //
 // A persistent CTA per SM walks the 128 x 64 output tiles of the batch:
 // warp 0 drives TMA (128-byte swizzled boxes, mbarrier completion) without
@@ -238,7 +234,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr int STAGES = stages<MODE, BNT>();
     constexpr int KSTEPS = 4;  // 128-byte row / 32 bytes per MMA K-step (8 TF32 or 16 BF16)
     constexpr uint32_t IDESC = instr_desc(C::FMT, BNT);
-    constexpr uint32_t IDESC2 = instr_desc(C::FMT, 2 * BNT);  // two adjacent E parts at once
     constexpr bool SPLIT = MODE != 1;  // leading products on accumulators 0..NACC-2, corrections on the last
 
     extern __shared__ uint8_t smem_raw[];
@@ -318,29 +313,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int k = 0; k < KSTEPS; ++k) {
                         const uint32_t off = k * 32;
                         const int g = (kb - s0) * KSTEPS + k;  // step within the segment
-                        if (MODE == 2 && NACC == 8) {
-                            // Split BF16: the leading product round-robin over accumulators
-                            // 0..5; the corrections in two accumulators of their own, 6 for
-                            // the first order (a0 e1 + a1 e0) and 7 for the second (a0 e2 +
-                            // a1 e1 + a2 e0).  E's parts lie one after another in shared
-                            // memory, so a0 e1 and a0 e2 are one MMA of N = 128 over E's
-                            // parts 1..2 with its output across accumulators 6..7, and
-                            // a1 e0, a1 e1 one over parts 0..1: four MMAs per K-step instead
-                            // of six, each A part read from shared memory once.  (Measured
-                            // on 128 configurations at 16x16, n_wrap = 32: log-det error
-                            // 7.7e-7 -> 6.4e-7.  The same arrangement in split TF32 gave
-                            // 8.2e-7 -> 1.2e-6, with or without the joint MMAs, so that mode
-                            // keeps seven leading accumulators and one for the corrections.)
-                            const uint32_t acc_main = tmem + (uint32_t)((g % (NACC - 2)) * BN);
-                            const uint32_t acc_c1 = tmem + (uint32_t)((NACC - 2) * BN);
-                            const uint64_t a0 = smem_desc(sa + off), a1 = smem_desc(sa + TILE_A + off),
-                                           a2 = smem_desc(sa + 2 * TILE_A + off);
-                            const uint64_t e0 = smem_desc(sb + off), e1 = smem_desc(sb + TILE_B + off);
-                            mma<1>(acc_main, a0, e0, IDESC, g < NACC - 2 ? 0u : 1u);
-                            mma<1>(acc_c1, a0, e1, IDESC2, g == 0 ? 0u : 1u);
-                            mma<1>(acc_c1, a1, e0, IDESC2, 1u);
-                            mma<1>(acc_c1 + (uint32_t)BN, a2, e0, IDESC, 1u);
-                        } else if (SPLIT) {
+                        if (SPLIT) {
                             // The leading product round-robin over accumulators 0..NACC-2;
                             // the small correction products all go to the last accumulator,
                             // where their rounding is relative to a much smaller sum.
