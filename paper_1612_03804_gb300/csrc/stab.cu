@@ -518,7 +518,7 @@ __device__ void lu_gepp_rows(double *P, int *org, int R, int kb, double *pvv, in
     __syncthreads();
 }
 
-// Round 1: row block g of the panel of item b nominates its pivot rows
+// Tournament stage 1: row block g of the panel of item b nominates its pivot rows
 // (panel-relative row numbers) into cand[(b * nblk + g) * 32 + j].
 __global__ void __launch_bounds__(LU_THREADS) k_lu_tslu_local(const double *A, long long sA, int lda, int N, int k0,
                                                               int kb, int nblk, int *cand, int *flag)
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tslu_local(const double *A, l
     if (threadIdx.x < kb) cand[((long long)b * nblk + g) * 32 + threadIdx.x] = threadIdx.x < nr ? org[threadIdx.x] : -1;
 }
 
-// Round 2: partial pivoting on the nominated rows; the pivot rows become
+// Tournament stage 2: partial pivoting on the nominated rows; the pivot rows become
 // the block row (factored), the block row's former rows move into the rows
 // the pivots left (original values), and the interchange record, the log
 // of the pivots and the sign are written as by the one-pass panel kernels.
@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tslu_final(double *A, long lo
     }
 }
 
-// Round 3: multipliers of the rows below the block row, L21 = A21 U11^{-1},
+// Tournament stage 3: multipliers of the rows below the block row, L21 = A21 U11^{-1},
 // one thread per row.
 __global__ void __launch_bounds__(128) k_lu_tslu_l21(double *A, long long sA, int lda, int N, int k0, int kb)
 {
