@@ -123,6 +123,23 @@ def test_particle_hole_identity(L, beta, mu, seed):
         assert abs((a - b) - ref) <= 1e-10 * max(abs(a), 1.0)
 
 
+@pytest.mark.parametrize("Lx,Ly,mu,seed", [(4, 4, -0.5, 11), (3, 5, 0.3, 12)])
+def test_flavours_are_the_negated_field(Lx, Ly, mu, seed):
+    """Eq. 1: B_tau(eta) = e^{-dtau K} diag(e^{eta dtau xi s_tau}), so the eta = -1 weight of s
+    is the eta = +1 weight of -s; and the total weight, log phi + 2 ld(+1) + 2 ld(-1), is
+    invariant under s -> -s (H_s of Eq. 6 is Z2-symmetric).  An eta in the kinetic factor,
+    one flavour counted twice, or a bare-weight term odd in s breaks one of the two."""
+    m = O.Model(Lx, Ly, mu=mu, xi=1.0, beta=2.0, dtau=0.1, n_wrap=5, J=1.0, h=2.774)
+    s = domain_field(seed, m.M, Lx, Ly, corr=2)
+    a, sa = O.weight(m, s, -1)
+    b, sb = O.weight(m, (-s).astype(np.int8), 1)
+    assert sa == sb and abs(a - b) <= 1e-13 * abs(a)
+    c, _ = O.weight(m, s, 1)
+    assert abs(c - a) > 1e-6 * abs(a)  # the two flavours differ on this field
+    lw, lw_neg = O.log_weight_total(m, s), O.log_weight_total(m, (-s).astype(np.int8))
+    assert abs(lw - lw_neg) <= 1e-13 * abs(lw)
+
+
 def _naive(m, s, eta):
     E = sla.expm(-m.dtau * O.build_K(m))
     B = np.eye(m.N)
