@@ -1,7 +1,8 @@
 """The headline configuration, 100x100 (N = 10^4), beta = 10, dtau = 0.1 (M = 100),
-n_wrap = 10, mu = -0.5, xi = 1, split-TF32 slice products with the FP64-accurate
-digit-split stabilisation, where the oracle's dense FP64 chain (about 10^14 flops per
-weight) is out of reach.  Properties that hold at any size, through the C ABI:
+n_wrap = 10, mu = -0.5, xi = 1, split-TF32 slice products (dense exp(-dtau K) as the
+benchmark runs them, and the separable form) with the FP64-accurate digit-split
+stabilisation, where the oracle's dense FP64 chain (about 10^14 flops per weight) is out of
+reach.  Properties that hold at any size, through the C ABI:
 
   - the uniform field s = +1 is free fermions at mu + eta xi (B_tau of Eq. 1 with a
     constant field): log|det| within 1e-6 relative of sum_k log(1 + e^{-beta (eps_k -
@@ -33,9 +34,11 @@ def _lib():
     torch.cuda.set_device(0)
 
 
-def _ctx(mu):
+def _ctx(mu, kinetic):
     from paper_1612_03804_gb300 import sldqmc
-    return sldqmc.Context(L, L, mu=mu, xi=XI, beta=BETA, dtau=DTAU, n_wrap=NW, prec="3xtf32", max_batch=1)
+    c = sldqmc.Context(L, L, mu=mu, xi=XI, beta=BETA, dtau=DTAU, n_wrap=NW, prec="3xtf32", max_batch=1)
+    c.set_kinetic_form(kinetic)
+    return c
 
 
 def _closed(mu_eff):
@@ -47,12 +50,13 @@ def _closed(mu_eff):
     return ld, np.real(np.fft.ifft2(occ))
 
 
-def test_uniform_field_closed_form():
+@pytest.mark.parametrize("kinetic", ["dense", "separable"])
+def test_uniform_field_closed_form(kinetic):
     import torch
     u = torch.ones((1, M, N), dtype=torch.int8, device="cuda")
     idx = torch.arange(N, device="cuda")
     x, y = idx % L, idx // L
-    with _ctx(MU) as ctx:
+    with _ctx(MU, kinetic) as ctx:
         for eta in (1, -1):
             ld = torch.zeros(1, dtype=torch.float64, device="cuda")
             sg = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -68,7 +72,7 @@ def test_uniform_field_closed_form():
                 rows = idx[r0:r0 + 500]
                 gref = g[(y[rows, None] - y[None, :]) % L, (x[rows, None] - x[None, :]) % L]
                 dG = max(dG, float((G[0, r0:r0 + 500] - gref).abs().max()))
-            print(f"100x100 uniform field, eta={eta}: log-det rel err {rel:.2e}, max|dG| {dG:.2e}")
+            print(f"100x100 uniform field, {kinetic}, eta={eta}: log-det rel err {rel:.2e}, max|dG| {dG:.2e}")
             assert sg.item() == 1
             assert rel <= LD_RTOL
             assert dG <= G_ATOL
@@ -76,13 +80,14 @@ def test_uniform_field_closed_form():
             torch.cuda.empty_cache()
 
 
-def test_random_field_particle_hole():
+@pytest.mark.parametrize("kinetic", ["dense", "separable"])
+def test_random_field_particle_hole(kinetic):
     import torch
     s = uniform_field(4242, M, N)
     d_s = torch.from_numpy(s[None]).cuda()
     out = {}
     for mu in (MU, -MU):
-        with _ctx(mu) as ctx:
+        with _ctx(mu, kinetic) as ctx:
             for eta in (1, -1):
                 ld = torch.zeros(1, dtype=torch.float64, device="cuda")
                 sg = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -93,7 +98,7 @@ def test_random_field_particle_hole():
         a, sa = out[(MU, eta)]
         b, sb = out[(-MU, -eta)]
         ref = BETA * N * MU + eta * DTAU * XI * float(s.astype(np.int64).sum())
-        print(f"100x100 random field, eta={eta}: ld(mu) - ld(-mu) - ref = {(a - b) - ref:.3e} "
+        print(f"100x100 random field, {kinetic}, eta={eta}: ld(mu) - ld(-mu) - ref = {(a - b) - ref:.3e} "
               f"(bound {LD_RTOL * (abs(a) + abs(b)):.3e})")
         assert sa == sb
         assert abs((a - b) - ref) <= LD_RTOL * (abs(a) + abs(b))
